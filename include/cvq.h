@@ -1,0 +1,160 @@
+/*
+ * cvq.h -- C-ABI of the GB300 (sm_103a) CV-ADAPT-VQE hot-path library, libcvq.so.
+ *
+ * The library simulates qumode ansatz circuits on a Fock space truncated to
+ * D levels per mode and restricted to the Hamiltonian's symmetry sector
+ * (arXiv 2606.05297):
+ *   - Bose-Hubbard (Eq. BoseHubbard, Sec. III.A): fixed total boson number N,
+ *     D = N + 1 (exact truncation, Sec. III.A);
+ *   - bosonic Kitaev chain with optional Kerr term (Eqs. BosonicKitaevChain,
+ *     BosonicKitaevChain_Kerr, Sec. III.B): fixed global parity, cutoff d.
+ *
+ * State vectors are arrays of cvq_c128 (interleaved re, im; the layout of a
+ * contiguous complex128 tensor) indexed by the lexicographic rank of the
+ * occupation tuple (n_0, ..., n_{L-1}) within the sector, mode 0 most
+ * significant.  For Bose-Hubbard that rank is the combinatorial number system
+ * of compositions of N; for the Kitaev chain (even d) it is
+ * floor(sum_r n_r d^(L-1-r) / 2).
+ *
+ * Conventions shared by every call:
+ *   - Return value: CVQ_OK (0) or an error code; the message of the last error
+ *     on the calling thread is cvq_last_error().  Nothing throws across the ABI.
+ *   - Pointers named *_dev, psi*, sigma, workspace are DEVICE pointers owned by
+ *     the caller (allocated on the current device, 256-byte aligned, not
+ *     aliased unless stated).  Pointers without that mark are HOST pointers.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls only enqueue work; results are valid after the stream is
+ *     synchronised.  Only cvq_init_sector and cvq_set_pool synchronise.
+ *   - Device-side failures are not possible by construction (every index is
+ *     derived from a checked sector); a CUDA launch error is reported as
+ *     CVQ_ECUDA.
+ *   - cvq_sector and cvq_pool are opaque, library-owned, immutable after
+ *     creation, and may be shared by concurrent calls on different streams.
+ *
+ * Limits: 1 <= L <= 16 modes (L >= 2 when periodic); at most 512 pool
+ * elements and 512 gates per call; local cutoff D = N + 1 (BH) or d (BKC) with
+ * 2 <= D <= 16; BKC requires even d; sector dimension <= 2^40.
+ */
+#ifndef CVQ_H
+#define CVQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } cvq_c128;
+
+enum cvq_status {
+    CVQ_OK = 0,
+    CVQ_EINVAL = 1,    /* bad argument (sizes, limits, op outside the sector's symmetry) */
+    CVQ_ENOMEM = 2,    /* host or device allocation failed */
+    CVQ_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    CVQ_ETIMEOUT = 4,  /* a bounded device wait ran out (batched engine) */
+    CVQ_EDEVICE = 5    /* a kernel reported an error through its status word */
+};
+
+enum cvq_kind { CVQ_BH = 0, CVQ_BKC = 1 };
+
+/* Pool generator types.  The gate is exp(theta A) (Sec. IV.B, O_r = exp(theta_r A_r))
+ * with the anti-Hermitian A below and e^{i phi} = i^phase (phase in 0..3):
+ *   HOP      BS(theta, phi), Sec. II.B:  e^{i phi} a_i a_j^dag - e^{-i phi} a_i^dag a_j
+ *   SQ2      S2(theta, phi), Sec. II.B:  e^{i phi} a_i a_j - e^{-i phi} a_i^dag a_j^dag
+ *   SQ1      S(theta, phi),  Sec. II.B:  (e^{-i phi} a_i^2 - e^{i phi} a_i^dag^2) / 2
+ *   PAIRHOP  e^{i phi} a_i^2 a_j^dag^2 - e^{-i phi} a_i^dag^2 a_j^2   (phase 1: i((a_i^dag)^2 a_j^2 + h.c.))
+ *   KERR     K(theta) = exp(i theta N^2), Sec. II.B:  A = i n_i^2
+ *   NN1      A = i n_i (n_i - 1)
+ *   ROT      R(theta) = exp(i theta N), Sec. II.B:  A = i n_i
+ *   XKERR    CK(theta) = exp(i theta N_1 N_2), Sec. II.B:  A = i n_i n_j
+ * j is ignored for single-mode types.  SQ2 and SQ1 break N and are rejected
+ * in a Bose-Hubbard sector (CVQ_EINVAL). */
+enum cvq_op_type {
+    CVQ_OP_HOP = 0, CVQ_OP_SQ2 = 1, CVQ_OP_SQ1 = 2, CVQ_OP_PAIRHOP = 3,
+    CVQ_OP_KERR = 4, CVQ_OP_NN1 = 5, CVQ_OP_ROT = 6, CVQ_OP_XKERR = 7
+};
+
+typedef struct { int type, i, j, phase; } cvq_op;
+
+/* Lattice model.  Bonds b = 0..nb-1 join r = b and s = (b + 1) mod L, with
+ * nb = L (periodic) or L - 1 (open).  H =
+ *     sum_b hop[b] (a_r^dag a_s + a_s^dag a_r) + pair[b] (a_r a_s + a_r^dag a_s^dag)
+ *   + sum_r onsite_nn1[r] n_r (n_r - 1) + onsite_n2[r] n_r^2 + onsite_n[r] n_r.
+ * Eq. (BoseHubbard): hop = -J, onsite_nn1 = -U/2, onsite_n = -mu.
+ * Eq. (BosonicKitaevChain): hop = -J, pair = -Delta, onsite_n = -mu; the Kerr
+ * extension adds onsite_nn1 = -U/2.  Any coefficient array may be NULL (zero).
+ * pair must be zero in a Bose-Hubbard sector. */
+typedef struct {
+    int kind;      /* CVQ_BH or CVQ_BKC */
+    int L;         /* modes */
+    int N;         /* BH: total boson number */
+    int d;         /* BKC: per-mode cutoff (even) */
+    int parity;    /* BKC: 0 even sector, 1 odd sector */
+    int periodic;  /* 1: bond (L-1, 0) present */
+    const double *hop, *pair, *onsite_nn1, *onsite_n2, *onsite_n;  /* host arrays */
+} cvq_model;
+
+typedef struct cvq_sector cvq_sector;
+typedef struct cvq_pool cvq_pool;
+
+/* Message of the last error returned on this thread ("" if none). */
+const char *cvq_last_error(void);
+
+/* Build the sector indexer and Hamiltonian tables (Sec. III) on the current
+ * device.  Copies everything it needs from *m.  Synchronises.  Errors:
+ * EINVAL (limits, odd d, pair terms in BH), ENOMEM, ECUDA. */
+int cvq_init_sector(const cvq_model *m, cvq_sector **out);
+int cvq_sector_dim(const cvq_sector *s, int64_t *dim);
+/* Host-side rank of the occupation tuple occ[0..L-1]; EINVAL if not in the sector. */
+int cvq_sector_index(const cvq_sector *s, const int *occ, int64_t *index);
+void cvq_destroy_sector(cvq_sector *s);
+
+/* Build the operator pool (Sec. IV.B, Table I): for every generator its
+ * block structure within the sector and the eigendecomposition of each
+ * Hermitian block (host FP64 Jacobi), uploaded once.  ops is a host array of
+ * K entries, copied.  Errors: EINVAL (bad type / modes / op that breaks the
+ * sector symmetry), ENOMEM, ECUDA. */
+int cvq_set_pool(const cvq_sector *s, const cvq_op *ops, int K, cvq_pool **out);
+void cvq_destroy_pool(cvq_pool *p);
+
+/* Device workspace, in bytes, needed by the calls below for ansatz length up
+ * to n_max (and for screening the whole pool; p may be NULL for cvq_apply_H
+ * alone).  Every call below takes (workspace, workspace_bytes): a caller-owned
+ * device buffer of at least the size this returns for the call's n, which the
+ * call uses as scratch (no allocation happens inside the calls).  EINVAL if
+ * workspace_bytes is too small.  Calls that share one workspace must be
+ * ordered (same stream). */
+int cvq_workspace_bytes(const cvq_sector *s, const cvq_pool *p, int n_max, size_t *bytes);
+
+/* sigma = H psi (matrix-free sector matvec), and if energy_dev != NULL also
+ * *energy_dev = Re <psi|H|psi> (Sec. IV.A/B energy).  psi and sigma: dim
+ * amplitudes, must not alias.  workspace: >= cvq_workspace_bytes(s, NULL, 0). */
+int cvq_apply_H(const cvq_sector *s, const cvq_c128 *psi, cvq_c128 *sigma, double *energy_dev,
+                void *workspace, size_t workspace_bytes, void *stream);
+
+/* Pool screen, Eq. (grad): grad_dev[k] = <psi|[H, A_{ops[k]}]|psi> = 2 Re <H psi|A psi>
+ * for every pool element (subset == NULL, n_subset ignored, K outputs) or for
+ * the n_subset pool indices in the host array subset (n_subset outputs). */
+int cvq_screen_pool(const cvq_sector *s, const cvq_pool *p, const cvq_c128 *psi, const int *subset,
+                    int n_subset, double *grad_dev, void *workspace, size_t workspace_bytes, void *stream);
+
+/* psi_out = exp(theta_n A_n) ... exp(theta_1 A_1) psi0 (Sec. IV.B ansatz),
+ * A_k = pool element op_ids[k] (host ints), theta host doubles, n >= 0.
+ * psi0 and psi_out may alias. */
+int cvq_apply_ansatz(const cvq_sector *s, const cvq_pool *p, const int *op_ids, const double *theta, int n,
+                     const cvq_c128 *psi0, cvq_c128 *psi_out, void *workspace, size_t workspace_bytes,
+                     void *stream);
+
+/* E(theta) = <psi_n|H|psi_n> and its gradient dE/dtheta_k, k = 0..n-1, by a
+ * reverse (adjoint) state sweep: lambda = H psi_n, then for k = n..1
+ * g_k = 2 Re <lambda|A_k psi_k>, psi <- U_k^dag psi, lambda <- U_k^dag lambda.
+ * E_dev: 1 double, grad_dev: n doubles (device).  psi0 is not modified. */
+int cvq_energy_and_grad(const cvq_sector *s, const cvq_pool *p, const int *op_ids, const double *theta, int n,
+                        const cvq_c128 *psi0, double *E_dev, double *grad_dev, void *workspace,
+                        size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CVQ_H */

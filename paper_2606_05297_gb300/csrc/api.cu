@@ -1,0 +1,587 @@
+// api.cu -- the C-ABI of libcvq.so (include/cvq.h): sector indexer and
+// Hamiltonian tables, pool builder with per-block eigendecompositions, and the
+// entry points that enqueue the kernels.
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "cvq_internal.cuh"
+
+using namespace cvq;
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(CVQ_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CVQ_CUDA(call, what)                         \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+extern "C" const char* cvq_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ objects
+
+struct cvq_sector {
+  SectorDev S;
+  int device;
+};
+
+struct cvq_pool {
+  const cvq_sector* sec;
+  int K;
+  std::vector<TypeDesc> types;   // distinct (type, phase) generators
+  std::vector<int> op_type, op_i, op_j;
+  TypeDesc* types_dev = nullptr;
+  GateArg* ops_dev = nullptr;    // one per pool element (screen)
+  void* blob = nullptr;          // device tables
+  PoolDev P{};
+  int ustride = PHASE_TABLE;     // complex entries per gate in a call's U buffer
+};
+
+static int64_t binom(int n, int k) {
+  if (k < 0 || n < 0 || k > n) return 0;
+  int64_t r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+static int64_t fact_ratio(int lo, int hi) {  // hi! / lo!
+  int64_t r = 1;
+  for (int v = lo + 1; v <= hi; ++v) r *= v;
+  return r;
+}
+
+// ------------------------------------------------------------------ sector
+
+extern "C" int cvq_init_sector(const cvq_model* m, cvq_sector** out) {
+  if (!m || !out) return fail(CVQ_EINVAL, "null argument");
+  *out = nullptr;
+  const int L = m->L;
+  if (L < 1 || L > LMAX) return fail(CVQ_EINVAL, "L = %d outside [1, %d]", L, LMAX);
+  if (m->periodic && L < 2) return fail(CVQ_EINVAL, "periodic chain needs L >= 2");
+  if (m->kind != CVQ_BH && m->kind != CVQ_BKC) return fail(CVQ_EINVAL, "unknown model kind %d", m->kind);
+  SectorDev S;
+  memset(&S, 0, sizeof S);
+  S.kind = m->kind;
+  S.L = L;
+  S.periodic = m->periodic ? 1 : 0;
+  S.nb = m->periodic ? L : L - 1;
+  if (m->kind == CVQ_BH) {
+    if (m->N < 0 || m->N + 1 > DMAX) return fail(CVQ_EINVAL, "BH needs 0 <= N <= %d", DMAX - 1);
+    S.N = m->N;
+    S.D = m->N + 1;
+    if (m->pair)
+      for (int b = 0; b < S.nb; ++b)
+        if (m->pair[b] != 0.0) return fail(CVQ_EINVAL, "pairing term breaks the fixed-N sector");
+    S.dim = binom(S.N + L - 1, L - 1);
+  } else {
+    if (m->d < 2 || m->d > DMAX || (m->d & 1)) return fail(CVQ_EINVAL, "BKC needs even d in [2, %d]", DMAX);
+    S.D = m->d;
+    S.half = m->d / 2;
+    S.parity = m->parity & 1;
+    int64_t full = 1;
+    for (int r = L - 1; r >= 0; --r) {
+      S.stride[r] = full;
+      if (full > ((int64_t)1 << 42) / m->d) return fail(CVQ_EINVAL, "sector dimension above 2^40");
+      full *= m->d;
+    }
+    S.dim = full / 2;
+  }
+  if (S.dim > ((int64_t)1 << 40)) return fail(CVQ_EINVAL, "sector dimension above 2^40");
+  for (int p = 0; p < LMAX; ++p)
+    for (int R = 0; R <= DMAX; ++R) S.G[p][R] = binom(R + p, p);
+  if (S.kind == CVQ_BH) {
+    // two-mode gate work items: classes M = n_i + n_j = 0..N, each holding the
+    // compositions of N - M into the other L - 2 modes
+    int64_t acc = 0;
+    for (int M = 0; M <= S.N; ++M) {
+      S.bh2_off[M] = acc;
+      if (L >= 3) acc += binom(S.N - M + L - 3, L - 3);
+      else if (L == 2) acc += (M == S.N) ? 1 : 0;
+    }
+    S.bh2_off[S.N + 1] = acc;
+    for (int M = S.N + 2; M <= MAX_CLASSES; ++M) S.bh2_off[M] = acc;
+  }
+  for (int b = 0; b < S.nb; ++b) {
+    S.hop[b] = m->hop ? m->hop[b] : 0.0;
+    S.pair[b] = m->pair ? m->pair[b] : 0.0;
+  }
+  for (int r = 0; r < L; ++r) {
+    S.nn1[r] = m->onsite_nn1 ? m->onsite_nn1[r] : 0.0;
+    S.n2[r] = m->onsite_n2 ? m->onsite_n2[r] : 0.0;
+    S.n1[r] = m->onsite_n ? m->onsite_n[r] : 0.0;
+  }
+  for (int n = 0; n < DMAX; ++n)
+    for (int e = -2; e <= 2; ++e) {
+      const int t = n + e;
+      S.sqf[n][e + 2] = (t < 0 || t >= S.D) ? 0.0 : std::sqrt((double)fact_ratio(std::min(n, t), std::max(n, t)));
+    }
+  cvq_sector* s = new (std::nothrow) cvq_sector;
+  if (!s) return fail(CVQ_ENOMEM, "host allocation");
+  s->S = S;
+  CVQ_CUDA(cudaGetDevice(&s->device), "cudaGetDevice");
+  *out = s;
+  return CVQ_OK;
+}
+
+extern "C" int cvq_sector_dim(const cvq_sector* s, int64_t* dim) {
+  if (!s || !dim) return fail(CVQ_EINVAL, "null argument");
+  *dim = s->S.dim;
+  return CVQ_OK;
+}
+
+extern "C" int cvq_sector_index(const cvq_sector* s, const int* occ, int64_t* index) {
+  if (!s || !occ || !index) return fail(CVQ_EINVAL, "null argument");
+  const SectorDev& S = s->S;
+  int tot = 0;
+  for (int r = 0; r < S.L; ++r) {
+    if (occ[r] < 0 || occ[r] >= S.D) return fail(CVQ_EINVAL, "occupation %d of mode %d outside [0, %d)", occ[r], r, S.D);
+    tot += occ[r];
+  }
+  if (S.kind == CVQ_BH) {
+    if (tot != S.N) return fail(CVQ_EINVAL, "occupations sum to %d, sector has N = %d", tot, S.N);
+    int64_t rk = 0;
+    int R = S.N;
+    for (int k = 0; k < S.L - 1; ++k) {
+      rk += S.G[S.L - 1 - k][R] - S.G[S.L - 1 - k][R - occ[k]];
+      R -= occ[k];
+    }
+    *index = rk;
+  } else {
+    if ((tot & 1) != S.parity) return fail(CVQ_EINVAL, "occupation parity differs from the sector's");
+    int64_t f = 0;
+    for (int r = 0; r < S.L; ++r) f += occ[r] * S.stride[r];
+    *index = f >> 1;
+  }
+  return CVQ_OK;
+}
+
+extern "C" void cvq_destroy_sector(cvq_sector* s) { delete s; }
+
+// ------------------------------------------------------------------ pool
+
+// Eigen-decomposition of a real symmetric matrix by cyclic Jacobi rotations:
+// A = V diag(w) V^T, V column m = eigenvector m.  A is overwritten.
+static void jacobi_eigen(std::vector<double>& A, int n, std::vector<double>& V, std::vector<double>& w) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < n; ++q) {
+        const double a = A[(size_t)p * n + q];
+        tot += a * a;
+        if (p != q) off += a * a;
+      }
+    if (off <= 1e-34 * (tot > 0 ? tot : 1.0)) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        // rotation angle phi with tan(2 phi) = 2 a_pq / (a_qq - a_pp); t = tan(phi), smaller root
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - s * akq;
+          A[(size_t)k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - s * aqk;
+          A[(size_t)q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = c * vkp - s * vkq;
+          V[(size_t)k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+struct PoolBuild {
+  std::vector<BlockDesc> blk;
+  std::vector<int2> mem;
+  std::vector<double> F, V, lam;
+};
+
+static std::complex<double> ipow(int p) {
+  static const std::complex<double> t[4] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+  return t[((p % 4) + 4) % 4];
+}
+
+// Build the block tables of one (type, phase) generator in sector S.
+static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, TypeDesc& t) {
+  memset(&t, 0, sizeof t);
+  t.type = type;
+  t.phase = phase & 3;
+  const std::complex<double> e = ipow(phase);
+  std::complex<double> cp(1, 0);
+  switch (type) {
+    case CVQ_OP_HOP: t.di = 1; t.dj = -1; cp = e; break;
+    case CVQ_OP_SQ2: t.di = 1; t.dj = 1; cp = e; break;
+    case CVQ_OP_SQ1: t.di = 2; t.dj = 0; t.single = 1; cp = 0.5 * std::conj(e); break;
+    case CVQ_OP_PAIRHOP: t.di = 2; t.dj = -2; cp = e; break;
+    case CVQ_OP_KERR: t.single = 1; t.diag = 1; break;
+    case CVQ_OP_NN1: t.single = 1; t.diag = 2; break;
+    case CVQ_OP_ROT: t.single = 1; t.diag = 3; break;
+    case CVQ_OP_XKERR: t.diag = 4; break;
+    default: return fail(CVQ_EINVAL, "unknown op type %d", type);
+  }
+  if (S.kind == CVQ_BH && (type == CVQ_OP_SQ2 || type == CVQ_OP_SQ1))
+    return fail(CVQ_EINVAL, "op type %d breaks the fixed-N sector", type);
+  t.cp_re = cp.real();
+  t.cp_im = cp.imag();
+  if (t.diag) return CVQ_OK;
+  const double acp = std::abs(cp);
+  const std::complex<double> om = std::complex<double>(0, 1) * std::conj(cp) / acp;
+  t.om_re = om.real();
+  t.om_im = om.imag();
+  t.blk_base = (int)pb.blk.size();
+  t.mem_base = (int)pb.mem.size();
+  t.f_base = (int)pb.F.size();
+  t.v_base = (int)pb.V.size() / 2;
+  t.lam_base = (int)pb.lam.size();
+  const int D = S.D;
+  t.nclass = (S.kind == CVQ_BH) ? S.N + 1 : 2;
+  auto allowed = [&](int cls, int a, int b) -> bool {
+    if (a < 0 || a >= D) return false;
+    if (t.single) return b == 0 && (a & 1) == cls;
+    if (b < 0 || b >= D) return false;
+    if (S.kind == CVQ_BH) return a + b == cls;
+    return ((a + b) & 1) == cls;
+  };
+  int nu = 0, nmem = 0, nf = 0, nlam = 0;
+  for (int cls = 0; cls < t.nclass; ++cls) {
+    t.class_off[cls] = (int)pb.blk.size() - t.blk_base;
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < (t.single ? 1 : D); ++b) {
+        if (!allowed(cls, a, b) || allowed(cls, a - t.di, b - t.dj)) continue;
+        std::vector<std::pair<int, int>> ch;
+        for (int x = a, y = b; allowed(cls, x, y); x += t.di, y += t.dj) ch.push_back({x, y});
+        const int n = (int)ch.size();
+        if (n > BMAX) return fail(CVQ_EINVAL, "block of size %d exceeds %d", n, BMAX);
+        BlockDesc bd;
+        memset(&bd, 0, sizeof bd);
+        bd.size = n;
+        bd.mem_off = nmem;
+        bd.u_off = nu;
+        bd.f_off = nf;
+        bd.ev_off = nlam;
+        std::vector<double> T((size_t)n * n, 0.0), Vr, w;
+        for (int k = 0; k + 1 < n; ++k) {
+          const int a0 = ch[k].first, b0 = ch[k].second, a1 = ch[k + 1].first, b1 = ch[k + 1].second;
+          double fk = (double)fact_ratio(std::min(a0, a1), std::max(a0, a1));
+          if (!t.single) fk *= (double)fact_ratio(std::min(b0, b1), std::max(b0, b1));
+          fk = std::sqrt(fk);
+          pb.F.push_back(fk);
+          T[(size_t)k * n + k + 1] = T[(size_t)(k + 1) * n + k] = acp * fk;
+        }
+        if (n > 1) {
+          jacobi_eigen(T, n, Vr, w);
+        } else {
+          Vr.assign(1, 1.0);
+          w.assign(1, 0.0);
+        }
+        std::complex<double> omk(1, 0);
+        for (int k = 0; k < n; ++k) {
+          for (int m = 0; m < n; ++m) {
+            const std::complex<double> v = omk * Vr[(size_t)k * n + m];
+            pb.V.push_back(v.real());
+            pb.V.push_back(v.imag());
+          }
+          omk *= om;
+        }
+        for (int m = 0; m < n; ++m) pb.lam.push_back(w[m]);
+        for (auto& pr : ch) pb.mem.push_back(make_int2(pr.first, pr.second));
+        pb.blk.push_back(bd);
+        nu += n * n;
+        nmem += n;
+        nf += n - 1;
+        nlam += n;
+        t.bmax = std::max(t.bmax, n);
+      }
+  }
+  t.class_off[t.nclass] = (int)pb.blk.size() - t.blk_base;
+  t.nblocks = t.class_off[t.nclass];
+  t.nu = nu;
+  return CVQ_OK;
+}
+
+extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_pool** out) {
+  if (!s || !out || (K > 0 && !ops)) return fail(CVQ_EINVAL, "null argument");
+  *out = nullptr;
+  if (K < 0 || K > MAX_GATES) return fail(CVQ_EINVAL, "pool size %d outside [0, %d]", K, MAX_GATES);
+  const SectorDev& S = s->S;
+  cvq_pool* p = new (std::nothrow) cvq_pool;
+  if (!p) return fail(CVQ_ENOMEM, "host allocation");
+  p->sec = s;
+  p->K = K;
+  PoolBuild pb;
+  std::map<std::pair<int, int>, int> seen;
+  for (int k = 0; k < K; ++k) {
+    const cvq_op& o = ops[k];
+    const bool single = (o.type == CVQ_OP_SQ1 || o.type == CVQ_OP_KERR || o.type == CVQ_OP_NN1 || o.type == CVQ_OP_ROT);
+    if (o.i < 0 || o.i >= S.L || (!single && (o.j < 0 || o.j >= S.L || o.j == o.i))) {
+      delete p;
+      return fail(CVQ_EINVAL, "pool element %d has bad modes (%d, %d)", k, o.i, o.j);
+    }
+    const bool diag = (o.type >= CVQ_OP_KERR);
+    const auto key = std::make_pair(o.type, diag ? 0 : (o.phase & 3));
+    auto it = seen.find(key);
+    int ti;
+    if (it == seen.end()) {
+      TypeDesc t;
+      const int rc = build_type(S, o.type, key.second, pb, t);
+      if (rc) { delete p; return rc; }
+      ti = (int)p->types.size();
+      p->types.push_back(t);
+      seen[key] = ti;
+    } else {
+      ti = it->second;
+    }
+    p->op_type.push_back(ti);
+    p->op_i.push_back(o.i);
+    p->op_j.push_back(single ? -1 : o.j);
+  }
+  for (auto& t : p->types) p->ustride = std::max(p->ustride, t.nu);
+  p->ustride = (p->ustride + 15) & ~15;
+  // device tables: types, ops, blocks, members, F, V, lam in one allocation
+  const size_t nT = p->types.size();
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_types = 0;
+  const size_t o_ops = al(o_types + nT * sizeof(TypeDesc));
+  const size_t o_blk = al(o_ops + (size_t)K * sizeof(GateArg));
+  const size_t o_mem = al(o_blk + pb.blk.size() * sizeof(BlockDesc));
+  const size_t o_F = al(o_mem + pb.mem.size() * sizeof(int2));
+  const size_t o_V = al(o_F + pb.F.size() * sizeof(double));
+  const size_t o_lam = al(o_V + pb.V.size() * sizeof(double));
+  const size_t total = al(o_lam + pb.lam.size() * sizeof(double)) + 256;
+  cudaError_t e = cudaMalloc(&p->blob, total);
+  if (e != cudaSuccess) { delete p; return fail(CVQ_ENOMEM, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e)); }
+  char* base = (char*)p->blob;
+  p->types_dev = (TypeDesc*)(base + o_types);
+  p->ops_dev = (GateArg*)(base + o_ops);
+  p->P.blk = (const BlockDesc*)(base + o_blk);
+  p->P.mem = (const int2*)(base + o_mem);
+  p->P.F = (const double*)(base + o_F);
+  p->P.V = (const double*)(base + o_V);
+  p->P.lam = (const double*)(base + o_lam);
+  std::vector<GateArg> ga(K);
+  for (int k = 0; k < K; ++k) {
+    memset(&ga[k], 0, sizeof(GateArg));
+    ga[k].i = p->op_i[k];
+    ga[k].j = p->op_j[k];
+    ga[k].t = p->types[p->op_type[k]];
+    ga[k].U = nullptr;
+  }
+  auto up = [&](size_t off, const void* src, size_t n) -> cudaError_t {
+    return n ? cudaMemcpy(base + off, src, n, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  if ((e = up(o_types, p->types.data(), nT * sizeof(TypeDesc))) != cudaSuccess ||
+      (e = up(o_ops, ga.data(), (size_t)K * sizeof(GateArg))) != cudaSuccess ||
+      (e = up(o_blk, pb.blk.data(), pb.blk.size() * sizeof(BlockDesc))) != cudaSuccess ||
+      (e = up(o_mem, pb.mem.data(), pb.mem.size() * sizeof(int2))) != cudaSuccess ||
+      (e = up(o_F, pb.F.data(), pb.F.size() * sizeof(double))) != cudaSuccess ||
+      (e = up(o_V, pb.V.data(), pb.V.size() * sizeof(double))) != cudaSuccess ||
+      (e = up(o_lam, pb.lam.data(), pb.lam.size() * sizeof(double))) != cudaSuccess) {
+    cudaFree(p->blob);
+    delete p;
+    return cuda_fail(e, "pool upload");
+  }
+  *out = p;
+  return CVQ_OK;
+}
+
+extern "C" void cvq_destroy_pool(cvq_pool* p) {
+  if (!p) return;
+  if (p->blob) cudaFree(p->blob);
+  delete p;
+}
+
+// ------------------------------------------------------------------ workspace
+
+struct Layout {
+  size_t psi, lam, U, partial, total;
+};
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Layout layout(const cvq_sector* s, const cvq_pool* p, int n_max) {
+  Layout l;
+  if (!p) {  // cvq_apply_H alone: one partial sum per CTA
+    l.psi = l.lam = l.U = l.partial = 0;
+    l.total = al256((size_t)NBLK * sizeof(double));
+    return l;
+  }
+  const size_t dim = (size_t)s->S.dim;
+  const int K = p ? p->K : 0;
+  const int ust = p ? p->ustride : PHASE_TABLE;
+  const int nred = std::max(std::max(n_max, K), 1) + 1;
+  l.psi = 0;
+  l.lam = al256(l.psi + dim * sizeof(double2));
+  l.U = al256(l.lam + dim * sizeof(double2));
+  l.partial = al256(l.U + (size_t)std::max(n_max, 0) * ust * sizeof(double2));
+  l.total = al256(l.partial + (size_t)nred * NBLK * sizeof(double));
+  return l;
+}
+
+extern "C" int cvq_workspace_bytes(const cvq_sector* s, const cvq_pool* p, int n_max, size_t* bytes) {
+  if (!s || !bytes) return fail(CVQ_EINVAL, "null argument");
+  if (n_max < 0 || n_max > MAX_GATES) return fail(CVQ_EINVAL, "n_max %d outside [0, %d]", n_max, MAX_GATES);
+  *bytes = layout(s, p, n_max).total;
+  return CVQ_OK;
+}
+
+static int check_ws(const cvq_sector* s, const cvq_pool* p, int n, void* ws, size_t wsb, Layout& l) {
+  if (!ws) return fail(CVQ_EINVAL, "workspace is NULL");
+  if ((uintptr_t)ws & 255) return fail(CVQ_EINVAL, "workspace not 256-byte aligned");
+  l = layout(s, p, n);
+  if (wsb < l.total) return fail(CVQ_EINVAL, "workspace of %zu bytes, %zu needed", wsb, l.total);
+  return CVQ_OK;
+}
+
+// ------------------------------------------------------------------ calls
+
+extern "C" int cvq_apply_H(const cvq_sector* s, const cvq_c128* psi, cvq_c128* sigma, double* energy_dev, void* ws,
+                           size_t wsb, void* stream) {
+  if (!s || !psi || !sigma) return fail(CVQ_EINVAL, "null argument");
+  if ((const void*)psi == (const void*)sigma) return fail(CVQ_EINVAL, "psi and sigma must not alias");
+  Layout l;
+  if (int rc = check_ws(s, nullptr, 0, ws, wsb, l)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* partial = (double*)((char*)ws + l.partial);
+  CVQ_CUDA(launch_apply_H(s->S, (const double2*)psi, (double2*)sigma, energy_dev ? partial : nullptr, st), "apply_H");
+  if (energy_dev) CVQ_CUDA(launch_reduce(partial, 1, NBLK, 1.0, energy_dev, st), "reduce");
+  return CVQ_OK;
+}
+
+extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq_c128* psi, const int* subset,
+                               int n_subset, double* grad_dev, void* ws, size_t wsb, void* stream) {
+  if (!s || !p || !psi || !grad_dev) return fail(CVQ_EINVAL, "null argument");
+  if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
+  SubsetArg sub;
+  if (subset) {
+    if (n_subset < 0 || n_subset > p->K) return fail(CVQ_EINVAL, "n_subset %d outside [0, K=%d]", n_subset, p->K);
+    for (int k = 0; k < n_subset; ++k) {
+      if (subset[k] < 0 || subset[k] >= p->K) return fail(CVQ_EINVAL, "subset[%d] = %d outside the pool", k, subset[k]);
+      sub.idx[k] = subset[k];
+    }
+    sub.n = n_subset;
+  } else {
+    sub.n = p->K;
+    for (int k = 0; k < p->K; ++k) sub.idx[k] = k;
+  }
+  Layout l;
+  if (int rc = check_ws(s, p, 0, ws, wsb, l)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double2* sigma = (double2*)((char*)ws + l.lam);
+  double* partial = (double*)((char*)ws + l.partial);
+  CVQ_CUDA(launch_apply_H(s->S, (const double2*)psi, sigma, nullptr, st), "apply_H");
+  CVQ_CUDA(launch_screen(s->S, p->ops_dev, sub, (const double2*)psi, sigma, partial, st), "screen");
+  CVQ_CUDA(launch_reduce(partial, sub.n, NBLK, 2.0, grad_dev, st), "reduce");
+  return CVQ_OK;
+}
+
+static int prepare_gates(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
+                         double2* U, cudaStream_t st) {
+  if (n < 0 || n > MAX_GATES) return fail(CVQ_EINVAL, "ansatz length %d outside [0, %d]", n, MAX_GATES);
+  if (n > 0 && (!op_ids || !theta)) return fail(CVQ_EINVAL, "null op_ids / theta");
+  BuildArgs a;
+  a.n = n;
+  a.ustride = p->ustride;
+  for (int k = 0; k < n; ++k) {
+    if (op_ids[k] < 0 || op_ids[k] >= p->K) return fail(CVQ_EINVAL, "op_ids[%d] = %d outside the pool", k, op_ids[k]);
+    if (!std::isfinite(theta[k])) return fail(CVQ_EINVAL, "theta[%d] is not finite", k);
+    a.type_of[k] = p->op_type[op_ids[k]];
+    a.op_i[k] = p->op_i[op_ids[k]];
+    a.op_j[k] = p->op_j[op_ids[k]];
+    a.theta[k] = theta[k];
+  }
+  CVQ_CUDA(launch_build_gates(a, p->types.data(), p->types_dev, p->P, U, st), "build gates");
+  return CVQ_OK;
+}
+
+static GateArg gate_arg(const cvq_pool* p, int op, const double2* U) {
+  GateArg g;
+  g.i = p->op_i[op];
+  g.j = p->op_j[op];
+  g.t = p->types[p->op_type[op]];
+  g.U = U;
+  return g;
+}
+
+extern "C" int cvq_apply_ansatz(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
+                                const cvq_c128* psi0, cvq_c128* psi_out, void* ws, size_t wsb, void* stream) {
+  if (!s || !p || !psi0 || !psi_out) return fail(CVQ_EINVAL, "null argument");
+  if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
+  Layout l;
+  if (int rc = check_ws(s, p, n, ws, wsb, l)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double2* U = (double2*)((char*)ws + l.U);
+  if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
+  if (n == 0 && psi_out != psi0)
+    CVQ_CUDA(cudaMemcpyAsync(psi_out, psi0, (size_t)s->S.dim * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy");
+  for (int k = 0; k < n; ++k) {
+    const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
+    const double2* src = (k == 0) ? (const double2*)psi0 : (const double2*)psi_out;
+    CVQ_CUDA(launch_gate(s->S, g, p->P, src, (double2*)psi_out, st), "gate");
+  }
+  return CVQ_OK;
+}
+
+extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta,
+                                   int n, const cvq_c128* psi0, double* E_dev, double* grad_dev, void* ws, size_t wsb,
+                                   void* stream) {
+  if (!s || !p || !psi0 || !E_dev || (n > 0 && !grad_dev)) return fail(CVQ_EINVAL, "null argument");
+  if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
+  Layout l;
+  if (int rc = check_ws(s, p, n, ws, wsb, l)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double2* psi = (double2*)((char*)ws + l.psi);
+  double2* lam = (double2*)((char*)ws + l.lam);
+  double2* U = (double2*)((char*)ws + l.U);
+  double* partial = (double*)((char*)ws + l.partial);
+  if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
+  if (n == 0) CVQ_CUDA(cudaMemcpyAsync(psi, psi0, (size_t)s->S.dim * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy");
+  for (int k = 0; k < n; ++k) {
+    const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
+    CVQ_CUDA(launch_gate(s->S, g, p->P, (k == 0) ? (const double2*)psi0 : psi, psi, st), "gate");
+  }
+  double* pE = partial + (size_t)n * NBLK;
+  CVQ_CUDA(launch_apply_H(s->S, psi, lam, pE, st), "apply_H");
+  CVQ_CUDA(launch_reduce(pE, 1, NBLK, 1.0, E_dev, st), "reduce E");
+  for (int k = n - 1; k >= 0; --k) {
+    const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
+    CVQ_CUDA(launch_gate_adjoint(s->S, g, p->P, psi, lam, partial + (size_t)k * NBLK, st), "adjoint gate");
+  }
+  CVQ_CUDA(launch_reduce(partial, n, NBLK, 2.0, grad_dev, st), "reduce grad");
+  return CVQ_OK;
+}

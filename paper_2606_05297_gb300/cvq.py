@@ -1,0 +1,222 @@
+"""Python binding of libcvq.so (include/cvq.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels behind the C ABI.  PyTorch provides
+device memory (complex128 state tensors, workspaces) and streams.  There is no
+fallback: if the native library is missing or fails to load, importing the
+first function raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .workloads import Model, Op
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcvq.so")
+
+OP_CODES = {"hop": 0, "sq2": 1, "sq1": 2, "pairhop": 3, "kerr": 4, "nn1": 5, "rot": 6, "xkerr": 7}
+KIND_CODES = {"bh": 0, "bkc": 1}
+
+
+class CvqError(RuntimeError):
+    pass
+
+
+class _Model(C.Structure):
+    _fields_ = [("kind", C.c_int), ("L", C.c_int), ("N", C.c_int), ("d", C.c_int), ("parity", C.c_int),
+                ("periodic", C.c_int), ("hop", C.POINTER(C.c_double)), ("pair", C.POINTER(C.c_double)),
+                ("onsite_nn1", C.POINTER(C.c_double)), ("onsite_n2", C.POINTER(C.c_double)),
+                ("onsite_n", C.POINTER(C.c_double))]
+
+
+class _Op(C.Structure):
+    _fields_ = [("type", C.c_int), ("i", C.c_int), ("j", C.c_int), ("phase", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcvq.so (built in-tree by paper_2606_05297_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise CvqError(f"native library {LIB_PATH} is missing: run paper_2606_05297_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, sz, i64 = C.c_void_p, C.c_size_t, C.c_int64
+        L.cvq_last_error.restype = C.c_char_p
+        L.cvq_init_sector.argtypes = [C.POINTER(_Model), C.POINTER(vp)]
+        L.cvq_sector_dim.argtypes = [vp, C.POINTER(i64)]
+        L.cvq_sector_index.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(i64)]
+        L.cvq_destroy_sector.argtypes = [vp]
+        L.cvq_destroy_sector.restype = None
+        L.cvq_set_pool.argtypes = [vp, C.POINTER(_Op), C.c_int, C.POINTER(vp)]
+        L.cvq_destroy_pool.argtypes = [vp]
+        L.cvq_destroy_pool.restype = None
+        L.cvq_workspace_bytes.argtypes = [vp, vp, C.c_int, C.POINTER(sz)]
+        L.cvq_apply_H.argtypes = [vp, vp, vp, vp, vp, sz, vp]
+        L.cvq_screen_pool.argtypes = [vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp, vp, sz, vp]
+        L.cvq_apply_ansatz.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int, vp, vp, vp, sz, vp]
+        L.cvq_energy_and_grad.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int, vp, vp, vp, vp,
+                                          sz, vp]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = lib().cvq_last_error().decode(errors="replace")
+        raise CvqError(f"{what} failed (code {rc}): {msg}")
+
+
+def _dbl(vals, n):
+    a = np.zeros(max(n, 1), dtype=np.float64)
+    if vals:
+        a[:len(vals)] = vals
+    return a
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+class Sector:
+    """cvq_sector: the symmetry sector of a lattice model on the current device."""
+
+    def __init__(self, model: Model):
+        self.model = model
+        nb = model.L if model.periodic else model.L - 1
+        self._arrs = [_dbl(model.hop, nb), _dbl(model.pair, nb), _dbl(model.nn1, model.L), _dbl(model.n2, model.L),
+                      _dbl(model.n1, model.L)]
+        P = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in self._arrs]
+        m = _Model(KIND_CODES[model.kind], model.L, model.N, model.d, model.parity, int(bool(model.periodic)), *P)
+        h = C.c_void_p()
+        _check(lib().cvq_init_sector(C.byref(m), C.byref(h)), "cvq_init_sector")
+        self.h = h
+        dim = C.c_int64()
+        _check(lib().cvq_sector_dim(h, C.byref(dim)), "cvq_sector_dim")
+        self.dim = int(dim.value)
+        self.L = model.L
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.cvq_destroy_sector(self.h)
+            self.h = None
+
+    def index(self, occ: Sequence[int]) -> int:
+        a = (C.c_int * self.L)(*[int(v) for v in occ])
+        out = C.c_int64()
+        _check(lib().cvq_sector_index(self.h, a, C.byref(out)), "cvq_sector_index")
+        return int(out.value)
+
+    def basis_state(self, occ: Sequence[int], device="cuda"):
+        import torch
+        v = torch.zeros(self.dim, dtype=torch.complex128, device=device)
+        v[self.index(occ)] = 1.0
+        return v
+
+    def workspace(self, pool: Optional["Pool"] = None, n_max: int = 0):
+        import torch
+        b = C.c_size_t()
+        _check(lib().cvq_workspace_bytes(self.h, pool.h if pool is not None else None, int(n_max), C.byref(b)),
+               "cvq_workspace_bytes")
+        return torch.empty(int(b.value), dtype=torch.uint8, device="cuda")
+
+
+class Pool:
+    """cvq_pool: operator pool generators with their block eigendecompositions."""
+
+    def __init__(self, sector: Sector, ops: Sequence[Op]):
+        self.sector = sector
+        self.ops = list(ops)
+        K = len(self.ops)
+        arr = (_Op * max(K, 1))(*[_Op(OP_CODES[o.type], o.i, o.j if o.j is not None else -1, o.phase)
+                                  for o in self.ops])
+        h = C.c_void_p()
+        _check(lib().cvq_set_pool(sector.h, arr, K, C.byref(h)), "cvq_set_pool")
+        self.h = h
+        self.K = K
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.cvq_destroy_pool(self.h)
+            self.h = None
+
+
+def _ws(sector, pool, n, ws):
+    if ws is None:
+        ws = sector.workspace(pool, n)
+    return ws, C.c_size_t(ws.numel())
+
+
+def apply_H(sector: Sector, psi, sigma=None, energy=None, ws=None, stream=None):
+    """sigma = H psi; energy (optional 1-element float64 device tensor) = Re <psi|H|psi>."""
+    import torch
+    if sigma is None:
+        sigma = torch.empty_like(psi)
+    ws, wsb = _ws(sector, None, 0, ws)
+    _check(lib().cvq_apply_H(sector.h, _ptr(psi), _ptr(sigma), _ptr(energy) if energy is not None else None,
+                             _ptr(ws), wsb, _stream(stream)), "cvq_apply_H")
+    return sigma
+
+
+def screen_pool(sector: Sector, pool: Pool, psi, subset=None, out=None, ws=None, stream=None):
+    """Eq. (grad) gradients of the pool (or of the pool indices in subset)."""
+    import torch
+    n = pool.K if subset is None else len(subset)
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.float64, device=psi.device)
+    ws, wsb = _ws(sector, pool, 0, ws)
+    if subset is None:
+        sp, ns = None, 0
+    else:
+        sa = (C.c_int * max(n, 1))(*[int(k) for k in subset])
+        sp, ns = sa, n
+    _check(lib().cvq_screen_pool(sector.h, pool.h, _ptr(psi), sp, ns, _ptr(out), _ptr(ws), wsb, _stream(stream)),
+           "cvq_screen_pool")
+    return out[:n]
+
+
+def _ids_theta(op_ids, theta):
+    n = len(op_ids)
+    ids = (C.c_int * max(n, 1))(*[int(k) for k in op_ids])
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+    if th.size != n:
+        raise ValueError("op_ids and theta differ in length")
+    return n, ids, th
+
+
+def apply_ansatz(sector: Sector, pool: Pool, op_ids, theta, psi0, out=None, ws=None, stream=None):
+    """psi_out = prod_k exp(theta_k A_{op_ids[k]}) psi0."""
+    import torch
+    n, ids, th = _ids_theta(op_ids, theta)
+    if out is None:
+        out = torch.empty_like(psi0)
+    ws, wsb = _ws(sector, pool, n, ws)
+    _check(lib().cvq_apply_ansatz(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n, _ptr(psi0),
+                                  _ptr(out), _ptr(ws), wsb, _stream(stream)), "cvq_apply_ansatz")
+    return out
+
+
+def energy_and_grad(sector: Sector, pool: Pool, op_ids, theta, psi0, E=None, grad=None, ws=None, stream=None):
+    """Energy and adjoint gradient of the ansatz; returns device tensors (E[1], grad[n])."""
+    import torch
+    n, ids, th = _ids_theta(op_ids, theta)
+    if E is None:
+        E = torch.empty(1, dtype=torch.float64, device=psi0.device)
+    if grad is None:
+        grad = torch.empty(max(n, 1), dtype=torch.float64, device=psi0.device)
+    ws, wsb = _ws(sector, pool, n, ws)
+    _check(lib().cvq_energy_and_grad(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n, _ptr(psi0),
+                                     _ptr(E), _ptr(grad), _ptr(ws), wsb, _stream(stream)), "cvq_energy_and_grad")
+    return E, grad[:n]
