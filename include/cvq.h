@@ -154,6 +154,43 @@ int cvq_energy_and_grad(const cvq_sector *s, const cvq_pool *p, const int *op_id
                         const cvq_c128 *psi0, double *E_dev, double *grad_dev, void *workspace,
                         size_t workspace_bytes, void *stream);
 
+/* One step of the Lanczos recurrence used for the exact ground energy E0
+ * that defines Delta E = |E - E0| (Sec. IV.B stopping rule; exact
+ * diagonalisation there).  Before the call the caller has w = H v and
+ * alpha_dev[0] = Re <v|H v> (cvq_apply_H with energy_dev = alpha_dev), v of
+ * unit norm, and beta_prev_dev[0] = beta_{j-1} (0 for j = 0; v_prev then
+ * ignored).  The call forms w <- w - alpha v - beta_{j-1} v_prev,
+ * beta_dev[0] = ||w|| and v_next = w / ||w|| (v_next = w if ||w|| = 0).
+ * v_next may alias v_prev; all vectors are dim amplitudes on the device.
+ * workspace: >= cvq_workspace_bytes(s, NULL, 0). */
+int cvq_lanczos_step(const cvq_sector *s, const cvq_c128 *v_prev, const cvq_c128 *v, cvq_c128 *w, cvq_c128 *v_next,
+                     const double *alpha_dev, const double *beta_prev_dev, double *beta_dev, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/* Algorithmic cost of one application of pool element `op` on the whole
+ * sector: bytes (amplitudes read + written, 16 B each) and flops (a complex
+ * multiply-add counts 8) of the forward gate and of its reverse step in
+ * cvq_energy_and_grad (gradient term + U^dag on psi and lambda).  Host only. */
+int cvq_op_cost(const cvq_sector *s, const cvq_pool *p, int op, double *fwd_bytes, double *fwd_flops,
+                double *adj_bytes, double *adj_flops);
+
+/* Live per-kernel timing.  cvq_profile_start(capacity) makes every later
+ * launch by this library (any thread, any stream) record a CUDA event pair on
+ * its stream, up to `capacity` launches; cvq_profile_stop waits for those
+ * events, writes one record per kernel kind into out[0..max_out) (*n_out of
+ * them), and turns timing off.  Each record sums launches, device time and
+ * the algorithmic bytes and flops of those launches.  Errors: EINVAL, ECUDA. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double ms;
+    double bytes;
+    double flops;
+} cvq_kernel_stat;
+
+int cvq_profile_start(int capacity);
+int cvq_profile_stop(cvq_kernel_stat *out, int max_out, int *n_out);
+
 #ifdef __cplusplus
 }
 #endif

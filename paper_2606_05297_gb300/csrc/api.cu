@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -41,6 +42,90 @@ static int cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" const char* cvq_last_error(void) { return g_err.c_str(); }
 
+// ------------------------------------------------------------------ profiling
+
+enum KernelKind { KK_APPLY_H, KK_SCREEN, KK_GATE, KK_GATE_DIAG, KK_ADJ, KK_ADJ_DIAG, KK_BUILD, KK_REDUCE, KK_LANCZOS, KK_COUNT };
+static const char* const kKindName[KK_COUNT] = {"apply_H", "screen", "gate_block", "gate_diag", "adjoint_block",
+                                                "adjoint_diag", "build_unitaries", "reduce", "lanczos"};
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof;
+static size_t g_prof_n = 0;
+
+// Brackets one launch with an event pair on its stream while timing is on.
+struct ProfScope {
+  int idx = -1;
+  cudaStream_t st;
+  ProfScope(int kind, cudaStream_t s, double bytes, double flops) : st(s) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on || g_prof_n >= g_prof.size()) return;
+    idx = (int)g_prof_n++;
+    g_prof[idx].kind = kind;
+    g_prof[idx].bytes = bytes;
+    g_prof[idx].flops = flops;
+    cudaEventRecord(g_prof[idx].a, st);
+  }
+  ~ProfScope() {
+    if (idx >= 0) cudaEventRecord(g_prof[idx].b, st);
+  }
+};
+
+extern "C" int cvq_profile_start(int capacity) {
+  if (capacity <= 0 || capacity > (1 << 22)) return fail(CVQ_EINVAL, "capacity %d outside [1, 2^22]", capacity);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof.size() < (size_t)capacity) {
+    size_t old = g_prof.size();
+    g_prof.resize(capacity);
+    for (size_t k = old; k < g_prof.size(); ++k) {
+      cudaError_t e1 = cudaEventCreate(&g_prof[k].a), e2 = cudaEventCreate(&g_prof[k].b);
+      if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        g_prof.resize(k);
+        return cuda_fail(e1 != cudaSuccess ? e1 : e2, "cudaEventCreate");
+      }
+    }
+  }
+  g_prof_n = 0;
+  g_prof_on = true;
+  return CVQ_OK;
+}
+
+extern "C" int cvq_profile_stop(cvq_kernel_stat* out, int max_out, int* n_out) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = false;
+  cvq_kernel_stat acc[KK_COUNT];
+  memset(acc, 0, sizeof acc);
+  for (size_t k = 0; k < g_prof_n; ++k) {
+    const ProfRec& r = g_prof[k];
+    CVQ_CUDA(cudaEventSynchronize(r.b), "cudaEventSynchronize");
+    float ms = 0.f;
+    CVQ_CUDA(cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+    acc[r.kind].launches += 1;
+    acc[r.kind].ms += ms;
+    acc[r.kind].bytes += r.bytes;
+    acc[r.kind].flops += r.flops;
+  }
+  g_prof_n = 0;
+  int n = 0;
+  for (int k = 0; k < KK_COUNT; ++k) {
+    if (!acc[k].launches) continue;
+    if (out && n < max_out) {
+      out[n] = acc[k];
+      snprintf(out[n].name, sizeof out[n].name, "%s", kKindName[k]);
+    }
+    ++n;
+  }
+  if (n_out) *n_out = std::min(n, max_out);
+  return CVQ_OK;
+}
+
 // ------------------------------------------------------------------ objects
 
 struct cvq_sector {
@@ -58,6 +143,7 @@ struct cvq_pool {
   void* blob = nullptr;          // device tables
   PoolDev P{};
   int ustride = PHASE_TABLE;     // complex entries per gate in a call's U buffer
+  std::vector<int> blk_size;     // host copy of every block's size (costs)
 };
 
 static int64_t binom(int n, int k) {
@@ -372,6 +458,7 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
     p->op_j.push_back(single ? -1 : o.j);
   }
   for (auto& t : p->types) p->ustride = std::max(p->ustride, t.nu);
+  for (auto& b : pb.blk) p->blk_size.push_back(b.size);
   p->ustride = (p->ustride + 15) & ~15;
   // device tables: types, ops, blocks, members, F, V, lam in one allocation
   const size_t nT = p->types.size();
@@ -468,6 +555,89 @@ static int check_ws(const cvq_sector* s, const cvq_pool* p, int n, void* ws, siz
   return CVQ_OK;
 }
 
+// ------------------------------------------------------------------ costs
+
+// Algorithmic bytes and flops of one application of pool element op: every
+// amplitude read and written once; a complex multiply-add = 8 flops.  Block
+// gates: b^2 complex MACs per block (forward); the reverse step applies U^dag
+// to psi and lambda (2 b^2) and forms the tridiagonal A psi and its overlap
+// with lambda (3 b - 2).  Diagonal gates: 1 (forward) or 3 (reverse) per amplitude.
+struct OpCost {
+  double fb, ff, ab, af;
+};
+
+static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
+  const SectorDev& S = s->S;
+  const TypeDesc& t = p->types[p->op_type[op]];
+  OpCost c;
+  const double dim = (double)S.dim;
+  c.fb = 32.0 * dim;
+  c.ab = 64.0 * dim;
+  if (t.diag) {
+    c.ff = 8.0 * dim;
+    c.af = 24.0 * dim;
+    return c;
+  }
+  double ff = 0.0, af = 0.0;
+  for (int cls = 0; cls < t.nclass; ++cls) {
+    double orbits;
+    if (S.kind == CVQ_BH) {
+      orbits = (double)(S.bh2_off[cls + 1] - S.bh2_off[cls]);
+    } else {
+      const int nm = t.single ? 1 : 2;
+      double items = 1.0;
+      for (int r = 0; r < S.L - nm; ++r) items *= S.D;
+      orbits = (S.L == nm) ? (cls == S.parity ? 1.0 : 0.0) : items / 2.0;
+    }
+    double bf = 0.0, baf = 0.0;
+    for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
+      const int b = p->blk_size[t.blk_base + bi];
+      bf += 8.0 * b * b;
+      baf += 8.0 * (2.0 * b * b + 3.0 * b - 2.0);
+    }
+    ff += orbits * bf;
+    af += orbits * baf;
+  }
+  c.ff = ff;
+  c.af = af;
+  return c;
+}
+
+extern "C" int cvq_op_cost(const cvq_sector* s, const cvq_pool* p, int op, double* fwd_bytes, double* fwd_flops,
+                           double* adj_bytes, double* adj_flops) {
+  if (!s || !p || p->sec != s) return fail(CVQ_EINVAL, "bad sector / pool");
+  if (op < 0 || op >= p->K) return fail(CVQ_EINVAL, "op %d outside the pool", op);
+  const OpCost c = op_cost(s, p, op);
+  if (fwd_bytes) *fwd_bytes = c.fb;
+  if (fwd_flops) *fwd_flops = c.ff;
+  if (adj_bytes) *adj_bytes = c.ab;
+  if (adj_flops) *adj_flops = c.af;
+  return CVQ_OK;
+}
+
+// sigma = H psi: every amplitude read and written once; per amplitude the
+// diagonal term (4 flops) and the energy term (4), and 4 flops per
+// off-diagonal matrix element (real coefficient x complex amplitude).
+static void apply_H_cost(const SectorDev& S, double& bytes, double& flops) {
+  const double dim = (double)S.dim;
+  bytes = 32.0 * dim;
+  double offd = 0.0;
+  for (int b = 0; b < S.nb; ++b) {
+    // fraction of sector states where a move (+1, -1) (resp. (+1, +1), (-1, -1)) stays in range
+    double fh, fp = 0.0;
+    if (S.kind == CVQ_BH) {
+      fh = (S.N >= 1) ? (double)S.G[S.L - 1][S.N - 1] / dim : 0.0;  // n_s >= 1: compositions of N - 1
+    } else {
+      const double q = (double)(S.D - 1) / S.D;
+      fh = q * q;
+      fp = q * q;
+    }
+    if (S.hop[b] != 0.0) offd += 2.0 * fh * dim;
+    if (S.pair[b] != 0.0) offd += 2.0 * fp * dim;
+  }
+  flops = 8.0 * dim + 4.0 * offd;
+}
+
 // ------------------------------------------------------------------ calls
 
 extern "C" int cvq_apply_H(const cvq_sector* s, const cvq_c128* psi, cvq_c128* sigma, double* energy_dev, void* ws,
@@ -478,8 +648,16 @@ extern "C" int cvq_apply_H(const cvq_sector* s, const cvq_c128* psi, cvq_c128* s
   if (int rc = check_ws(s, nullptr, 0, ws, wsb, l)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   double* partial = (double*)((char*)ws + l.partial);
-  CVQ_CUDA(launch_apply_H(s->S, (const double2*)psi, (double2*)sigma, energy_dev ? partial : nullptr, st), "apply_H");
-  if (energy_dev) CVQ_CUDA(launch_reduce(partial, 1, NBLK, 1.0, energy_dev, st), "reduce");
+  double hb, hf;
+  apply_H_cost(s->S, hb, hf);
+  {
+    ProfScope ps(KK_APPLY_H, st, hb, hf);
+    CVQ_CUDA(launch_apply_H(s->S, (const double2*)psi, (double2*)sigma, energy_dev ? partial : nullptr, st), "apply_H");
+  }
+  if (energy_dev) {
+    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK, NBLK);
+    CVQ_CUDA(launch_reduce(partial, 1, NBLK, 1.0, energy_dev, st), "reduce");
+  }
   return CVQ_OK;
 }
 
@@ -504,9 +682,24 @@ extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq
   cudaStream_t st = (cudaStream_t)stream;
   double2* sigma = (double2*)((char*)ws + l.lam);
   double* partial = (double*)((char*)ws + l.partial);
-  CVQ_CUDA(launch_apply_H(s->S, (const double2*)psi, sigma, nullptr, st), "apply_H");
-  CVQ_CUDA(launch_screen(s->S, p->ops_dev, sub, (const double2*)psi, sigma, partial, st), "screen");
-  CVQ_CUDA(launch_reduce(partial, sub.n, NBLK, 2.0, grad_dev, st), "reduce");
+  double hb, hf;
+  apply_H_cost(s->S, hb, hf);
+  {
+    ProfScope ps(KK_APPLY_H, st, hb, hf);
+    CVQ_CUDA(launch_apply_H(s->S, (const double2*)psi, sigma, nullptr, st), "apply_H");
+  }
+  {
+    // per screened element and amplitude: the generator row (2 complex MACs, or 1
+    // for a diagonal generator) and its overlap with sigma (1 complex MAC)
+    double fl = 0.0;
+    for (int k = 0; k < sub.n; ++k) fl += (double)s->S.dim * (p->types[p->op_type[sub.idx[k]]].diag ? 16.0 : 24.0);
+    ProfScope ps(KK_SCREEN, st, 32.0 * (double)s->S.dim, fl);
+    CVQ_CUDA(launch_screen(s->S, p->ops_dev, sub, (const double2*)psi, sigma, partial, st), "screen");
+  }
+  {
+    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * sub.n, (double)NBLK * sub.n);
+    CVQ_CUDA(launch_reduce(partial, sub.n, NBLK, 2.0, grad_dev, st), "reduce");
+  }
   return CVQ_OK;
 }
 
@@ -525,6 +718,7 @@ static int prepare_gates(const cvq_sector* s, const cvq_pool* p, const int* op_i
     a.op_j[k] = p->op_j[op_ids[k]];
     a.theta[k] = theta[k];
   }
+  ProfScope ps(KK_BUILD, st, 0.0, 0.0);
   CVQ_CUDA(launch_build_gates(a, p->types.data(), p->types_dev, p->P, U, st), "build gates");
   return CVQ_OK;
 }
@@ -552,6 +746,8 @@ extern "C" int cvq_apply_ansatz(const cvq_sector* s, const cvq_pool* p, const in
   for (int k = 0; k < n; ++k) {
     const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
     const double2* src = (k == 0) ? (const double2*)psi0 : (const double2*)psi_out;
+    const OpCost c = op_cost(s, p, op_ids[k]);
+    ProfScope ps(g.t.diag ? KK_GATE_DIAG : KK_GATE, st, c.fb, c.ff);
     CVQ_CUDA(launch_gate(s->S, g, p->P, src, (double2*)psi_out, st), "gate");
   }
   return CVQ_OK;
@@ -573,15 +769,54 @@ extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const
   if (n == 0) CVQ_CUDA(cudaMemcpyAsync(psi, psi0, (size_t)s->S.dim * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy");
   for (int k = 0; k < n; ++k) {
     const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
+    const OpCost c = op_cost(s, p, op_ids[k]);
+    ProfScope ps(g.t.diag ? KK_GATE_DIAG : KK_GATE, st, c.fb, c.ff);
     CVQ_CUDA(launch_gate(s->S, g, p->P, (k == 0) ? (const double2*)psi0 : psi, psi, st), "gate");
   }
   double* pE = partial + (size_t)n * NBLK;
-  CVQ_CUDA(launch_apply_H(s->S, psi, lam, pE, st), "apply_H");
-  CVQ_CUDA(launch_reduce(pE, 1, NBLK, 1.0, E_dev, st), "reduce E");
+  double hb, hf;
+  apply_H_cost(s->S, hb, hf);
+  {
+    ProfScope ps(KK_APPLY_H, st, hb, hf);
+    CVQ_CUDA(launch_apply_H(s->S, psi, lam, pE, st), "apply_H");
+  }
+  {
+    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK, NBLK);
+    CVQ_CUDA(launch_reduce(pE, 1, NBLK, 1.0, E_dev, st), "reduce E");
+  }
   for (int k = n - 1; k >= 0; --k) {
     const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
+    const OpCost c = op_cost(s, p, op_ids[k]);
+    ProfScope ps(g.t.diag ? KK_ADJ_DIAG : KK_ADJ, st, c.ab, c.af);
     CVQ_CUDA(launch_gate_adjoint(s->S, g, p->P, psi, lam, partial + (size_t)k * NBLK, st), "adjoint gate");
   }
-  CVQ_CUDA(launch_reduce(partial, n, NBLK, 2.0, grad_dev, st), "reduce grad");
+  {
+    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * n, (double)NBLK * n);
+    CVQ_CUDA(launch_reduce(partial, n, NBLK, 2.0, grad_dev, st), "reduce grad");
+  }
+  return CVQ_OK;
+}
+
+extern "C" int cvq_lanczos_step(const cvq_sector* s, const cvq_c128* v_prev, const cvq_c128* v, cvq_c128* w,
+                                cvq_c128* v_next, const double* alpha_dev, const double* beta_prev_dev, double* beta_dev,
+                                void* ws, size_t wsb, void* stream) {
+  if (!s || !v_prev || !v || !w || !v_next || !alpha_dev || !beta_prev_dev || !beta_dev)
+    return fail(CVQ_EINVAL, "null argument");
+  if ((const void*)w == (const void*)v || (const void*)v_next == (const void*)v || (const void*)v_next == (const void*)w)
+    return fail(CVQ_EINVAL, "w, v and v_next must be distinct");
+  Layout l;
+  if (int rc = check_ws(s, nullptr, 0, ws, wsb, l)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* partial = (double*)((char*)ws + l.partial);
+  const double dim = (double)s->S.dim;
+  {
+    ProfScope ps(KK_LANCZOS, st, 64.0 * dim, 16.0 * dim);
+    CVQ_CUDA(launch_lanczos_update(s->S, (const double2*)v_prev, (const double2*)v, (double2*)w, alpha_dev,
+                                   beta_prev_dev, partial, st), "lanczos update");
+  }
+  {
+    ProfScope ps(KK_LANCZOS, st, 32.0 * dim, 2.0 * dim);
+    CVQ_CUDA(launch_lanczos_scale(s->S, (const double2*)w, (double2*)v_next, partial, beta_dev, st), "lanczos scale");
+  }
   return CVQ_OK;
 }

@@ -170,5 +170,11 @@ struct SubsetArg {
 
 cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const double2* psi,
                           const double2* sigma, double* partial, cudaStream_t st);
+// Lanczos: w <- w - alpha v - beta_prev v_prev with partial sums of ||w||^2,
+// then v_next = w / ||w||.
+cudaError_t launch_lanczos_update(const SectorDev& S, const double2* v_prev, const double2* v, double2* w,
+                                  const double* alpha, const double* beta_prev, double* partial, cudaStream_t st);
+cudaError_t launch_lanczos_scale(const SectorDev& S, const double2* w, double2* v_next, const double* partial,
+                                 double* beta, cudaStream_t st);
 
 }  // namespace cvq

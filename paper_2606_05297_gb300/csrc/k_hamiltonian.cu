@@ -204,3 +204,66 @@ cudaError_t launch_reduce(const double* partial, int nred, int nblk, double scal
 }
 
 }  // namespace cvq
+
+namespace cvq {
+
+// ------------------------------------------------------------ Lanczos
+
+__global__ void __launch_bounds__(NTHREADS) k_lanczos_update(int64_t dim, const double2* __restrict__ vp,
+                                                             const double2* __restrict__ v, double2* __restrict__ w,
+                                                             const double* __restrict__ alpha,
+                                                             const double* __restrict__ beta_prev,
+                                                             double* __restrict__ partial) {
+  const double a = alpha[0], b = beta_prev[0];
+  double acc = 0.0;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < dim; x += (int64_t)gridDim.x * blockDim.x) {
+    double2 t = w[x];
+    const double2 c = v[x];
+    t.x = fma(-a, c.x, t.x);
+    t.y = fma(-a, c.y, t.y);
+    if (b != 0.0) {
+      const double2 q = vp[x];
+      t.x = fma(-b, q.x, t.x);
+      t.y = fma(-b, q.y, t.y);
+    }
+    w[x] = t;
+    acc = fma(t.x, t.x, acc);
+    acc = fma(t.y, t.y, acc);
+  }
+  const double s = block_sum_h(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// beta = sqrt(sum of partials) (fixed order), v_next = w / beta.
+__global__ void __launch_bounds__(NTHREADS) k_lanczos_scale(int64_t dim, const double2* __restrict__ w,
+                                                            double2* __restrict__ vn, const double* __restrict__ partial,
+                                                            double* __restrict__ beta) {
+  __shared__ double nb;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < NBLK; b += blockDim.x) v += partial[b];
+  v = block_sum_h(v);
+  if (threadIdx.x == 0) {
+    nb = sqrt(v);
+    if (blockIdx.x == 0) beta[0] = nb;
+  }
+  __syncthreads();
+  const double inv = (nb > 0.0) ? 1.0 / nb : 1.0;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < dim; x += (int64_t)gridDim.x * blockDim.x) {
+    const double2 t = w[x];
+    vn[x] = make_double2(t.x * inv, t.y * inv);
+  }
+}
+
+cudaError_t launch_lanczos_update(const SectorDev& S, const double2* v_prev, const double2* v, double2* w,
+                                  const double* alpha, const double* beta_prev, double* partial, cudaStream_t st) {
+  k_lanczos_update<<<NBLK, NTHREADS, 0, st>>>(S.dim, v_prev, v, w, alpha, beta_prev, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_scale(const SectorDev& S, const double2* w, double2* v_next, const double* partial,
+                                 double* beta, cudaStream_t st) {
+  k_lanczos_scale<<<NBLK, NTHREADS, 0, st>>>(S.dim, w, v_next, partial, beta);
+  return cudaGetLastError();
+}
+
+}  // namespace cvq

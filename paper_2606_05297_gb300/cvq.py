@@ -63,6 +63,9 @@ def lib():
         L.cvq_apply_ansatz.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int, vp, vp, vp, sz, vp]
         L.cvq_energy_and_grad.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int, vp, vp, vp, vp,
                                           sz, vp]
+        L.cvq_lanczos_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        dp = C.POINTER(C.c_double)
+        L.cvq_op_cost.argtypes = [vp, vp, C.c_int, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -220,3 +223,40 @@ def energy_and_grad(sector: Sector, pool: Pool, op_ids, theta, psi0, E=None, gra
     _check(lib().cvq_energy_and_grad(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n, _ptr(psi0),
                                      _ptr(E), _ptr(grad), _ptr(ws), wsb, _stream(stream)), "cvq_energy_and_grad")
     return E, grad[:n]
+
+
+def lanczos_step(sector: Sector, v_prev, v, w, v_next, alpha, beta_prev, beta, ws=None, stream=None):
+    """w <- w - alpha v - beta_prev v_prev; beta = ||w||; v_next = w / beta (all on the device)."""
+    ws, wsb = _ws(sector, None, 0, ws)
+    _check(lib().cvq_lanczos_step(sector.h, _ptr(v_prev), _ptr(v), _ptr(w), _ptr(v_next), _ptr(alpha),
+                                  _ptr(beta_prev), _ptr(beta), _ptr(ws), wsb, _stream(stream)), "cvq_lanczos_step")
+
+
+def op_cost(sector: Sector, pool: Pool, op: int):
+    """Algorithmic (fwd_bytes, fwd_flops, adj_bytes, adj_flops) of one pool element's gate."""
+    v = [C.c_double() for _ in range(4)]
+    _check(lib().cvq_op_cost(sector.h, pool.h, int(op), *[C.byref(x) for x in v]), "cvq_op_cost")
+    return tuple(x.value for x in v)
+
+
+class _KStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
+def profile_start(capacity: int = 1 << 20):
+    """Time every later launch of this library with CUDA events on its stream."""
+    L = lib()
+    L.cvq_profile_start.argtypes = [C.c_int]
+    _check(L.cvq_profile_start(int(capacity)), "cvq_profile_start")
+
+
+def profile_stop():
+    """Stop timing; returns {kernel: dict(launches, ms, bytes, flops)}."""
+    L = lib()
+    L.cvq_profile_stop.argtypes = [C.POINTER(_KStat), C.c_int, C.POINTER(C.c_int)]
+    out = (_KStat * 32)()
+    n = C.c_int()
+    _check(L.cvq_profile_stop(out, 32, C.byref(n)), "cvq_profile_stop")
+    return {out[k].name.decode(): dict(launches=int(out[k].launches), ms=out[k].ms, bytes=out[k].bytes,
+                                       flops=out[k].flops) for k in range(n.value)}

@@ -1,0 +1,44 @@
+"""Host-side logic of the product driver (CPU only): BFGS and selection."""
+import numpy as np
+
+from paper_2606_05297_gb300.adapt import BFGS, select
+
+
+def test_bfgs_on_quadratic_and_rosenbrock():
+    """Textbook checks: Rosenbrock from (-1.2, 1) reaches (1, 1); a strictly
+    convex quadratic reaches A^-1 b."""
+    def rosen(x):
+        f = 100 * (x[1] - x[0] ** 2) ** 2 + (1 - x[0]) ** 2
+        g = np.array([-400 * x[0] * (x[1] - x[0] ** 2) - 2 * (1 - x[0]), 200 * (x[1] - x[0] ** 2)])
+        return f, g
+    r = BFGS(rosen).minimize([-1.2, 1.0], gtol=1e-10, max_iter=500)
+    assert np.max(np.abs(r.x - 1.0)) < 1e-8 and r.status == "gtol"
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((6, 6))
+    A = M @ M.T + 6 * np.eye(6)
+    b = rng.standard_normal(6)
+    r = BFGS(lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b)).minimize(np.zeros(6), gtol=1e-12)
+    assert np.max(np.abs(r.x - np.linalg.solve(A, b))) < 1e-10
+
+
+def test_bfgs_matches_oracle_iterates():
+    """The product BFGS and the oracle's follow the same textbook rules, so on
+    a smooth test function they produce the same iterates up to rounding."""
+    from oracle import bfgs as ob
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((5, 5))
+    A = M @ M.T + np.eye(5)
+
+    def f(x):
+        return float(x @ A @ x / 2 + np.sum(np.cos(x))), A @ x - np.sin(x)
+    x0 = rng.standard_normal(5)
+    r1 = BFGS(f).minimize(x0, gtol=1e-10)
+    r2 = ob.minimize(f, x0, gtol=1e-10)
+    assert r1.nfev == r2["nfev"] and r1.nit == r2["nit"]
+    assert np.max(np.abs(r1.x - r2["x"])) < 1e-12
+
+
+def test_selection_tie_rule():
+    assert select([0.1, -2.0, 2.0, 1.0])[0] == 1
+    assert select([0.1, 2.0 * (1 - 5e-10), -2.0])[0] == 1
+    assert select([0.1, 2.0 * (1 - 5e-9), -2.0])[0] == 2
