@@ -293,10 +293,10 @@ def ground_energy(sector: cvq.Sector, max_iter: int = 400, tol: float = 1e-13, s
         v, vp = vp, v
         if (j + 1) % check_every == 0 or j == m - 1:
             a = alpha[: j + 1].cpu().numpy()
-            b = beta[1: j + 1].cpu().numpy()
-            T = np.diag(a) + np.diag(b[:-1], 1) + np.diag(b[:-1], -1) if j > 0 else np.diag(a)
+            b = beta[: j + 2].cpu().numpy()  # b[1..j] couple the j+1 Lanczos vectors, b[j+1] is the next norm
+            T = np.diag(a) + np.diag(b[1:j + 1], 1) + np.diag(b[1:j + 1], -1)
             e = float(np.linalg.eigvalsh(T)[0])
-            if (last is not None and abs(e - last) <= tol * max(1.0, abs(e))) or b[-1] < 1e-14:
+            if (last is not None and abs(e - last) <= tol * max(1.0, abs(e))) or b[j + 1] < 1e-14:
                 return e
             last = e
     return last
