@@ -1,0 +1,66 @@
+"""A fixed, kernel-focused case for profilers: repeated energy-and-gradient
+evaluations of a random ansatz on one workload.
+
+    python -m paper_2606_05297_gb300.profile_case --workload bh12 --depth 40 --reps 3
+
+Workloads: bh12 (Bose-Hubbard L=12, N=12 periodic, 1,352,078 amplitudes),
+bkc8 (Kitaev chain + Kerr L=8, d=8, 8,388,608 amplitudes), bkc10 (L=10, d=6,
+30,233,088 amplitudes).  Each repetition runs one cvq_energy_and_grad call
+(depth forward gates, one H psi, depth reverse steps) and one pool screen.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def make(workload: str):
+    from paper_2606_05297_gb300 import workloads as W
+    if workload == "bh12":
+        m = W.c2_model(3.4)
+        return m, W.bh_allpairs_pool(m.L)
+    if workload == "bkc8":
+        m = W.c3_model(0, K=0.1)
+        return m, W.bkc_kerr_pool(m.L)
+    if workload == "bkc10":
+        m = W.c5_model()
+        return m, W.bkc_kerr_pool(m.L)
+    raise ValueError(workload)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="bh12", choices=["bh12", "bkc8", "bkc10"])
+    ap.add_argument("--depth", type=int, default=40)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args()
+    import torch
+    from paper_2606_05297_gb300 import build, cvq
+    from paper_2606_05297_gb300 import workloads as W
+    build.build()
+    m, pool = make(a.workload)
+    s = cvq.Sector(m)
+    p = cvq.Pool(s, pool)
+    ids, th = W.random_ansatz(len(pool), a.depth, a.seed, scale=0.2)
+    psi0 = torch.from_numpy(W.random_state(s.dim, a.seed + 1)).cuda()
+    ws = s.workspace(p, a.depth)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.reps):
+        E, g = cvq.energy_and_grad(s, p, ids, th, psi0, ws=ws)
+        cvq.screen_pool(s, p, psi0, ws=ws)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    print(f"{a.workload}: dim={s.dim} depth={a.depth} reps={a.reps} E={E.item():.12f} "
+          f"|g|={g.abs().max().item():.6e} {dt / a.reps * 1e3:.2f} ms/rep")
+
+
+if __name__ == "__main__":
+    main()
