@@ -732,6 +732,91 @@ static GateArg gate_arg(const cvq_pool* p, int op, const double2* U) {
   return g;
 }
 
+// The ansatz as launch segments: each block gate alone, and maximal runs of
+// consecutive diagonal gates (they commute) fused into one pass.
+struct Seg {
+  int k0, m;
+  bool diag;
+};
+
+static std::vector<Seg> segments(const cvq_pool* p, const int* ids, int n) {
+  std::vector<Seg> v;
+  int k = 0;
+  while (k < n) {
+    if (!p->types[p->op_type[ids[k]]].diag) {
+      v.push_back({k, 1, false});
+      ++k;
+      continue;
+    }
+    int m = 0, npair = 0;
+    while (k + m < n && m < MAX_RUN) {
+      const TypeDesc& t = p->types[p->op_type[ids[k + m]]];
+      if (!t.diag) break;
+      if (t.diag == 4) {
+        if (npair == MAX_RUN_PAIRS) break;
+        ++npair;
+      }
+      ++m;
+    }
+    v.push_back({k, m, true});
+    k += m;
+  }
+  return v;
+}
+
+// Angles of a diagonal run: per mode and occupation sum_k theta_k f_k(n), and
+// the cross-Kerr terms separately.
+static void diag_run_arg(const cvq_sector* s, const cvq_pool* p, const int* ids, const double* theta, const Seg& g,
+                         DiagRunArg& a) {
+  memset(&a, 0, sizeof a);
+  a.m = g.m;
+  for (int q = 0; q < g.m; ++q) {
+    const int op = ids[g.k0 + q];
+    const TypeDesc& t = p->types[p->op_type[op]];
+    const double th = theta[g.k0 + q];
+    a.diag[q] = t.diag;
+    a.gi[q] = p->op_i[op];
+    a.gj[q] = p->op_j[op];
+    if (t.diag == 4) {
+      a.pi[a.npair] = p->op_i[op];
+      a.pj[a.npair] = p->op_j[op];
+      a.pth[a.npair] = th;
+      ++a.npair;
+    } else {
+      for (int nn = 0; nn < s->S.D; ++nn) {
+        const int f = (t.diag == 1) ? nn * nn : (t.diag == 2) ? nn * (nn - 1) : nn;
+        a.ang[a.gi[q]][nn] += th * (double)f;
+      }
+    }
+  }
+}
+
+// psi_out = U_n ... U_1 psi0 (the first segment reads psi0, the rest work in place).
+static int forward_sweep(const cvq_sector* s, const cvq_pool* p, const int* ids, const double* theta, int n,
+                         const double2* U, const double2* psi0, double2* out, cudaStream_t st) {
+  if (n == 0) {
+    if (out != psi0)
+      CVQ_CUDA(cudaMemcpyAsync(out, psi0, (size_t)s->S.dim * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy");
+    return CVQ_OK;
+  }
+  const double dim = (double)s->S.dim;
+  for (const Seg& g : segments(p, ids, n)) {
+    const double2* src = (g.k0 == 0) ? psi0 : out;
+    if (g.diag) {
+      DiagRunArg a;
+      diag_run_arg(s, p, ids, theta, g, a);
+      ProfScope ps(KK_GATE_DIAG, st, 32.0 * dim, dim * (8.0 + 2.0 * s->S.L + 2.0 * a.npair));
+      CVQ_CUDA(launch_diag_run(s->S, a, src, out, nullptr, nullptr, false, st), "diagonal run");
+    } else {
+      const GateArg ga = gate_arg(p, ids[g.k0], U + (size_t)g.k0 * p->ustride);
+      const OpCost c = op_cost(s, p, ids[g.k0]);
+      ProfScope ps(KK_GATE, st, c.fb, c.ff);
+      CVQ_CUDA(launch_gate(s->S, ga, p->P, src, out, st), "gate");
+    }
+  }
+  return CVQ_OK;
+}
+
 extern "C" int cvq_apply_ansatz(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
                                 const cvq_c128* psi0, cvq_c128* psi_out, void* ws, size_t wsb, void* stream) {
   if (!s || !p || !psi0 || !psi_out) return fail(CVQ_EINVAL, "null argument");
@@ -741,16 +826,7 @@ extern "C" int cvq_apply_ansatz(const cvq_sector* s, const cvq_pool* p, const in
   cudaStream_t st = (cudaStream_t)stream;
   double2* U = (double2*)((char*)ws + l.U);
   if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
-  if (n == 0 && psi_out != psi0)
-    CVQ_CUDA(cudaMemcpyAsync(psi_out, psi0, (size_t)s->S.dim * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy");
-  for (int k = 0; k < n; ++k) {
-    const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
-    const double2* src = (k == 0) ? (const double2*)psi0 : (const double2*)psi_out;
-    const OpCost c = op_cost(s, p, op_ids[k]);
-    ProfScope ps(g.t.diag ? KK_GATE_DIAG : KK_GATE, st, c.fb, c.ff);
-    CVQ_CUDA(launch_gate(s->S, g, p->P, src, (double2*)psi_out, st), "gate");
-  }
-  return CVQ_OK;
+  return forward_sweep(s, p, op_ids, theta, n, U, (const double2*)psi0, (double2*)psi_out, st);
 }
 
 extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta,
@@ -766,13 +842,7 @@ extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const
   double2* U = (double2*)((char*)ws + l.U);
   double* partial = (double*)((char*)ws + l.partial);
   if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
-  if (n == 0) CVQ_CUDA(cudaMemcpyAsync(psi, psi0, (size_t)s->S.dim * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy");
-  for (int k = 0; k < n; ++k) {
-    const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
-    const OpCost c = op_cost(s, p, op_ids[k]);
-    ProfScope ps(g.t.diag ? KK_GATE_DIAG : KK_GATE, st, c.fb, c.ff);
-    CVQ_CUDA(launch_gate(s->S, g, p->P, (k == 0) ? (const double2*)psi0 : psi, psi, st), "gate");
-  }
+  if (int rc = forward_sweep(s, p, op_ids, theta, n, U, (const double2*)psi0, psi, st)) return rc;
   double* pE = partial + (size_t)n * NBLK;
   double hb, hf;
   apply_H_cost(s->S, hb, hf);
@@ -784,11 +854,21 @@ extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const
     ProfScope ps(KK_REDUCE, st, 8.0 * NBLK, NBLK);
     CVQ_CUDA(launch_reduce(pE, 1, NBLK, 1.0, E_dev, st), "reduce E");
   }
-  for (int k = n - 1; k >= 0; --k) {
-    const GateArg g = gate_arg(p, op_ids[k], U + (size_t)k * p->ustride);
-    const OpCost c = op_cost(s, p, op_ids[k]);
-    ProfScope ps(g.t.diag ? KK_ADJ_DIAG : KK_ADJ, st, c.ab, c.af);
-    CVQ_CUDA(launch_gate_adjoint(s->S, g, p->P, psi, lam, partial + (size_t)k * NBLK, st), "adjoint gate");
+  const std::vector<Seg> segs = segments(p, op_ids, n);
+  const double dim = (double)s->S.dim;
+  for (auto it = segs.rbegin(); it != segs.rend(); ++it) {
+    const Seg& g = *it;
+    if (g.diag) {
+      DiagRunArg a;
+      diag_run_arg(s, p, op_ids, theta, g, a);
+      ProfScope ps(KK_ADJ_DIAG, st, 64.0 * dim, dim * (24.0 + 2.0 * s->S.L + 2.0 * g.m));
+      CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, lam, partial + (size_t)g.k0 * NBLK, true, st), "adjoint diagonal run");
+    } else {
+      const GateArg ga = gate_arg(p, op_ids[g.k0], U + (size_t)g.k0 * p->ustride);
+      const OpCost c = op_cost(s, p, op_ids[g.k0]);
+      ProfScope ps(KK_ADJ, st, c.ab, c.af);
+      CVQ_CUDA(launch_gate_adjoint(s->S, ga, p->P, psi, lam, partial + (size_t)g.k0 * NBLK, st), "adjoint gate");
+    }
   }
   {
     ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * n, (double)NBLK * n);

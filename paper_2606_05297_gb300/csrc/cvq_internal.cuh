@@ -162,6 +162,21 @@ cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const d
                         cudaStream_t st);
 cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, double2* psi, double2* lam,
                                 double* partial, cudaStream_t st);
+// A run of consecutive diagonal gates (they commute) applied in one pass:
+// psi[x] *= exp(i phi(x)),  phi = sum_r ang[r][n_r] + sum_p pth[p] n_{pi[p]} n_{pj[p]}.
+// The reverse pass forms every gradient of the run from the same (psi, lambda).
+constexpr int MAX_RUN = 32, MAX_RUN_PAIRS = 8;
+struct DiagRunArg {
+  int m, npair;
+  int diag[MAX_RUN], gi[MAX_RUN], gj[MAX_RUN];   // per gate: f type (1..4) and modes
+  int pi[MAX_RUN_PAIRS], pj[MAX_RUN_PAIRS];
+  double pth[MAX_RUN_PAIRS];
+  double ang[LMAX][DMAX];                        // single-mode angles per occupation
+};
+
+cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const double2* src, double2* dst, double2* lam,
+                            double* partial, bool adjoint, cudaStream_t st);
+
 // Pool indices screened by one launch (passed by value).
 struct SubsetArg {
   int n;

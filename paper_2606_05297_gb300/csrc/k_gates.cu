@@ -420,3 +420,71 @@ cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P,
 }
 
 }  // namespace cvq
+
+namespace cvq {
+
+// ------------------------------------------------------------ diagonal runs
+
+template <int KIND, bool ADJ>
+__global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ SectorDev S, const __grid_constant__ DiagRunArg a,
+                                                       const double2* src, double2* dst, double2* lam, double* partial) {
+  __shared__ int64_t Gs[LMAX][DMAX + 1];
+  __shared__ double ang[LMAX][DMAX];
+  if (KIND == CVQ_BH) load_G(Gs, S);
+  for (int e = threadIdx.x; e < LMAX * DMAX; e += blockDim.x) ang[e / DMAX][e % DMAX] = a.ang[e / DMAX][e % DMAX];
+  __syncthreads();
+  double acc[MAX_RUN];
+#pragma unroll
+  for (int k = 0; k < MAX_RUN; ++k) acc[k] = 0.0;
+  const int L = S.L;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t w = (KIND == CVQ_BKC) ? bkc_unrank(x, S) : bh_unrank(x, L, S.N, Gs);
+    double phi = 0.0;
+    for (int r = 0; r < L; ++r) phi += ang[r][occ_get(w, r)];
+    for (int p = 0; p < a.npair; ++p) phi = fma(a.pth[p], (double)(occ_get(w, a.pi[p]) * occ_get(w, a.pj[p])), phi);
+    double sn, cs;
+    sincos(phi, &sn, &cs);
+    if (!ADJ) {
+      const double2 v = src[x];
+      dst[x] = make_double2(fma(cs, v.x, -sn * v.y), fma(cs, v.y, sn * v.x));
+    } else {
+      const double2 ps = dst[x], la = lam[x];
+      // Re(conj(la) * i f ps) = -f * Im(conj(la) ps)
+      const double c = fma(la.y, ps.x, -la.x * ps.y);
+#pragma unroll
+      for (int k = 0; k < MAX_RUN; ++k) {
+        if (k < a.m) {
+          const int ni = occ_get(w, a.gi[k]);
+          const int dg = a.diag[k];
+          const int f = (dg == 1) ? ni * ni : (dg == 2) ? ni * (ni - 1) : (dg == 3) ? ni : ni * occ_get(w, a.gj[k]);
+          acc[k] = fma((double)f, c, acc[k]);
+        }
+      }
+      dst[x] = make_double2(fma(cs, ps.x, sn * ps.y), fma(cs, ps.y, -sn * ps.x));
+      lam[x] = make_double2(fma(cs, la.x, sn * la.y), fma(cs, la.y, -sn * la.x));
+    }
+  }
+  if (ADJ) {
+#pragma unroll
+    for (int k = 0; k < MAX_RUN; ++k) {
+      if (k < a.m) {
+        const double s = block_sum(acc[k]);
+        if (threadIdx.x == 0) partial[(size_t)k * NBLK + blockIdx.x] = s;
+      }
+    }
+  }
+}
+
+cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const double2* src, double2* dst, double2* lam,
+                            double* partial, bool adjoint, cudaStream_t st) {
+  if (S.kind == CVQ_BH) {
+    if (adjoint) k_diag_run<CVQ_BH, true><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    else k_diag_run<CVQ_BH, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+  } else {
+    if (adjoint) k_diag_run<CVQ_BKC, true><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    else k_diag_run<CVQ_BKC, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cvq

@@ -150,6 +150,32 @@ def test_energy_and_grad(torch_cuda, name):
     assert abs(E0.item() - os_.energy(psi0)[0]) <= E_REL * max(1.0, abs(Eref))
 
 
+@pytest.mark.parametrize("name", ["bh_pbc_L5_N4", "bkck_L4_d6"])
+def test_long_diagonal_runs(torch_cuda, name):
+    """Consecutive diagonal gates are fused into runs of at most 32 gates and
+    8 cross-Kerr terms; longer stretches must split without changing results."""
+    torch = torch_cuda
+    m = SMALL[name]
+    L = m.L
+    ops = [W.Op(t, r) for r in range(L) for t in ("kerr", "nn1", "rot")]
+    ops += [W.Op("xkerr", i, j) for i in range(L) for j in range(i + 1, L)]
+    ops.append(W.Op("hop", 0, 1, 1))
+    cvq, s, p, os_, ops = _setup(torch, m, ops=ops)
+    rng = np.random.default_rng(9)
+    ids = [int(k) for k in rng.integers(0, len(ops) - 1, 75)]
+    ids[40] = len(ops) - 1
+    xk = [k for k, o in enumerate(ops) if o.type == "xkerr"]
+    ids[:12] = [xk[q % len(xk)] for q in range(12)]
+    th = rng.uniform(-0.7, 0.7, len(ids))
+    psi0 = W.random_state(s.dim, 10)
+    E, g = cvq.energy_and_grad(s, p, ids, th, torch.from_numpy(psi0).cuda())
+    Eref, gref = os_.energy_and_grad([ops[i] for i in ids], th, psi0)
+    assert abs(E.item() - Eref) <= E_REL * max(1.0, abs(Eref))
+    assert np.max(np.abs(_np(g) - gref)) < G_ABS
+    out = _np(cvq.apply_ansatz(s, p, ids, th, torch.from_numpy(psi0).cuda()))
+    assert np.max(np.abs(out - os_.apply_ansatz([ops[i] for i in ids], th, psi0))) < PSI_ABS
+
+
 MEDIUM = {
     "bh_pbc_L8_N6": W.bose_hubbard(8, 6, J=1.0, U=-2.5, periodic=True),
     "bh_open_L6_N9": W.bose_hubbard(6, 9, J=0.7, U=1.3, periodic=False),
