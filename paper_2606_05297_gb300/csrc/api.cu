@@ -44,9 +44,11 @@ extern "C" const char* cvq_last_error(void) { return g_err.c_str(); }
 
 // ------------------------------------------------------------------ profiling
 
-enum KernelKind { KK_APPLY_H, KK_SCREEN, KK_GATE, KK_GATE_DIAG, KK_ADJ, KK_ADJ_DIAG, KK_BUILD, KK_REDUCE, KK_LANCZOS, KK_COUNT };
+enum KernelKind {
+  KK_APPLY_H, KK_SCREEN, KK_GATE, KK_GATE_DIAG, KK_ADJ, KK_ADJ_DIAG, KK_BUILD, KK_REDUCE, KK_LANCZOS, KK_CONVERT, KK_COUNT
+};
 static const char* const kKindName[KK_COUNT] = {"apply_H", "screen", "gate_block", "gate_diag", "adjoint_block",
-                                                "adjoint_diag", "build_unitaries", "reduce", "lanczos"};
+                                                "adjoint_diag", "build_unitaries", "reduce", "lanczos", "convert"};
 
 struct ProfRec {
   int kind;
@@ -130,6 +132,9 @@ extern "C" int cvq_profile_stop(cvq_kernel_stat* out, int max_out, int* n_out) {
 
 struct cvq_sector {
   SectorDev S;
+  SectorTabs tabs;               // host copy of the device tables
+  SectorTabs* tabs_dev = nullptr;
+  double hop[LMAX], pair[LMAX];  // bond coefficients (FP64, host side)
   int device;
 };
 
@@ -159,6 +164,12 @@ static int64_t fact_ratio(int lo, int hi) {  // hi! / lo!
   return r;
 }
 
+// Round-to-nearest split of a double into a df pair (hi + lo).
+static float2 split_df(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
 // ------------------------------------------------------------------ sector
 
 extern "C" int cvq_init_sector(const cvq_model* m, cvq_sector** out) {
@@ -168,36 +179,50 @@ extern "C" int cvq_init_sector(const cvq_model* m, cvq_sector** out) {
   if (L < 1 || L > LMAX) return fail(CVQ_EINVAL, "L = %d outside [1, %d]", L, LMAX);
   if (m->periodic && L < 2) return fail(CVQ_EINVAL, "periodic chain needs L >= 2");
   if (m->kind != CVQ_BH && m->kind != CVQ_BKC) return fail(CVQ_EINVAL, "unknown model kind %d", m->kind);
-  SectorDev S;
+  cvq_sector* s = new (std::nothrow) cvq_sector;
+  if (!s) return fail(CVQ_ENOMEM, "host allocation");
+  SectorDev& S = s->S;
+  SectorTabs& T = s->tabs;
   memset(&S, 0, sizeof S);
+  memset(&T, 0, sizeof T);
+  memset(s->hop, 0, sizeof s->hop);
+  memset(s->pair, 0, sizeof s->pair);
   S.kind = m->kind;
   S.L = L;
   S.periodic = m->periodic ? 1 : 0;
   S.nb = m->periodic ? L : L - 1;
+  int rc = CVQ_OK;
   if (m->kind == CVQ_BH) {
-    if (m->N < 0 || m->N + 1 > DMAX) return fail(CVQ_EINVAL, "BH needs 0 <= N <= %d", DMAX - 1);
+    if (m->N < 0 || m->N + 1 > DMAX) rc = fail(CVQ_EINVAL, "BH needs 0 <= N <= %d", DMAX - 1);
     S.N = m->N;
     S.D = m->N + 1;
     if (m->pair)
       for (int b = 0; b < S.nb; ++b)
-        if (m->pair[b] != 0.0) return fail(CVQ_EINVAL, "pairing term breaks the fixed-N sector");
+        if (m->pair[b] != 0.0) rc = fail(CVQ_EINVAL, "pairing term breaks the fixed-N sector");
     S.dim = binom(S.N + L - 1, L - 1);
   } else {
-    if (m->d < 2 || m->d > DMAX || (m->d & 1)) return fail(CVQ_EINVAL, "BKC needs even d in [2, %d]", DMAX);
-    S.D = m->d;
-    S.half = m->d / 2;
-    S.parity = m->parity & 1;
-    int64_t full = 1;
-    for (int r = L - 1; r >= 0; --r) {
-      S.stride[r] = full;
-      if (full > ((int64_t)1 << 42) / m->d) return fail(CVQ_EINVAL, "sector dimension above 2^40");
-      full *= m->d;
+    if (m->d < 2 || m->d > DMAX || (m->d & 1)) {
+      rc = fail(CVQ_EINVAL, "BKC needs even d in [2, %d]", DMAX);
+    } else {
+      S.D = m->d;
+      S.half = m->d / 2;
+      S.parity = m->parity & 1;
+      int64_t full = 1;
+      for (int r = L - 1; r >= 0 && !rc; --r) {
+        S.stride[r] = full;
+        if (full > ((int64_t)1 << 42) / m->d) rc = fail(CVQ_EINVAL, "sector dimension above 2^40");
+        full *= m->d;
+      }
+      S.dim = full / 2;
     }
-    S.dim = full / 2;
   }
-  if (S.dim > ((int64_t)1 << 40)) return fail(CVQ_EINVAL, "sector dimension above 2^40");
+  if (!rc && S.dim > ((int64_t)1 << 40)) rc = fail(CVQ_EINVAL, "sector dimension above 2^40");
+  if (rc) {
+    delete s;
+    return rc;
+  }
   for (int p = 0; p < LMAX; ++p)
-    for (int R = 0; R <= DMAX; ++R) S.G[p][R] = binom(R + p, p);
+    for (int R = 0; R <= DMAX; ++R) T.G[p][R] = binom(R + p, p);
   if (S.kind == CVQ_BH) {
     // two-mode gate work items: classes M = n_i + n_j = 0..N, each holding the
     // compositions of N - M into the other L - 2 modes
@@ -211,23 +236,39 @@ extern "C" int cvq_init_sector(const cvq_model* m, cvq_sector** out) {
     for (int M = S.N + 2; M <= MAX_CLASSES; ++M) S.bh2_off[M] = acc;
   }
   for (int b = 0; b < S.nb; ++b) {
-    S.hop[b] = m->hop ? m->hop[b] : 0.0;
-    S.pair[b] = m->pair ? m->pair[b] : 0.0;
+    s->hop[b] = m->hop ? m->hop[b] : 0.0;
+    s->pair[b] = m->pair ? m->pair[b] : 0.0;
+    T.hop[b] = split_df(s->hop[b]);
+    T.pair[b] = split_df(s->pair[b]);
   }
   for (int r = 0; r < L; ++r) {
-    S.nn1[r] = m->onsite_nn1 ? m->onsite_nn1[r] : 0.0;
-    S.n2[r] = m->onsite_n2 ? m->onsite_n2[r] : 0.0;
-    S.n1[r] = m->onsite_n ? m->onsite_n[r] : 0.0;
+    const double c2 = m->onsite_nn1 ? m->onsite_nn1[r] : 0.0;
+    const double cq = m->onsite_n2 ? m->onsite_n2[r] : 0.0;
+    const double c1 = m->onsite_n ? m->onsite_n[r] : 0.0;
+    for (int n = 0; n < S.D; ++n) T.diagE[r][n] = split_df(c2 * n * (n - 1) + cq * n * n + c1 * n);
   }
-  for (int n = 0; n < DMAX; ++n)
+  for (int n = 0; n < DMAX; ++n) {
     for (int e = -2; e <= 2; ++e) {
       const int t = n + e;
-      S.sqf[n][e + 2] = (t < 0 || t >= S.D) ? 0.0 : std::sqrt((double)fact_ratio(std::min(n, t), std::max(n, t)));
+      T.sq[n][e + 2] = (t < 0 || t >= S.D) ? make_float2(0.f, 0.f)
+                                             : split_df(std::sqrt((double)fact_ratio(std::min(n, t), std::max(n, t))));
     }
-  cvq_sector* s = new (std::nothrow) cvq_sector;
-  if (!s) return fail(CVQ_ENOMEM, "host allocation");
-  s->S = S;
-  CVQ_CUDA(cudaGetDevice(&s->device), "cudaGetDevice");
+    for (int q = 0; q < DMAX; ++q) {
+      T.P[0][n][q] = split_df(std::sqrt((double)(n + 1) * q));
+      T.P[1][n][q] = split_df(std::sqrt((double)n * (q + 1)));
+      T.P[2][n][q] = split_df(std::sqrt((double)(n + 1) * (q + 1)));
+      T.P[3][n][q] = split_df(std::sqrt((double)n * q));
+    }
+  }
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaMalloc(&s->tabs_dev, sizeof(SectorTabs));
+  if (e == cudaSuccess) e = cudaMemcpy(s->tabs_dev, &T, sizeof(SectorTabs), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (s->tabs_dev) cudaFree(s->tabs_dev);
+    delete s;
+    return cuda_fail(e, "sector tables");
+  }
+  S.tab = s->tabs_dev;
   *out = s;
   return CVQ_OK;
 }
@@ -251,7 +292,7 @@ extern "C" int cvq_sector_index(const cvq_sector* s, const int* occ, int64_t* in
     int64_t rk = 0;
     int R = S.N;
     for (int k = 0; k < S.L - 1; ++k) {
-      rk += S.G[S.L - 1 - k][R] - S.G[S.L - 1 - k][R - occ[k]];
+      rk += s->tabs.G[S.L - 1 - k][R] - s->tabs.G[S.L - 1 - k][R - occ[k]];
       R -= occ[k];
     }
     *index = rk;
@@ -264,7 +305,11 @@ extern "C" int cvq_sector_index(const cvq_sector* s, const int* occ, int64_t* in
   return CVQ_OK;
 }
 
-extern "C" void cvq_destroy_sector(cvq_sector* s) { delete s; }
+extern "C" void cvq_destroy_sector(cvq_sector* s) {
+  if (!s) return;
+  if (s->tabs_dev) cudaFree(s->tabs_dev);
+  delete s;
+}
 
 // ------------------------------------------------------------------ pool
 
@@ -315,7 +360,8 @@ static void jacobi_eigen(std::vector<double>& A, int n, std::vector<double>& V, 
 struct PoolBuild {
   std::vector<BlockDesc> blk;
   std::vector<int2> mem;
-  std::vector<double> F, V, lam;
+  std::vector<float2> F;
+  std::vector<double> V, lam;
 };
 
 static std::complex<double> ipow(int p) {
@@ -345,6 +391,7 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
     return fail(CVQ_EINVAL, "op type %d breaks the fixed-N sector", type);
   t.cp_re = cp.real();
   t.cp_im = cp.imag();
+  t.realu = (cp.imag() == 0.0) ? 1 : 0;
   if (t.diag) return CVQ_OK;
   const double acp = std::abs(cp);
   const std::complex<double> om = std::complex<double>(0, 1) * std::conj(cp) / acp;
@@ -387,7 +434,7 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
           double fk = (double)fact_ratio(std::min(a0, a1), std::max(a0, a1));
           if (!t.single) fk *= (double)fact_ratio(std::min(b0, b1), std::max(b0, b1));
           fk = std::sqrt(fk);
-          pb.F.push_back(fk);
+          pb.F.push_back(split_df(fk));
           T[(size_t)k * n + k + 1] = T[(size_t)(k + 1) * n + k] = acp * fk;
         }
         if (n > 1) {
@@ -468,7 +515,7 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
   const size_t o_blk = al(o_ops + (size_t)K * sizeof(GateArg));
   const size_t o_mem = al(o_blk + pb.blk.size() * sizeof(BlockDesc));
   const size_t o_F = al(o_mem + pb.mem.size() * sizeof(int2));
-  const size_t o_V = al(o_F + pb.F.size() * sizeof(double));
+  const size_t o_V = al(o_F + pb.F.size() * sizeof(float2));
   const size_t o_lam = al(o_V + pb.V.size() * sizeof(double));
   const size_t total = al(o_lam + pb.lam.size() * sizeof(double)) + 256;
   cudaError_t e = cudaMalloc(&p->blob, total);
@@ -478,7 +525,7 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
   p->ops_dev = (GateArg*)(base + o_ops);
   p->P.blk = (const BlockDesc*)(base + o_blk);
   p->P.mem = (const int2*)(base + o_mem);
-  p->P.F = (const double*)(base + o_F);
+  p->P.F = (const float2*)(base + o_F);
   p->P.V = (const double*)(base + o_V);
   p->P.lam = (const double*)(base + o_lam);
   std::vector<GateArg> ga(K);
@@ -496,7 +543,7 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
       (e = up(o_ops, ga.data(), (size_t)K * sizeof(GateArg))) != cudaSuccess ||
       (e = up(o_blk, pb.blk.data(), pb.blk.size() * sizeof(BlockDesc))) != cudaSuccess ||
       (e = up(o_mem, pb.mem.data(), pb.mem.size() * sizeof(int2))) != cudaSuccess ||
-      (e = up(o_F, pb.F.data(), pb.F.size() * sizeof(double))) != cudaSuccess ||
+      (e = up(o_F, pb.F.data(), pb.F.size() * sizeof(float2))) != cudaSuccess ||
       (e = up(o_V, pb.V.data(), pb.V.size() * sizeof(double))) != cudaSuccess ||
       (e = up(o_lam, pb.lam.data(), pb.lam.size() * sizeof(double))) != cudaSuccess) {
     cudaFree(p->blob);
@@ -521,21 +568,18 @@ struct Layout {
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// psi and lambda (df states, 16 B per amplitude), per-call block unitaries
+// (n x ustride df complex), reduction partials ((max(n, K) + 1) x NBLK).
 static Layout layout(const cvq_sector* s, const cvq_pool* p, int n_max) {
   Layout l;
-  if (!p) {  // cvq_apply_H alone: one partial sum per CTA
-    l.psi = l.lam = l.U = l.partial = 0;
-    l.total = al256((size_t)NBLK * sizeof(double));
-    return l;
-  }
   const size_t dim = (size_t)s->S.dim;
   const int K = p ? p->K : 0;
   const int ust = p ? p->ustride : PHASE_TABLE;
   const int nred = std::max(std::max(n_max, K), 1) + 1;
   l.psi = 0;
-  l.lam = al256(l.psi + dim * sizeof(double2));
-  l.U = al256(l.lam + dim * sizeof(double2));
-  l.partial = al256(l.U + (size_t)std::max(n_max, 0) * ust * sizeof(double2));
+  l.lam = al256(l.psi + dim * sizeof(cdf));
+  l.U = al256(l.lam + dim * sizeof(cdf));
+  l.partial = al256(l.U + (size_t)std::max(n_max, 0) * ust * sizeof(cdf));
   l.total = al256(l.partial + (size_t)nred * NBLK * sizeof(double));
   return l;
 }
@@ -618,7 +662,8 @@ extern "C" int cvq_op_cost(const cvq_sector* s, const cvq_pool* p, int op, doubl
 // sigma = H psi: every amplitude read and written once; per amplitude the
 // diagonal term (4 flops) and the energy term (4), and 4 flops per
 // off-diagonal matrix element (real coefficient x complex amplitude).
-static void apply_H_cost(const SectorDev& S, double& bytes, double& flops) {
+static void apply_H_cost(const cvq_sector* s, double& bytes, double& flops) {
+  const SectorDev& S = s->S;
   const double dim = (double)S.dim;
   bytes = 32.0 * dim;
   double offd = 0.0;
@@ -626,19 +671,39 @@ static void apply_H_cost(const SectorDev& S, double& bytes, double& flops) {
     // fraction of sector states where a move (+1, -1) (resp. (+1, +1), (-1, -1)) stays in range
     double fh, fp = 0.0;
     if (S.kind == CVQ_BH) {
-      fh = (S.N >= 1) ? (double)S.G[S.L - 1][S.N - 1] / dim : 0.0;  // n_s >= 1: compositions of N - 1
+      fh = (S.N >= 1) ? (double)s->tabs.G[S.L - 1][S.N - 1] / dim : 0.0;  // n_s >= 1: compositions of N - 1
     } else {
       const double q = (double)(S.D - 1) / S.D;
       fh = q * q;
       fp = q * q;
     }
-    if (S.hop[b] != 0.0) offd += 2.0 * fh * dim;
-    if (S.pair[b] != 0.0) offd += 2.0 * fp * dim;
+    if (s->hop[b] != 0.0) offd += 2.0 * fh * dim;
+    if (s->pair[b] != 0.0) offd += 2.0 * fp * dim;
   }
   flops = 8.0 * dim + 4.0 * offd;
 }
 
 // ------------------------------------------------------------------ calls
+
+static int to_df(const cvq_sector* s, const cvq_c128* src, cdf* dst, cudaStream_t st) {
+  ProfScope ps(KK_CONVERT, st, 32.0 * (double)s->S.dim, 0.0);
+  CVQ_CUDA(launch_to_df(s->S.dim, (const double2*)src, dst, st), "to df");
+  return CVQ_OK;
+}
+
+static int from_df(const cvq_sector* s, const cdf* src, cvq_c128* dst, cudaStream_t st) {
+  ProfScope ps(KK_CONVERT, st, 32.0 * (double)s->S.dim, 0.0);
+  CVQ_CUDA(launch_from_df(s->S.dim, src, (double2*)dst, st), "from df");
+  return CVQ_OK;
+}
+
+static int run_apply_H(const cvq_sector* s, const cdf* psi, cdf* sigma, double* partial, cudaStream_t st) {
+  double hb, hf;
+  apply_H_cost(s, hb, hf);
+  ProfScope ps(KK_APPLY_H, st, hb, hf);
+  CVQ_CUDA(launch_apply_H(s->S, psi, sigma, partial, st), "apply_H");
+  return CVQ_OK;
+}
 
 extern "C" int cvq_apply_H(const cvq_sector* s, const cvq_c128* psi, cvq_c128* sigma, double* energy_dev, void* ws,
                            size_t wsb, void* stream) {
@@ -647,13 +712,12 @@ extern "C" int cvq_apply_H(const cvq_sector* s, const cvq_c128* psi, cvq_c128* s
   Layout l;
   if (int rc = check_ws(s, nullptr, 0, ws, wsb, l)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  cdf* vpsi = (cdf*)((char*)ws + l.psi);
+  cdf* vsig = (cdf*)((char*)ws + l.lam);
   double* partial = (double*)((char*)ws + l.partial);
-  double hb, hf;
-  apply_H_cost(s->S, hb, hf);
-  {
-    ProfScope ps(KK_APPLY_H, st, hb, hf);
-    CVQ_CUDA(launch_apply_H(s->S, (const double2*)psi, (double2*)sigma, energy_dev ? partial : nullptr, st), "apply_H");
-  }
+  if (int rc = to_df(s, psi, vpsi, st)) return rc;
+  if (int rc = run_apply_H(s, vpsi, vsig, energy_dev ? partial : nullptr, st)) return rc;
+  if (int rc = from_df(s, vsig, sigma, st)) return rc;
   if (energy_dev) {
     ProfScope ps(KK_REDUCE, st, 8.0 * NBLK, NBLK);
     CVQ_CUDA(launch_reduce(partial, 1, NBLK, 1.0, energy_dev, st), "reduce");
@@ -680,21 +744,18 @@ extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq
   Layout l;
   if (int rc = check_ws(s, p, 0, ws, wsb, l)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  double2* sigma = (double2*)((char*)ws + l.lam);
+  cdf* vpsi = (cdf*)((char*)ws + l.psi);
+  cdf* vsig = (cdf*)((char*)ws + l.lam);
   double* partial = (double*)((char*)ws + l.partial);
-  double hb, hf;
-  apply_H_cost(s->S, hb, hf);
-  {
-    ProfScope ps(KK_APPLY_H, st, hb, hf);
-    CVQ_CUDA(launch_apply_H(s->S, (const double2*)psi, sigma, nullptr, st), "apply_H");
-  }
+  if (int rc = to_df(s, psi, vpsi, st)) return rc;
+  if (int rc = run_apply_H(s, vpsi, vsig, nullptr, st)) return rc;
   {
     // per screened element and amplitude: the generator row (2 complex MACs, or 1
     // for a diagonal generator) and its overlap with sigma (1 complex MAC)
     double fl = 0.0;
     for (int k = 0; k < sub.n; ++k) fl += (double)s->S.dim * (p->types[p->op_type[sub.idx[k]]].diag ? 16.0 : 24.0);
     ProfScope ps(KK_SCREEN, st, 32.0 * (double)s->S.dim, fl);
-    CVQ_CUDA(launch_screen(s->S, p->ops_dev, sub, (const double2*)psi, sigma, partial, st), "screen");
+    CVQ_CUDA(launch_screen(s->S, p->ops_dev, sub, vpsi, vsig, partial, st), "screen");
   }
   {
     ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * sub.n, (double)NBLK * sub.n);
@@ -703,8 +764,8 @@ extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq
   return CVQ_OK;
 }
 
-static int prepare_gates(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
-                         double2* U, cudaStream_t st) {
+static int prepare_gates(const cvq_sector*, const cvq_pool* p, const int* op_ids, const double* theta, int n, cdf* U,
+                         cudaStream_t st) {
   if (n < 0 || n > MAX_GATES) return fail(CVQ_EINVAL, "ansatz length %d outside [0, %d]", n, MAX_GATES);
   if (n > 0 && (!op_ids || !theta)) return fail(CVQ_EINVAL, "null op_ids / theta");
   BuildArgs a;
@@ -714,16 +775,14 @@ static int prepare_gates(const cvq_sector* s, const cvq_pool* p, const int* op_i
     if (op_ids[k] < 0 || op_ids[k] >= p->K) return fail(CVQ_EINVAL, "op_ids[%d] = %d outside the pool", k, op_ids[k]);
     if (!std::isfinite(theta[k])) return fail(CVQ_EINVAL, "theta[%d] is not finite", k);
     a.type_of[k] = p->op_type[op_ids[k]];
-    a.op_i[k] = p->op_i[op_ids[k]];
-    a.op_j[k] = p->op_j[op_ids[k]];
     a.theta[k] = theta[k];
   }
   ProfScope ps(KK_BUILD, st, 0.0, 0.0);
-  CVQ_CUDA(launch_build_gates(a, p->types.data(), p->types_dev, p->P, U, st), "build gates");
+  CVQ_CUDA(launch_build_gates(a, p->types_dev, p->P, U, st), "build gates");
   return CVQ_OK;
 }
 
-static GateArg gate_arg(const cvq_pool* p, int op, const double2* U) {
+static GateArg gate_arg(const cvq_pool* p, int op, const cdf* U) {
   GateArg g;
   g.i = p->op_i[op];
   g.j = p->op_j[op];
@@ -764,12 +823,21 @@ static std::vector<Seg> segments(const cvq_pool* p, const int* ids, int n) {
   return v;
 }
 
-// Angles of a diagonal run: per mode and occupation sum_k theta_k f_k(n), and
-// the cross-Kerr terms separately.
+static float4 cdf_of(double re, double im) {
+  const float2 a = split_df(re), b = split_df(im);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Phase tables of a diagonal run: per mode and occupation
+// exp(i sum_k theta_k f_k(n)) over the run's single-mode gates on that mode,
+// and exp(i theta_p n_i n_j) for each cross-Kerr gate.  FP64 on the host.
 static void diag_run_arg(const cvq_sector* s, const cvq_pool* p, const int* ids, const double* theta, const Seg& g,
                          DiagRunArg& a) {
   memset(&a, 0, sizeof a);
   a.m = g.m;
+  double ang[LMAX][DMAX];
+  memset(ang, 0, sizeof ang);
+  const int D = s->S.D;
   for (int q = 0; q < g.m; ++q) {
     const int op = ids[g.k0 + q];
     const TypeDesc& t = p->types[p->op_type[op]];
@@ -778,40 +846,37 @@ static void diag_run_arg(const cvq_sector* s, const cvq_pool* p, const int* ids,
     a.gi[q] = p->op_i[op];
     a.gj[q] = p->op_j[op];
     if (t.diag == 4) {
-      a.pi[a.npair] = p->op_i[op];
-      a.pj[a.npair] = p->op_j[op];
-      a.pth[a.npair] = th;
-      ++a.npair;
+      const int pp = a.npair++;
+      a.pi[pp] = p->op_i[op];
+      a.pj[pp] = p->op_j[op];
+      for (int u = 0; u < D; ++u)
+        for (int v = 0; v < D; ++v) a.TP[pp][u * D + v] = cdf_of(std::cos(th * u * v), std::sin(th * u * v));
     } else {
-      for (int nn = 0; nn < s->S.D; ++nn) {
+      for (int nn = 0; nn < D; ++nn) {
         const int f = (t.diag == 1) ? nn * nn : (t.diag == 2) ? nn * (nn - 1) : nn;
-        a.ang[a.gi[q]][nn] += th * (double)f;
+        ang[a.gi[q]][nn] += th * (double)f;
       }
     }
   }
+  for (int r = 0; r < LMAX; ++r)
+    for (int nn = 0; nn < DMAX; ++nn) a.T[r][nn] = cdf_of(std::cos(ang[r][nn]), std::sin(ang[r][nn]));
 }
 
-// psi_out = U_n ... U_1 psi0 (the first segment reads psi0, the rest work in place).
+// U_n ... U_1 applied in place to the df state psi.
 static int forward_sweep(const cvq_sector* s, const cvq_pool* p, const int* ids, const double* theta, int n,
-                         const double2* U, const double2* psi0, double2* out, cudaStream_t st) {
-  if (n == 0) {
-    if (out != psi0)
-      CVQ_CUDA(cudaMemcpyAsync(out, psi0, (size_t)s->S.dim * sizeof(double2), cudaMemcpyDeviceToDevice, st), "copy");
-    return CVQ_OK;
-  }
+                         const cdf* U, cdf* psi, cudaStream_t st) {
   const double dim = (double)s->S.dim;
   for (const Seg& g : segments(p, ids, n)) {
-    const double2* src = (g.k0 == 0) ? psi0 : out;
     if (g.diag) {
       DiagRunArg a;
       diag_run_arg(s, p, ids, theta, g, a);
-      ProfScope ps(KK_GATE_DIAG, st, 32.0 * dim, dim * (8.0 + 2.0 * s->S.L + 2.0 * a.npair));
-      CVQ_CUDA(launch_diag_run(s->S, a, src, out, nullptr, nullptr, false, st), "diagonal run");
+      ProfScope ps(KK_GATE_DIAG, st, 32.0 * dim, dim * (8.0 * s->S.L + 8.0 * a.npair));
+      CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, nullptr, nullptr, false, st), "diagonal run");
     } else {
       const GateArg ga = gate_arg(p, ids[g.k0], U + (size_t)g.k0 * p->ustride);
       const OpCost c = op_cost(s, p, ids[g.k0]);
       ProfScope ps(KK_GATE, st, c.fb, c.ff);
-      CVQ_CUDA(launch_gate(s->S, ga, p->P, src, out, st), "gate");
+      CVQ_CUDA(launch_gate(s->S, ga, p->P, psi, psi, st), "gate");
     }
   }
   return CVQ_OK;
@@ -824,9 +889,12 @@ extern "C" int cvq_apply_ansatz(const cvq_sector* s, const cvq_pool* p, const in
   Layout l;
   if (int rc = check_ws(s, p, n, ws, wsb, l)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  double2* U = (double2*)((char*)ws + l.U);
+  cdf* psi = (cdf*)((char*)ws + l.psi);
+  cdf* U = (cdf*)((char*)ws + l.U);
   if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
-  return forward_sweep(s, p, op_ids, theta, n, U, (const double2*)psi0, (double2*)psi_out, st);
+  if (int rc = to_df(s, psi0, psi, st)) return rc;
+  if (int rc = forward_sweep(s, p, op_ids, theta, n, U, psi, st)) return rc;
+  return from_df(s, psi, psi_out, st);
 }
 
 extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta,
@@ -837,19 +905,15 @@ extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const
   Layout l;
   if (int rc = check_ws(s, p, n, ws, wsb, l)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  double2* psi = (double2*)((char*)ws + l.psi);
-  double2* lam = (double2*)((char*)ws + l.lam);
-  double2* U = (double2*)((char*)ws + l.U);
+  cdf* psi = (cdf*)((char*)ws + l.psi);
+  cdf* lam = (cdf*)((char*)ws + l.lam);
+  cdf* U = (cdf*)((char*)ws + l.U);
   double* partial = (double*)((char*)ws + l.partial);
   if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
-  if (int rc = forward_sweep(s, p, op_ids, theta, n, U, (const double2*)psi0, psi, st)) return rc;
+  if (int rc = to_df(s, psi0, psi, st)) return rc;
+  if (int rc = forward_sweep(s, p, op_ids, theta, n, U, psi, st)) return rc;
   double* pE = partial + (size_t)n * NBLK;
-  double hb, hf;
-  apply_H_cost(s->S, hb, hf);
-  {
-    ProfScope ps(KK_APPLY_H, st, hb, hf);
-    CVQ_CUDA(launch_apply_H(s->S, psi, lam, pE, st), "apply_H");
-  }
+  if (int rc = run_apply_H(s, psi, lam, pE, st)) return rc;
   {
     ProfScope ps(KK_REDUCE, st, 8.0 * NBLK, NBLK);
     CVQ_CUDA(launch_reduce(pE, 1, NBLK, 1.0, E_dev, st), "reduce E");
@@ -861,7 +925,7 @@ extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const
     if (g.diag) {
       DiagRunArg a;
       diag_run_arg(s, p, op_ids, theta, g, a);
-      ProfScope ps(KK_ADJ_DIAG, st, 64.0 * dim, dim * (24.0 + 2.0 * s->S.L + 2.0 * g.m));
+      ProfScope ps(KK_ADJ_DIAG, st, 64.0 * dim, dim * (8.0 * s->S.L + 8.0 * a.npair + 24.0 + 4.0 * g.m));
       CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, lam, partial + (size_t)g.k0 * NBLK, true, st), "adjoint diagonal run");
     } else {
       const GateArg ga = gate_arg(p, op_ids[g.k0], U + (size_t)g.k0 * p->ustride);

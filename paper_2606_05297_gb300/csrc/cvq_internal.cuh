@@ -3,13 +3,16 @@
 //
 // Occupation tuples (n_0..n_{L-1}) travel through the kernels packed four bits
 // per mode in one uint64 (L <= 16, D <= 16), so that no kernel needs a
-// dynamically indexed per-thread array.
+// dynamically indexed per-thread array.  States inside a call are stored as
+// double-float complex numbers (df.cuh); the C ABI's complex128 buffers are
+// converted at the entry and exit of a call.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "cvq.h"
+#include "df.cuh"
 
 namespace cvq {
 
@@ -20,42 +23,80 @@ constexpr int MAX_CLASSES = 17;   // BH: total pair occupation M = 0..N (N <= 15
 constexpr int MAX_GATES = 512;    // ansatz length per call and pool size
 constexpr int NTHREADS = 256;
 constexpr int NBLK = 152 * 4;     // fixed grid: 4 CTAs per SM on the 152 SMs of a GB300
-constexpr int PHASE_TABLE = 256;  // diagonal gates: e^{i theta f}, f = 0..(D-1)^2 <= 225
+constexpr int PHASE_TABLE = 256;  // complex entries reserved per gate (>= D^2)
 
 // ------------------------------------------------------------------ sector
+
+// Tables too large for kernel parameters; device-resident, staged into shared
+// memory by the kernels that index them per thread.
+struct SectorTabs {
+  int64_t G[LMAX][DMAX + 1];        // BH: G[p][R] = C(R + p, p)
+  float2 diagE[LMAX][DMAX];         // df: nn1 n(n-1) + n2 n^2 + n1 n, per site and occupation
+  float2 P[4][DMAX][DMAX];          // df: sqrt factors of the H moves (+1,-1) (-1,+1) (+1,+1) (-1,-1) on (n_r, n_s)
+  float2 sq[DMAX][5];               // df: sqrt(max(n,n+e)!/min(n,n+e)!) for e = -2..2
+  float2 hop[LMAX], pair[LMAX];     // df bond coefficients
+};
 
 struct SectorDev {
   int kind, L, N, D, parity, periodic, nb, half;   // half = d / 2 (BKC)
   int64_t dim;
   int64_t stride[LMAX];                 // BKC: d^(L-1-r)
-  int64_t G[LMAX][DMAX + 1];            // BH: G[p][R] = C(R + p, p)
   int64_t bh2_off[MAX_CLASSES + 1];     // BH two-mode gate work items of class M start at bh2_off[M]
-  double hop[LMAX], pair[LMAX], nn1[LMAX], n2[LMAX], n1[LMAX];
-  double sqf[DMAX][5];                  // sqrt(max(n,n+e)! / min(n,n+e)!) for e = -2..2
+  const SectorTabs* tab;                // device copy
 };
 
-__device__ __forceinline__ int occ_get(uint64_t w, int r) { return (int)((w >> (4 * r)) & 15ull); }
-__device__ __forceinline__ uint64_t occ_shift(uint64_t w, int r, int delta) {
+__host__ __device__ __forceinline__ int occ_get(uint64_t w, int r) { return (int)((w >> (4 * r)) & 15ull); }
+__host__ __device__ __forceinline__ uint64_t occ_shift(uint64_t w, int r, int delta) {
   return w + (uint64_t)((int64_t)delta * (int64_t)(1ull << (4 * r)));
 }
 
 // Lexicographic rank of a composition of N (combinatorial number system):
 // rank = sum_{k < L-1} G[L-1-k][R_k] - G[L-1-k][R_{k+1}],  R_k = n_k + ... + n_{L-1}.
-__device__ __forceinline__ int64_t bh_rank(uint64_t w, int L, int N, const int64_t (*G)[DMAX + 1]) {
+__host__ __device__ __forceinline__ int64_t bh_rank(uint64_t w, int L, int N, const int64_t (*G)[DMAX + 1]) {
   int64_t r = 0;
   int R = N;
   for (int k = 0; k < L - 1; ++k) {
-    int n = occ_get(w, k);
+    const int n = occ_get(w, k);
     r += G[L - 1 - k][R] - G[L - 1 - k][R - n];
     R -= n;
   }
   return r;
 }
 
+// Suffix sums R_k = n_k + ... + n_{L-1}, packed like the occupations.
+__host__ __device__ __forceinline__ uint64_t bh_suffix(uint64_t w, int L) {
+  uint64_t s = 0;
+  int R = 0;
+  for (int k = L - 1; k >= 0; --k) {
+    R += occ_get(w, k);
+    s |= (uint64_t)R << (4 * k);
+  }
+  return s;
+}
+
+// Rank change when w is moved by (+dr on mode r, -dr on mode s): only the terms
+// of positions min(r,s)..max(r,s) change; wR holds the suffix sums of w.
+__host__ __device__ __forceinline__ int64_t bh_move_delta(uint64_t w, uint64_t wR, int r, int s, int dr, int L,
+                                                 const int64_t (*G)[DMAX + 1]) {
+  int lo = r, hi = s, dlo = dr;
+  if (s < r) { lo = s; hi = r; dlo = -dr; }
+  int64_t d = 0;
+  const int top = (hi < L - 1) ? hi : L - 2;
+  for (int k = lo; k <= top; ++k) {
+    const int p = L - 1 - k;
+    const int R = occ_get(wR, k), n = occ_get(w, k);
+    const int Rn = (k == lo) ? R : R - dlo;
+    const int nn = (k == lo) ? n + dlo : (k == hi) ? n - dlo : n;
+    d += (G[p][Rn] - G[p][Rn - nn]) - (G[p][R] - G[p][R - n]);
+  }
+  return d;
+}
+
 // Inverse of bh_rank for a chain of Lc modes holding Nc bosons; the tuple is
-// written to consecutive nibbles starting at nibble 0.
-__device__ __forceinline__ uint64_t bh_unrank(int64_t x, int Lc, int Nc, const int64_t (*G)[DMAX + 1]) {
-  uint64_t w = 0;
+// written to consecutive nibbles starting at nibble 0, its suffix sums to *wR.
+__host__ __device__ __forceinline__ uint64_t bh_unrank(int64_t x, int Lc, int Nc, const int64_t (*G)[DMAX + 1],
+                                              uint64_t* wR = nullptr) {
+  uint64_t w = 0, sR = 0;
   int R = Nc;
   for (int k = 0; k < Lc - 1; ++k) {
     const int p = Lc - 1 - k;
@@ -64,14 +105,19 @@ __device__ __forceinline__ uint64_t bh_unrank(int64_t x, int Lc, int Nc, const i
     while (n < R && x >= base - G[p][R - n - 1]) ++n;
     x -= base - G[p][R - n];
     w |= (uint64_t)n << (4 * k);
+    sR |= (uint64_t)R << (4 * k);
     R -= n;
   }
-  if (Lc > 0) w |= (uint64_t)R << (4 * (Lc - 1));
+  if (Lc > 0) {
+    w |= (uint64_t)R << (4 * (Lc - 1));
+    sR |= (uint64_t)R << (4 * (Lc - 1));
+  }
+  if (wR) *wR = sR;
   return w;
 }
 
 // Kitaev chain, even d: index = floor(f / 2), f = sum_r n_r d^(L-1-r).
-__device__ __forceinline__ uint64_t bkc_unrank(int64_t x, const SectorDev& S) {
+__host__ __device__ __forceinline__ uint64_t bkc_unrank(int64_t x, const SectorDev& S) {
   const int L = S.L, d = S.D;
   int64_t hi = x / S.half;
   const int lo = (int)(x - hi * S.half);
@@ -87,17 +133,6 @@ __device__ __forceinline__ uint64_t bkc_unrank(int64_t x, const SectorDev& S) {
   const int nl = 2 * lo + ((S.parity - par) & 1);
   w |= (uint64_t)nl << (4 * (L - 1));
   return w;
-}
-
-__device__ __forceinline__ int64_t bkc_full(uint64_t w, const SectorDev& S) {
-  int64_t f = 0;
-  for (int r = 0; r < S.L; ++r) f += (int64_t)occ_get(w, r) * S.stride[r];
-  return f;
-}
-
-// Copy the binomial table into shared memory (BH kernels).
-__device__ __forceinline__ void load_G(int64_t (*Gs)[DMAX + 1], const SectorDev& S) {
-  for (int t = threadIdx.x; t < LMAX * (DMAX + 1); t += blockDim.x) Gs[t / (DMAX + 1)][t % (DMAX + 1)] = S.G[t / (DMAX + 1)][t % (DMAX + 1)];
 }
 
 // ------------------------------------------------------------------ pool
@@ -121,6 +156,7 @@ struct TypeDesc {
   int di, dj;                      // the generator's move (a, b) -> (a + di, b + dj)
   int nclass;
   int nblocks, nu, bmax;           // blocks, complex entries of one gate's U, largest block
+  int realu;                       // c_plus real: A and exp(theta A) are real
   int class_off[MAX_CLASSES + 1];  // blocks of class c are blk[class_off[c] .. class_off[c+1])
   double cp_re, cp_im;             // c_plus
   double om_re, om_im;             // omega
@@ -130,8 +166,8 @@ struct TypeDesc {
 struct PoolDev {
   const BlockDesc* blk;
   const int2* mem;
-  const double* F;
-  const double* V;
+  const float2* F;     // df tridiagonal factors
+  const double* V;     // complex W V, row-major per block
   const double* lam;
 };
 
@@ -139,7 +175,7 @@ struct PoolDev {
 struct GateArg {
   int i, j;              // modes
   TypeDesc t;            // structure of the generator
-  const double2* U;      // this gate's block unitaries (t.nu entries) or phase table (diagonal)
+  const cdf* U;          // this gate's block unitaries (t.nu entries, df complex)
 };
 
 // Per-call list of gates for the unitary build kernel (passed by value).
@@ -147,35 +183,22 @@ struct BuildArgs {
   int n;
   int ustride;           // complex entries reserved per gate
   int type_of[MAX_GATES];
-  int op_i[MAX_GATES], op_j[MAX_GATES];
   double theta[MAX_GATES];
 };
 
-// ------------------------------------------------------------- launchers
-// All launchers enqueue on `stream` and return the launch status.
-
-cudaError_t launch_apply_H(const SectorDev& S, const double2* psi, double2* sigma, double* partial, cudaStream_t st);
-cudaError_t launch_reduce(const double* partial, int nred, int nblk, double scale, double* out, cudaStream_t st);
-cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_host, const TypeDesc* types_dev, PoolDev P,
-                               double2* U, cudaStream_t st);
-cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const double2* src, double2* dst,
-                        cudaStream_t st);
-cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, double2* psi, double2* lam,
-                                double* partial, cudaStream_t st);
 // A run of consecutive diagonal gates (they commute) applied in one pass:
-// psi[x] *= exp(i phi(x)),  phi = sum_r ang[r][n_r] + sum_p pth[p] n_{pi[p]} n_{pj[p]}.
-// The reverse pass forms every gradient of the run from the same (psi, lambda).
-constexpr int MAX_RUN = 32, MAX_RUN_PAIRS = 8;
+// psi[x] *= prod_r T[r][n_r] * prod_p TP[p][n_{pi[p]} D + n_{pj[p]}], the
+// tables holding exp(i sum_k theta_k f_k(n)) per mode and exp(i theta_p n_i n_j)
+// per cross-Kerr gate (built on the host in FP64, passed by value).  The
+// reverse pass forms every gradient of the run from the same (psi, lambda).
+constexpr int MAX_RUN = 32, MAX_RUN_PAIRS = 4;
 struct DiagRunArg {
   int m, npair;
   int diag[MAX_RUN], gi[MAX_RUN], gj[MAX_RUN];   // per gate: f type (1..4) and modes
   int pi[MAX_RUN_PAIRS], pj[MAX_RUN_PAIRS];
-  double pth[MAX_RUN_PAIRS];
-  double ang[LMAX][DMAX];                        // single-mode angles per occupation
+  cdf T[LMAX][DMAX];
+  cdf TP[MAX_RUN_PAIRS][DMAX * DMAX];
 };
-
-cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const double2* src, double2* dst, double2* lam,
-                            double* partial, bool adjoint, cudaStream_t st);
 
 // Pool indices screened by one launch (passed by value).
 struct SubsetArg {
@@ -183,13 +206,50 @@ struct SubsetArg {
   int idx[MAX_GATES];
 };
 
-cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const double2* psi,
-                          const double2* sigma, double* partial, cudaStream_t st);
-// Lanczos: w <- w - alpha v - beta_prev v_prev with partial sums of ||w||^2,
-// then v_next = w / ||w||.
+// ------------------------------------------------------------- launchers
+// All launchers enqueue on `stream` and return the launch status.  States
+// (cdf*) are df complex; the C ABI's complex128 buffers go through
+// launch_to_df / launch_from_df.
+
+cudaError_t launch_to_df(int64_t dim, const double2* src, cdf* dst, cudaStream_t st);
+cudaError_t launch_from_df(int64_t dim, const cdf* src, double2* dst, cudaStream_t st);
+cudaError_t launch_apply_H(const SectorDev& S, const cdf* psi, cdf* sigma, double* partial, cudaStream_t st);
+cudaError_t launch_reduce(const double* partial, int nred, int nblk, double scale, double* out, cudaStream_t st);
+cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_dev, PoolDev P, cdf* U, cudaStream_t st);
+cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* src, cdf* dst, cudaStream_t st);
+cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial,
+                                cudaStream_t st);
+cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
+                            double* partial, bool adjoint, cudaStream_t st);
+cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const cdf* psi,
+                          const cdf* sigma, double* partial, cudaStream_t st);
+// Lanczos on complex128 vectors: w <- w - alpha v - beta_prev v_prev with
+// partial sums of ||w||^2, then v_next = w / ||w||.
 cudaError_t launch_lanczos_update(const SectorDev& S, const double2* v_prev, const double2* v, double2* w,
                                   const double* alpha, const double* beta_prev, double* partial, cudaStream_t st);
 cudaError_t launch_lanczos_scale(const SectorDev& S, const double2* w, double2* v_next, const double* partial,
                                  double* beta, cudaStream_t st);
+
+// ------------------------------------------------------------- shared device helpers
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (warp == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;  // valid in thread 0
+}
+
+__device__ __forceinline__ void load_G(int64_t (*Gs)[DMAX + 1], const SectorDev& S) {
+  const int64_t* src = &S.tab->G[0][0];
+  int64_t* dst = &Gs[0][0];
+  for (int t = threadIdx.x; t < LMAX * (DMAX + 1); t += blockDim.x) dst[t] = src[t];
+}
 
 }  // namespace cvq

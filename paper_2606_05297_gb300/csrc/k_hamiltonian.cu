@@ -1,122 +1,123 @@
 // k_hamiltonian.cu -- matrix-free sector matvec sigma = H psi with the fused
 // energy reduction Re <psi|sigma> (Sec. IV.A/B), the Eq. (grad) pool screen
-// g_k = 2 Re <H psi|A_k psi>, and the fixed-order final reduction.
+// g_k = 2 Re <H psi|A_k psi>, the fixed-order final reduction, and the
+// Lanczos vector update used for E0.
 //
 // Every kernel runs a fixed grid (NBLK CTAs x NTHREADS threads) in grid-stride
 // loops and leaves one partial sum per CTA, so the reductions are
-// deterministic for a given sector.
+// deterministic for a given sector.  The matvec and the screen work on df
+// states (df.cuh); the Lanczos update works on the caller's complex128 vectors.
 #include "cvq_internal.cuh"
 
 namespace cvq {
 
-__device__ __forceinline__ double block_sum_h(double v) {
-  __shared__ double red[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
-  if (warp == 0)
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-struct SectorTables {
-  int64_t G[LMAX][DMAX + 1];
-  double sqf[DMAX][5];
-};
-
-__device__ __forceinline__ void load_tables(SectorTables& T, const SectorDev& S) {
-  for (int e = threadIdx.x; e < LMAX * (DMAX + 1); e += blockDim.x) T.G[e / (DMAX + 1)][e % (DMAX + 1)] = S.G[e / (DMAX + 1)][e % (DMAX + 1)];
-  for (int e = threadIdx.x; e < DMAX * 5; e += blockDim.x) T.sqf[e / 5][e % 5] = S.sqf[e / 5][e % 5];
-  __syncthreads();
-}
-
 template <int KIND>
-__device__ __forceinline__ uint64_t unrank(int64_t x, const SectorDev& S, const SectorTables& T) {
-  return (KIND == CVQ_BKC) ? bkc_unrank(x, S) : bh_unrank(x, S.L, S.N, T.G);
+__device__ __forceinline__ uint64_t unrank(int64_t x, const SectorDev& S, const int64_t (*G)[DMAX + 1], uint64_t* wR) {
+  if (KIND == CVQ_BKC) return bkc_unrank(x, S);
+  return bh_unrank(x, S.L, S.N, G, wR);
 }
 
-// Index of the tuple w moved by (dr on mode r, ds on mode s); f is the BKC
-// full index of w.
+// Index of the tuple w (index x) moved by (dr on mode r, ds on mode s);
+// f is the BKC full index, wR the BH suffix sums.
 template <int KIND>
-__device__ __forceinline__ int64_t moved_index(uint64_t w, int64_t f, int r, int dr, int s, int ds, const SectorDev& S,
-                                               const SectorTables& T) {
+__device__ __forceinline__ int64_t moved_index(int64_t x, uint64_t w, uint64_t wR, int64_t f, int r, int dr, int s,
+                                               int ds, const SectorDev& S, const int64_t (*G)[DMAX + 1]) {
   if (KIND == CVQ_BKC) {
     int64_t g = f + (int64_t)dr * S.stride[r];
     if (s >= 0) g += (int64_t)ds * S.stride[s];
     return g >> 1;
   } else {
-    uint64_t v = occ_shift(w, r, dr);
-    if (s >= 0) v = occ_shift(v, s, ds);
-    return bh_rank(v, S.L, S.N, T.G);
+    return x + bh_move_delta(w, wR, r, s, dr, S.L, G);  // number-conserving moves: ds = -dr
   }
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(NTHREADS) k_apply_H(const __grid_constant__ SectorDev S, const double2* __restrict__ psi,
-                                                      double2* __restrict__ sigma, double* __restrict__ partial) {
-  __shared__ SectorTables T;
-  load_tables(T, S);
-  const int L = S.L, Dm1 = S.D - 1;
-  double eacc = 0.0;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t w = unrank<KIND>(x, S, T);
-    const int64_t f = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
-    const double2 p = psi[x];
-    double dg = 0.0;
-    for (int r = 0; r < L; ++r) {
-      const double n = (double)occ_get(w, r);
-      dg += S.nn1[r] * n * (n - 1.0) + S.n2[r] * n * n + S.n1[r] * n;
+__global__ void __launch_bounds__(NTHREADS) k_apply_H(const __grid_constant__ SectorDev S, const cdf* __restrict__ psi,
+                                                      cdf* __restrict__ sigma, double* __restrict__ partial) {
+  __shared__ int64_t Gs[LMAX][DMAX + 1];
+  __shared__ float2 dE[LMAX][DMAX];
+  __shared__ float2 P[4][DMAX][DMAX];
+  __shared__ float2 hop[LMAX], pair[LMAX];
+  if (KIND == CVQ_BH) load_G(Gs, S);
+  {
+    const float2* a = &S.tab->diagE[0][0];
+    for (int e = threadIdx.x; e < LMAX * DMAX; e += blockDim.x) (&dE[0][0])[e] = a[e];
+    const float2* b = &S.tab->P[0][0][0];
+    for (int e = threadIdx.x; e < 4 * DMAX * DMAX; e += blockDim.x) (&P[0][0][0])[e] = b[e];
+    for (int e = threadIdx.x; e < LMAX; e += blockDim.x) {
+      hop[e] = S.tab->hop[e];
+      pair[e] = S.tab->pair[e];
     }
-    double ar = dg * p.x, ai = dg * p.y;
+  }
+  __syncthreads();
+  const int L = S.L, Dm1 = S.D - 1;
+  dfacc eacc;
+  acc_zero(eacc);
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t wR = 0;
+    const uint64_t w = unrank<KIND>(x, S, Gs, &wR);
+    const int64_t f = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
+    const cdf p = psi[x];
+    dfacc dg;
+    acc_zero(dg);
+    for (int r = 0; r < L; ++r) {
+      const float2 e = dE[r][occ_get(w, r)];
+      acc_add(dg, df_make(e.x, e.y));
+    }
+    const df d = acc_get(dg);
+    dfacc ar, ai;
+    acc_zero(ar);
+    acc_zero(ai);
+    acc_mac(ar, d, re_of(p));
+    acc_mac(ai, d, im_of(p));
     for (int b = 0; b < S.nb; ++b) {
       const int r = b, s = (b + 1 == L) ? 0 : b + 1;
       const int nr = occ_get(w, r), ns = occ_get(w, s);
-      const double h = S.hop[b];
-      if (h != 0.0) {
-        if (ns >= 1 && nr < Dm1) {   // <x| a_r^dag a_s |x - e_r + e_s>... neighbour x + e_r - e_s
-          const double c = h * T.sqf[nr][3] * T.sqf[ns][1];
-          const double2 q = psi[moved_index<KIND>(w, f, r, +1, s, -1, S, T)];
-          ar = fma(c, q.x, ar);
-          ai = fma(c, q.y, ai);
+      const df h = df_make(hop[b].x, hop[b].y);
+      if (h.h != 0.f) {
+        if (ns >= 1 && nr < Dm1) {  // neighbour x + e_r - e_s: sqrt((n_r + 1) n_s)
+          const df c = df_mul(h, df_make(P[0][nr][ns].x, P[0][nr][ns].y));
+          const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, +1, s, -1, S, Gs)];
+          acc_mac(ar, c, re_of(q));
+          acc_mac(ai, c, im_of(q));
         }
-        if (nr >= 1 && ns < Dm1) {   // neighbour x - e_r + e_s
-          const double c = h * T.sqf[nr][1] * T.sqf[ns][3];
-          const double2 q = psi[moved_index<KIND>(w, f, r, -1, s, +1, S, T)];
-          ar = fma(c, q.x, ar);
-          ai = fma(c, q.y, ai);
+        if (nr >= 1 && ns < Dm1) {  // neighbour x - e_r + e_s: sqrt(n_r (n_s + 1))
+          const df c = df_mul(h, df_make(P[1][nr][ns].x, P[1][nr][ns].y));
+          const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, -1, s, +1, S, Gs)];
+          acc_mac(ar, c, re_of(q));
+          acc_mac(ai, c, im_of(q));
         }
       }
-      const double pc = S.pair[b];
-      if (KIND == CVQ_BKC && pc != 0.0) {
-        if (nr < Dm1 && ns < Dm1) {  // neighbour x + e_r + e_s (a_r a_s lowers it to x)
-          const double c = pc * T.sqf[nr][3] * T.sqf[ns][3];
-          const double2 q = psi[moved_index<KIND>(w, f, r, +1, s, +1, S, T)];
-          ar = fma(c, q.x, ar);
-          ai = fma(c, q.y, ai);
-        }
-        if (nr >= 1 && ns >= 1) {    // neighbour x - e_r - e_s
-          const double c = pc * T.sqf[nr][1] * T.sqf[ns][1];
-          const double2 q = psi[moved_index<KIND>(w, f, r, -1, s, -1, S, T)];
-          ar = fma(c, q.x, ar);
-          ai = fma(c, q.y, ai);
+      if (KIND == CVQ_BKC) {
+        const df pc = df_make(pair[b].x, pair[b].y);
+        if (pc.h != 0.f) {
+          if (nr < Dm1 && ns < Dm1) {  // neighbour x + e_r + e_s (a_r a_s lowers it to x)
+            const df c = df_mul(pc, df_make(P[2][nr][ns].x, P[2][nr][ns].y));
+            const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, +1, s, +1, S, Gs)];
+            acc_mac(ar, c, re_of(q));
+            acc_mac(ai, c, im_of(q));
+          }
+          if (nr >= 1 && ns >= 1) {  // neighbour x - e_r - e_s
+            const df c = df_mul(pc, df_make(P[3][nr][ns].x, P[3][nr][ns].y));
+            const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, -1, s, -1, S, Gs)];
+            acc_mac(ar, c, re_of(q));
+            acc_mac(ai, c, im_of(q));
+          }
         }
       }
     }
-    sigma[x] = make_double2(ar, ai);
-    eacc = fma(p.x, ar, eacc);
-    eacc = fma(p.y, ai, eacc);
+    const df sr = acc_get(ar), si = acc_get(ai);
+    sigma[x] = make_cdf(sr, si);
+    acc_mac(eacc, re_of(p), sr);
+    acc_mac(eacc, im_of(p), si);
   }
   if (partial) {
-    const double s = block_sum_h(eacc);
+    const double s = block_sum(acc_to_double(eacc));
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
   }
 }
 
-cudaError_t launch_apply_H(const SectorDev& S, const double2* psi, double2* sigma, double* partial, cudaStream_t st) {
+cudaError_t launch_apply_H(const SectorDev& S, const cdf* psi, cdf* sigma, double* partial, cudaStream_t st) {
   if (S.kind == CVQ_BH) k_apply_H<CVQ_BH><<<NBLK, NTHREADS, 0, st>>>(S, psi, sigma, partial);
   else k_apply_H<CVQ_BKC><<<NBLK, NTHREADS, 0, st>>>(S, psi, sigma, partial);
   return cudaGetLastError();
@@ -124,63 +125,89 @@ cudaError_t launch_apply_H(const SectorDev& S, const double2* psi, double2* sigm
 
 // ------------------------------------------------------------ screen
 
+// c times a df, exact when c is 0, +-1 or a power of two (all c_plus here)
+__device__ __forceinline__ df df_scale(df a, float c) { return df_make(a.h * c, a.l * c); }
+
 // Row rule of a pool generator: (A psi)[x] = cp F(x, x+m) psi[x+m]
 // - conj(cp) F(x, x-m) psi[x-m] for the move m = (di on mode i, dj on mode j),
-// or i f(n(x)) psi[x] for a diagonal generator.
+// or i f(n(x)) psi[x] for a diagonal generator.  Per element the kernel
+// accumulates Re sum_x conj(sigma[x]) (A psi)[x].
 template <int KIND>
 __global__ void __launch_bounds__(NTHREADS) k_screen(const __grid_constant__ SectorDev S, const GateArg* __restrict__ pool,
-                                                     const __grid_constant__ SubsetArg sub, const double2* __restrict__ psi,
-                                                     const double2* __restrict__ sigma, double* __restrict__ partial) {
-  __shared__ SectorTables T;
-  load_tables(T, S);
+                                                     const __grid_constant__ SubsetArg sub, const cdf* __restrict__ psi,
+                                                     const cdf* __restrict__ sigma, double* __restrict__ partial) {
+  __shared__ int64_t Gs[LMAX][DMAX + 1];
+  __shared__ float2 sq[DMAX][5];
+  if (KIND == CVQ_BH) load_G(Gs, S);
+  for (int e = threadIdx.x; e < DMAX * 5; e += blockDim.x) (&sq[0][0])[e] = (&S.tab->sq[0][0])[e];
+  __syncthreads();
   const int L = S.L, Dm1 = S.D - 1;
   for (int k = 0; k < sub.n; ++k) {
     const GateArg& op = pool[sub.idx[k]];
     const int i = op.i, j = op.t.single ? -1 : op.j;
     const int di = op.t.di, dj = op.t.dj, dg = op.t.diag;
-    const double2 cp = make_double2(op.t.cp_re, op.t.cp_im);
-    double acc = 0.0;
+    const float cpr = (float)op.t.cp_re, cpi = (float)op.t.cp_im;
+    dfacc acc;
+    acc_zero(acc);
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x) {
-      const uint64_t w = unrank<KIND>(x, S, T);
-      const double2 s = sigma[x];
+      uint64_t wR = 0;
+      const uint64_t w = unrank<KIND>(x, S, Gs, &wR);
+      const cdf s = sigma[x];
       const int ni = occ_get(w, i);
       if (dg) {
-        int f;
-        if (dg == 1) f = ni * ni;
-        else if (dg == 2) f = ni * (ni - 1);
-        else if (dg == 3) f = ni;
-        else f = ni * occ_get(w, j);
-        const double2 p = psi[x];
-        // Re(conj(s) * i f p)
-        acc = fma((double)f, fma(s.y, p.x, -s.x * p.y), acc);
+        const int f = (dg == 1) ? ni * ni : (dg == 2) ? ni * (ni - 1) : (dg == 3) ? ni : ni * occ_get(w, j);
+        if (f) {
+          const cdf p = psi[x];
+          dfacc c;  // Re(conj(s) * i f p) = f (s.im p.re - s.re p.im)
+          acc_zero(c);
+          acc_mac(c, im_of(s), re_of(p));
+          acc_mac(c, df_neg(re_of(s)), im_of(p));
+          acc_macf(acc, acc_get(c), (float)f);
+        }
         continue;
       }
       const int nj = (j >= 0) ? occ_get(w, j) : 0;
       const int64_t f = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
-      double tr = 0.0, ti = 0.0;
       if (ni + di >= 0 && ni + di <= Dm1 && (j < 0 || (nj + dj >= 0 && nj + dj <= Dm1))) {
-        const double F = T.sqf[ni][di + 2] * (j >= 0 ? T.sqf[nj][dj + 2] : 1.0);
-        const double2 q = psi[moved_index<KIND>(w, f, i, di, j, dj, S, T)];
-        tr += F * (cp.x * q.x - cp.y * q.y);
-        ti += F * (cp.x * q.y + cp.y * q.x);
+        df F = df_make(sq[ni][di + 2].x, sq[ni][di + 2].y);
+        if (j >= 0) F = df_mul(F, df_make(sq[nj][dj + 2].x, sq[nj][dj + 2].y));
+        const cdf q = psi[moved_index<KIND>(x, w, wR, f, i, di, j, dj, S, Gs)];
+        dfacc z;  // Re(cp conj(s) q)
+        acc_zero(z);
+        if (cpr != 0.f) {
+          acc_mac(z, df_scale(re_of(s), cpr), re_of(q));
+          acc_mac(z, df_scale(im_of(s), cpr), im_of(q));
+        }
+        if (cpi != 0.f) {
+          acc_mac(z, df_scale(re_of(s), -cpi), im_of(q));
+          acc_mac(z, df_scale(im_of(s), cpi), re_of(q));
+        }
+        acc_mac(acc, F, acc_get(z));
       }
       if (ni - di >= 0 && ni - di <= Dm1 && (j < 0 || (nj - dj >= 0 && nj - dj <= Dm1))) {
-        const double F = T.sqf[ni][2 - di] * (j >= 0 ? T.sqf[nj][2 - dj] : 1.0);
-        const double2 q = psi[moved_index<KIND>(w, f, i, -di, j, -dj, S, T)];
-        // -conj(cp) * q
-        tr -= F * (cp.x * q.x + cp.y * q.y);
-        ti -= F * (cp.x * q.y - cp.y * q.x);
+        df F = df_make(sq[ni][2 - di].x, sq[ni][2 - di].y);
+        if (j >= 0) F = df_mul(F, df_make(sq[nj][2 - dj].x, sq[nj][2 - dj].y));
+        const cdf q = psi[moved_index<KIND>(x, w, wR, f, i, -di, j, -dj, S, Gs)];
+        dfacc z;  // Re(-conj(cp) conj(s) q)
+        acc_zero(z);
+        if (cpr != 0.f) {
+          acc_mac(z, df_scale(re_of(s), -cpr), re_of(q));
+          acc_mac(z, df_scale(im_of(s), -cpr), im_of(q));
+        }
+        if (cpi != 0.f) {
+          acc_mac(z, df_scale(re_of(s), -cpi), im_of(q));
+          acc_mac(z, df_scale(im_of(s), cpi), re_of(q));
+        }
+        acc_mac(acc, F, acc_get(z));
       }
-      acc = fma(s.x, tr, acc);
-      acc = fma(s.y, ti, acc);
     }
-    const double r = block_sum_h(acc);
+    const double r = block_sum(acc_to_double(acc));
     if (threadIdx.x == 0) partial[(size_t)k * NBLK + blockIdx.x] = r;
   }
 }
 
-cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const double2* psi,
-                          const double2* sigma, double* partial, cudaStream_t st) {
+cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const cdf* psi,
+                          const cdf* sigma, double* partial, cudaStream_t st) {
   if (sub.n <= 0) return cudaSuccess;
   if (S.kind == CVQ_BH) k_screen<CVQ_BH><<<NBLK, NTHREADS, 0, st>>>(S, pool_ops, sub, psi, sigma, partial);
   else k_screen<CVQ_BKC><<<NBLK, NTHREADS, 0, st>>>(S, pool_ops, sub, psi, sigma, partial);
@@ -193,7 +220,7 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblk, double sc
   const int r = blockIdx.x;
   double v = 0.0;
   for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += partial[(size_t)r * nblk + b];
-  v = block_sum_h(v);
+  v = block_sum(v);
   if (threadIdx.x == 0) out[r] = scale * v;
 }
 
@@ -202,10 +229,6 @@ cudaError_t launch_reduce(const double* partial, int nred, int nblk, double scal
   k_reduce<<<nred, NTHREADS, 0, st>>>(partial, nblk, scale, out);
   return cudaGetLastError();
 }
-
-}  // namespace cvq
-
-namespace cvq {
 
 // ------------------------------------------------------------ Lanczos
 
@@ -230,7 +253,7 @@ __global__ void __launch_bounds__(NTHREADS) k_lanczos_update(int64_t dim, const 
     acc = fma(t.x, t.x, acc);
     acc = fma(t.y, t.y, acc);
   }
-  const double s = block_sum_h(acc);
+  const double s = block_sum(acc);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
@@ -241,7 +264,7 @@ __global__ void __launch_bounds__(NTHREADS) k_lanczos_scale(int64_t dim, const d
   __shared__ double nb;
   double v = 0.0;
   for (int b = threadIdx.x; b < NBLK; b += blockDim.x) v += partial[b];
-  v = block_sum_h(v);
+  v = block_sum(v);
   if (threadIdx.x == 0) {
     nb = sqrt(v);
     if (blockIdx.x == 0) beta[0] = nb;
