@@ -39,8 +39,11 @@ def test_adapt_trace_matches_oracle_on_bh_L4(gpu):
     ref_recs = [t for t in ref["trace"] if t["kind"] == "adapt"]
     assert abs(A.trace[0]["E"] - ref["trace"][0]["E"]) < 1e-10 * abs(ref["trace"][0]["E"])
     assert [r["op"] for r in recs] == [t["op"] for t in ref_recs]
+    # Both BFGS runs stop at an L-inf gradient tolerance (1e-9 for the warm
+    # start, min(1e-6, 1e-5 |g|) per ADAPT step), so their parameters agree only
+    # to that scale and the next screen's max |g| to ~1e-7.
     for r, t in zip(recs, ref_recs):
-        assert abs(r["gmax"] - t["gmax"]) < 1e-8
+        assert abs(r["gmax"] - t["gmax"]) < 1e-6
         assert abs(r["E"] - t["E"]) < 1e-10 * abs(t["E"])
 
 
