@@ -1,7 +1,7 @@
 """A fixed, kernel-focused case for profilers: repeated energy-and-gradient
 evaluations of a random ansatz on one workload.
 
-    python -m paper_2606_05297_gb300.profile_case --workload bh12 --depth 40 --reps 3
+    python -m paper_2606_05297_gb300.profile_case --workload bh12 --depth 40 --reps 3 [--warm 5]
 
 Workloads: bh12 (Bose-Hubbard L=12, N=12 periodic, 1,352,078 amplitudes),
 bkc8 (Kitaev chain + Kerr L=8, d=8, 8,388,608 amplitudes), bkc10 (L=10, d=6,
@@ -40,6 +40,7 @@ def main():
     ap.add_argument("--depth", type=int, default=40)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--warm", type=int, default=0, help="unprofiled repetitions before cudaProfilerStart")
     a = ap.parse_args()
     import torch
     from paper_2606_05297_gb300 import build, cvq
@@ -51,13 +52,18 @@ def main():
     ids, th = W.random_ansatz(len(pool), a.depth, a.seed, scale=0.2)
     psi0 = torch.from_numpy(W.random_state(s.dim, a.seed + 1)).cuda()
     ws = s.workspace(p, a.depth)
+    for _ in range(a.warm):
+        cvq.energy_and_grad(s, p, ids, th, psi0, ws=ws)
+        cvq.screen_pool(s, p, psi0, ws=ws)
     torch.cuda.synchronize()
+    torch.cuda.profiler.start()  # profiled range, for profilers started with --profile-from-start off
     t0 = time.perf_counter()
     for _ in range(a.reps):
         E, g = cvq.energy_and_grad(s, p, ids, th, psi0, ws=ws)
         cvq.screen_pool(s, p, psi0, ws=ws)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
     print(f"{a.workload}: dim={s.dim} depth={a.depth} reps={a.reps} E={E.item():.12f} "
           f"|g|={g.abs().max().item():.6e} {dt / a.reps * 1e3:.2f} ms/rep")
 
