@@ -174,6 +174,26 @@ int cvq_lanczos_step(const cvq_sector *s, const cvq_c128 *v_prev, const cvq_c128
 int cvq_op_cost(const cvq_sector *s, const cvq_pool *p, int op, double *fwd_bytes, double *fwd_flops,
                 double *adj_bytes, double *adj_flops);
 
+/* Pool screen for callers that cannot allocate device memory.  The paper has
+ * no counterpart to this call: it exists for code that must not call
+ * cudaMalloc when it screens -- code running while a stream is captured into a
+ * CUDA graph, real-time loops that cannot afford the device-wide
+ * synchronisation an allocation implies, and hosts whose own allocator owns
+ * all device memory.  It computes the same values as cvq_screen_pool for the
+ * n_subset pool indices in the host array subset (1 <= n_subset <= 64,
+ * EINVAL otherwise) and writes them to grad_dev[0..n_subset), with no
+ * workspace: psi is read as complex128, each row of H psi is formed on the
+ * fly, and the per-block partial sums live in a fixed device array of 64 x 608
+ * doubles (311,296 bytes) that every GPU which loads the library keeps until
+ * the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress), so make it before any stream
+ * capture.  All calls on a device share the array: calls that overlap on the
+ * GPU (different streams without ordering) race and give wrong results.
+ * Each call overwrites the array rows it reads, so no clearing is needed.
+ * Errors: EINVAL, ECUDA. */
+int cvq_screen_subset_noalloc(const cvq_sector *s, const cvq_pool *p, const cvq_c128 *psi, const int *subset,
+                              int n_subset, double *grad_dev, void *stream);
+
 /* Live per-kernel timing.  cvq_profile_start(capacity) makes every later
  * launch by this library (any thread, any stream) record a CUDA event pair on
  * its stream, up to `capacity` launches; cvq_profile_stop waits for those

@@ -964,3 +964,22 @@ extern "C" int cvq_lanczos_step(const cvq_sector* s, const cvq_c128* v_prev, con
   }
   return CVQ_OK;
 }
+
+// ------------------------------------------------------------------ internal accessors
+// Used by translation units that add entry points of their own (k_noalloc.cu)
+// without reaching into these structures directly.
+
+namespace cvq {
+
+const SectorDev* internal_sector(const cvq_sector* s) { return s ? &s->S : nullptr; }
+
+const GateArg* internal_pool_ops(const cvq_pool* p, const cvq_sector** sec, int* K) {
+  if (!p) return nullptr;
+  if (sec) *sec = p->sec;
+  if (K) *K = p->K;
+  return p->ops_dev;
+}
+
+int internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
+}  // namespace cvq

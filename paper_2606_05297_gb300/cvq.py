@@ -64,6 +64,7 @@ def lib():
         L.cvq_energy_and_grad.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int, vp, vp, vp, vp,
                                           sz, vp]
         L.cvq_lanczos_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.cvq_screen_subset_noalloc.argtypes = [vp, vp, vp, C.POINTER(C.c_int), C.c_int, vp, vp]
         dp = C.POINTER(C.c_double)
         L.cvq_op_cost.argtypes = [vp, vp, C.c_int, dp, dp, dp, dp]
         _lib = L
@@ -260,3 +261,18 @@ def profile_stop():
     _check(L.cvq_profile_stop(out, 32, C.byref(n)), "cvq_profile_stop")
     return {out[k].name.decode(): dict(launches=int(out[k].launches), ms=out[k].ms, bytes=out[k].bytes,
                                        flops=out[k].flops) for k in range(n.value)}
+
+
+def screen_subset_noalloc(sector: Sector, pool: Pool, psi, subset, out=None, stream=None):
+    """Eq. (grad) gradients of at most 64 pool elements without any workspace
+    or device allocation inside the call (cvq_screen_subset_noalloc): for
+    callers that cannot allocate at that point, e.g. inside a stream capture.
+    `out` must be preallocated by such callers; calls overlapping on the GPU race."""
+    import torch
+    n = len(subset)
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.float64, device=psi.device)
+    sa = (C.c_int * max(n, 1))(*[int(k) for k in subset])
+    _check(lib().cvq_screen_subset_noalloc(sector.h, pool.h, _ptr(psi), sa, n, _ptr(out), _stream(stream)),
+           "cvq_screen_subset_noalloc")
+    return out[:n]
