@@ -358,6 +358,7 @@ static void jacobi_eigen(std::vector<double>& A, int n, std::vector<double>& V, 
 }
 
 struct PoolBuild {
+  std::vector<int4> chunks;
   std::vector<BlockDesc> blk;
   std::vector<int2> mem;
   std::vector<float2> F;
@@ -465,6 +466,32 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
   t.class_off[t.nclass] = (int)pb.blk.size() - t.blk_base;
   t.nblocks = t.class_off[t.nclass];
   t.nu = nu;
+  t.nmem = nmem;
+  t.nf = nf;
+  if (S.kind == CVQ_BH) {
+    // Equal-work schedule: orbits of class M cost about 24 + sum_blocks (b^2 + 4 b)
+    // units; classes are cut into chunks of about total / (4 NBLK) units so that
+    // every CTA gets a similar share and each chunk has a single block structure.
+    std::vector<double> w(t.nclass, 24.0);
+    double total = 0.0;
+    for (int M = 0; M < t.nclass; ++M) {
+      for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
+        const int b = pb.blk[t.blk_base + bi].size;
+        w[M] += (double)b * b + 4.0 * b;
+      }
+      total += w[M] * (double)(S.bh2_off[M + 1] - S.bh2_off[M]);
+    }
+    const double target = std::max(total / (4.0 * NBLK), 1.0);
+    t.chunk_base = (int)pb.chunks.size();
+    for (int M = 0; M < t.nclass; ++M) {
+      const int64_t cnt = S.bh2_off[M + 1] - S.bh2_off[M];
+      if (cnt > INT32_MAX) return fail(CVQ_EINVAL, "too many orbits in one class");
+      const int64_t per = std::max<int64_t>(64, (int64_t)std::ceil(target / w[M]));
+      for (int64_t u0 = 0; u0 < cnt; u0 += per)
+        pb.chunks.push_back(make_int4(M, (int)u0, (int)std::min(cnt, u0 + per), 0));
+    }
+    t.nchunks = (int)pb.chunks.size() - t.chunk_base;
+  }
   return CVQ_OK;
 }
 
@@ -510,7 +537,8 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
   // device tables: types, ops, blocks, members, F, V, lam in one allocation
   const size_t nT = p->types.size();
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t o_types = 0;
+  const size_t o_chunks = 0;
+  const size_t o_types = al(o_chunks + pb.chunks.size() * sizeof(int4));
   const size_t o_ops = al(o_types + nT * sizeof(TypeDesc));
   const size_t o_blk = al(o_ops + (size_t)K * sizeof(GateArg));
   const size_t o_mem = al(o_blk + pb.blk.size() * sizeof(BlockDesc));
@@ -521,6 +549,7 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
   cudaError_t e = cudaMalloc(&p->blob, total);
   if (e != cudaSuccess) { delete p; return fail(CVQ_ENOMEM, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e)); }
   char* base = (char*)p->blob;
+  p->P.chunks = (const int4*)(base + o_chunks);
   p->types_dev = (TypeDesc*)(base + o_types);
   p->ops_dev = (GateArg*)(base + o_ops);
   p->P.blk = (const BlockDesc*)(base + o_blk);
@@ -539,7 +568,8 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
   auto up = [&](size_t off, const void* src, size_t n) -> cudaError_t {
     return n ? cudaMemcpy(base + off, src, n, cudaMemcpyHostToDevice) : cudaSuccess;
   };
-  if ((e = up(o_types, p->types.data(), nT * sizeof(TypeDesc))) != cudaSuccess ||
+  if ((e = up(o_chunks, pb.chunks.data(), pb.chunks.size() * sizeof(int4))) != cudaSuccess ||
+      (e = up(o_types, p->types.data(), nT * sizeof(TypeDesc))) != cudaSuccess ||
       (e = up(o_ops, ga.data(), (size_t)K * sizeof(GateArg))) != cudaSuccess ||
       (e = up(o_blk, pb.blk.data(), pb.blk.size() * sizeof(BlockDesc))) != cudaSuccess ||
       (e = up(o_mem, pb.mem.data(), pb.mem.size() * sizeof(int2))) != cudaSuccess ||

@@ -157,6 +157,8 @@ struct TypeDesc {
   int nclass;
   int nblocks, nu, bmax;           // blocks, complex entries of one gate's U, largest block
   int realu;                       // c_plus real: A and exp(theta A) are real
+  int nmem, nf;                    // members and generator factors of all blocks
+  int chunk_base, nchunks;         // BH: equal-work schedule of (class, orbit range) chunks
   int class_off[MAX_CLASSES + 1];  // blocks of class c are blk[class_off[c] .. class_off[c+1])
   double cp_re, cp_im;             // c_plus
   double om_re, om_im;             // omega
@@ -164,6 +166,7 @@ struct TypeDesc {
 };
 
 struct PoolDev {
+  const int4* chunks;  // BH: (class M, first orbit, end orbit, 0)
   const BlockDesc* blk;
   const int2* mem;
   const float2* F;     // df tridiagonal factors
@@ -177,6 +180,19 @@ struct GateArg {
   TypeDesc t;            // structure of the generator
   const cdf* U;          // this gate's block unitaries (t.nu entries, df complex)
 };
+
+// Shared memory of a block-gate kernel: the gate tables (block unitaries,
+// block descriptors, members, generator factors) followed by each thread's
+// staging columns for bmax amplitudes and bmax sector indices.
+__host__ __device__ __forceinline__ size_t gate_tables_bytes(const TypeDesc& t) {
+  const size_t b = (size_t)t.nu * sizeof(cdf) + (size_t)t.nblocks * sizeof(BlockDesc) +
+                   (size_t)(DMAX * DMAX) * sizeof(int2) + (size_t)(DMAX * DMAX) * sizeof(float2);
+  return (b + 15) & ~(size_t)15;
+}
+
+__host__ __device__ __forceinline__ size_t gate_smem_bytes(const TypeDesc& t) {
+  return gate_tables_bytes(t) + (size_t)NTHREADS * t.bmax * (sizeof(cdf) + sizeof(int64_t));
+}
 
 // Per-call list of gates for the unitary build kernel (passed by value).
 struct BuildArgs {

@@ -1,13 +1,20 @@
 // k_gate_impl.cuh -- block gate kernels (forward and reverse), instantiated
 // once per (sector kind, direction) in k_gate_{bh,bkc}_{fwd,adj}.cu so that
 // the translation units compile in parallel.
+//
+// A thread owns one orbit of the gate (the occupations of every other mode
+// fixed) and walks its blocks.  Each block's amplitudes are staged in the
+// thread's own column of shared memory (entry l of thread t at l*NTHREADS+t,
+// so a warp's accesses never share a bank) together with their sector
+// indices; the block unitary is read from shared memory as a broadcast.  The
+// block size is a runtime loop bound, so the code does not grow with it.
 #pragma once
 
 #include "cvq_internal.cuh"
 
 namespace cvq {
 
-// ------------------------------------------------------------ block math
+// ------------------------------------------------------------ member indices
 
 struct BkcIdx {  // member (a, b) of an orbit with base f0: (f0 + a s_i + b s_j) >> 1
   int64_t f0, si, sj;
@@ -24,9 +31,10 @@ struct BhIdx {   // member (a, M - a): rank of member (0, M) plus the rank chang
   }
 };
 
-// out += u * v (complex df), accumulating the real and imaginary parts
+// ------------------------------------------------------------ complex df helpers
+
 template <bool REALU>
-__device__ __forceinline__ void cmac(dfacc& ar, dfacc& ai, cdf u, cdf v) {
+__device__ __forceinline__ void cmac(dfacc& ar, dfacc& ai, cdf u, cdf v) {  // += u v
   acc_mac(ar, re_of(u), re_of(v));
   acc_mac(ai, re_of(u), im_of(v));
   if (!REALU) {
@@ -35,9 +43,8 @@ __device__ __forceinline__ void cmac(dfacc& ar, dfacc& ai, cdf u, cdf v) {
   }
 }
 
-// out += conj(u) * v
 template <bool REALU>
-__device__ __forceinline__ void cmac_conj(dfacc& ar, dfacc& ai, cdf u, cdf v) {
+__device__ __forceinline__ void cmac_conj(dfacc& ar, dfacc& ai, cdf u, cdf v) {  // += conj(u) v
   acc_mac(ar, re_of(u), re_of(v));
   acc_mac(ai, re_of(u), im_of(v));
   if (!REALU) {
@@ -45,107 +52,6 @@ __device__ __forceinline__ void cmac_conj(dfacc& ar, dfacc& ai, cdf u, cdf v) {
     acc_mac(ai, df_neg(im_of(u)), re_of(v));
   }
 }
-
-template <int B, bool REALU, class IDX>
-__device__ __forceinline__ void block_fwd(const cdf* __restrict__ Ub, const int2* __restrict__ mem, const IDX& idx,
-                                          const cdf* src, cdf* dst) {
-  int64_t x[B];
-  cdf in[B];
-#pragma unroll
-  for (int l = 0; l < B; ++l) {
-    x[l] = idx(mem[l]);
-    in[l] = src[x[l]];
-  }
-#pragma unroll
-  for (int k = 0; k < B; ++k) {
-    dfacc ar, ai;
-    acc_zero(ar);
-    acc_zero(ai);
-#pragma unroll
-    for (int l = 0; l < B; ++l) cmac<REALU>(ar, ai, Ub[k * B + l], in[l]);
-    dst[x[k]] = make_cdf(acc_get(ar), acc_get(ai));
-  }
-}
-
-// Reverse step for one block.  With the tridiagonal generator
-// A[k][k+1] = cp F_k, A[k+1][k] = -conj(cp) F_k the gradient term
-// Re sum_k conj(lam_k) (A psi)_k equals sum_k F_k Re(cp z_k),
-// z_k = conj(lam_k) psi_{k+1} - lam_{k+1} conj(psi_k).  Then psi <- U^dag psi,
-// lam <- U^dag lam.
-template <int B, bool REALU, class IDX>
-__device__ __forceinline__ void block_adj(const cdf* __restrict__ Ub, const int2* __restrict__ mem,
-                                          const float2* __restrict__ F, float cpr, float cpi, const IDX& idx, cdf* psi,
-                                          cdf* lam, dfacc& gacc) {
-  int64_t x[B];
-  cdf ps[B], la[B];
-#pragma unroll
-  for (int l = 0; l < B; ++l) {
-    x[l] = idx(mem[l]);
-    ps[l] = psi[x[l]];
-    la[l] = lam[x[l]];
-  }
-#pragma unroll
-  for (int k = 0; k + 1 < B; ++k) {
-    const df Fk = df_make(F[k].x, F[k].y);
-    if (cpr != 0.f) {  // Re z_k
-      dfacc z;
-      acc_zero(z);
-      acc_mac(z, re_of(la[k]), re_of(ps[k + 1]));
-      acc_mac(z, im_of(la[k]), im_of(ps[k + 1]));
-      acc_mac(z, df_neg(re_of(la[k + 1])), re_of(ps[k]));
-      acc_mac(z, df_neg(im_of(la[k + 1])), im_of(ps[k]));
-      const df zr = acc_get(z);
-      acc_mac(gacc, Fk, df_make(zr.h * cpr, zr.l * cpr));
-    }
-    if (cpi != 0.f) {  // -Im z_k
-      dfacc z;
-      acc_zero(z);
-      acc_mac(z, re_of(la[k]), im_of(ps[k + 1]));
-      acc_mac(z, df_neg(im_of(la[k])), re_of(ps[k + 1]));
-      acc_mac(z, df_neg(im_of(la[k + 1])), re_of(ps[k]));
-      acc_mac(z, re_of(la[k + 1]), im_of(ps[k]));
-      const df zi = acc_get(z);
-      acc_mac(gacc, Fk, df_make(-zi.h * cpi, -zi.l * cpi));
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < B; ++k) {
-    dfacc pr, pi, lr, li;
-    acc_zero(pr);
-    acc_zero(pi);
-    acc_zero(lr);
-    acc_zero(li);
-#pragma unroll
-    for (int l = 0; l < B; ++l) {
-      const cdf u = Ub[l * B + k];  // conj(U_lk)
-      cmac_conj<REALU>(pr, pi, u, ps[l]);
-      cmac_conj<REALU>(lr, li, u, la[l]);
-    }
-    psi[x[k]] = make_cdf(acc_get(pr), acc_get(pi));
-    lam[x[k]] = make_cdf(acc_get(lr), acc_get(li));
-  }
-}
-
-#define CVQ_BLOCK_SWITCH(B, CALL)                    \
-  switch (B) {                                       \
-    case 1: { constexpr int BB = 1; CALL; } break;   \
-    case 2: { constexpr int BB = 2; CALL; } break;   \
-    case 3: { constexpr int BB = 3; CALL; } break;   \
-    case 4: { constexpr int BB = 4; CALL; } break;   \
-    case 5: { constexpr int BB = 5; CALL; } break;   \
-    case 6: { constexpr int BB = 6; CALL; } break;   \
-    case 7: { constexpr int BB = 7; CALL; } break;   \
-    case 8: { constexpr int BB = 8; CALL; } break;   \
-    case 9: { constexpr int BB = 9; CALL; } break;   \
-    case 10: { constexpr int BB = 10; CALL; } break; \
-    case 11: { constexpr int BB = 11; CALL; } break; \
-    case 12: { constexpr int BB = 12; CALL; } break; \
-    case 13: { constexpr int BB = 13; CALL; } break; \
-    case 14: { constexpr int BB = 14; CALL; } break; \
-    case 15: { constexpr int BB = 15; CALL; } break; \
-    case 16: { constexpr int BB = 16; CALL; } break; \
-    default: break;                                  \
-  }
 
 // ------------------------------------------------------------ orbit enumeration
 
@@ -159,8 +65,8 @@ __host__ __device__ __forceinline__ int64_t bkc_items(const SectorDev& S, int nm
   return n;  // = 1 when no outer mode exists
 }
 
-__host__ __device__ __forceinline__ void bkc_orbit(const SectorDev& S, int i, int j, int64_t t, int64_t items, int64_t& f0,
-                                          int& q) {
+__host__ __device__ __forceinline__ void bkc_orbit(const SectorDev& S, int i, int j, int64_t t, int64_t items,
+                                                   int64_t& f0, int& q) {
   const int nm = (j >= 0) ? 2 : 1;
   if (S.L == nm) {  // no outer mode: one orbit, class fixed by the sector parity
     f0 = 0;
@@ -190,13 +96,11 @@ __host__ __device__ __forceinline__ void bkc_orbit(const SectorDev& S, int i, in
   f0 = f;
 }
 
-// Bose-Hubbard two-mode orbit t: class M (= n_i + n_j) and the tuple of its
-// first member (n_i, n_j) = (0, M).
-__host__ __device__ __forceinline__ uint64_t bh_orbit(const SectorDev& S, const int64_t (*G)[DMAX + 1], int i, int j,
-                                             int64_t t, int& M) {
-  M = 0;
-  while (M < S.N && t >= S.bh2_off[M + 1]) ++M;
-  const int64_t u = t - S.bh2_off[M];
+// Bose-Hubbard two-mode orbit u of class M (= n_i + n_j): the tuple of its
+// first member (n_i, n_j) = (0, M), built from the u-th composition of N - M
+// over the other L - 2 modes.
+__host__ __device__ __forceinline__ uint64_t bh_orbit_of_class(const SectorDev& S, const int64_t (*G)[DMAX + 1],
+                                                               int i, int j, int M, int64_t u) {
   const uint64_t wo = bh_unrank(u, S.L - 2, S.N - M, G);
   uint64_t w = (uint64_t)M << (4 * j);
   int k = 0;
@@ -208,79 +112,159 @@ __host__ __device__ __forceinline__ uint64_t bh_orbit(const SectorDev& S, const 
   return w;
 }
 
-// ------------------------------------------------------------ block kernels
-
-struct GateSmem {
-  cdf* U;
-  int2* mem;
-  float2* F;
-  BlockDesc* blk;
-};
-
-__device__ __forceinline__ GateSmem stage_gate(const GateArg& g, PoolDev P, bool needF, char* smem) {
-  GateSmem s;
-  const TypeDesc& t = g.t;
-  s.U = reinterpret_cast<cdf*>(smem);
-  s.blk = reinterpret_cast<BlockDesc*>(s.U + t.nu);
-  int nmem = 0, nf = 0;
-  for (int bi = 0; bi < t.nblocks; ++bi) {
-    const BlockDesc bd = P.blk[t.blk_base + bi];
-    nmem = max(nmem, bd.mem_off + bd.size);
-    nf = max(nf, bd.f_off + bd.size - 1);
-  }
-  s.mem = reinterpret_cast<int2*>(s.blk + t.nblocks);
-  s.F = reinterpret_cast<float2*>(s.mem + nmem);
-  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) s.U[e] = g.U[e];
-  for (int e = threadIdx.x; e < t.nblocks; e += blockDim.x) s.blk[e] = P.blk[t.blk_base + e];
-  for (int e = threadIdx.x; e < nmem; e += blockDim.x) s.mem[e] = P.mem[t.mem_base + e];
-  if (needF)
-    for (int e = threadIdx.x; e < nf; e += blockDim.x) s.F[e] = P.F[t.f_base + e];
-  __syncthreads();
-  return s;
+// The same for a global orbit number t (classes in increasing M).
+__host__ __device__ __forceinline__ uint64_t bh_orbit(const SectorDev& S, const int64_t (*G)[DMAX + 1], int i, int j,
+                                                      int64_t t, int& M) {
+  M = 0;
+  while (M < S.N && t >= S.bh2_off[M + 1]) ++M;
+  return bh_orbit_of_class(S, G, i, j, M, t - S.bh2_off[M]);
 }
 
+__device__ __forceinline__ BhIdx bh_idx_of(const SectorDev& S, const int64_t (*G)[DMAX + 1], int i, int j,
+                                           uint64_t w0) {
+  BhIdx h;
+  h.w0 = w0;
+  h.wR0 = bh_suffix(w0, S.L);
+  h.r0 = bh_rank(w0, S.L, S.N, G);
+  h.i = i;
+  h.j = j;
+  h.L = S.L;
+  h.G = G;
+  return h;
+}
+
+}  // namespace cvq
+
+namespace cvq {
+
+// ------------------------------------------------------------ one block
+
+// Forward: psi[x_k] <- sum_l U_kl psi[x_l].  Reverse: accumulate the gradient
+// term sum_k F_k Re(cp z_k), z_k = conj(lam_k) psi_{k+1} - lam_{k+1} conj(psi_k)
+// (the tridiagonal generator A[k][k+1] = cp F_k, A[k+1][k] = -conj(cp) F_k),
+// then psi <- U^dag psi and lam <- U^dag lam.
+template <bool ADJ, bool REALU, class IDX>
+__device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__ Ub, const int2* __restrict__ mem,
+                                            const float2* __restrict__ F, const float cpr, const float cpi,
+                                            const IDX& idx, const cdf* src, cdf* dst, cdf* lam, cdf* stg,
+                                            int64_t* sx, dfacc& gacc) {
+  const int tid = threadIdx.x;
+#pragma unroll 4
+  for (int l = 0; l < b; ++l) {
+    const int64_t x = idx(mem[l]);
+    sx[l * NTHREADS + tid] = x;
+    stg[l * NTHREADS + tid] = src[x];
+  }
+  if (!ADJ) {
+    for (int k = 0; k < b; ++k) {
+      dfacc ar, ai;
+      acc_zero(ar);
+      acc_zero(ai);
+      for (int l = 0; l < b; ++l) cmac<REALU>(ar, ai, Ub[k * b + l], stg[l * NTHREADS + tid]);
+      dst[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
+    }
+    return;
+  }
+  if (b > 1) {
+    cdf lk = lam[sx[tid]];
+    for (int k = 0; k + 1 < b; ++k) {
+      const cdf lk1 = lam[sx[(k + 1) * NTHREADS + tid]];
+      const cdf pk = stg[k * NTHREADS + tid], pk1 = stg[(k + 1) * NTHREADS + tid];
+      const df Fk = df_make(F[k].x, F[k].y);
+      if (cpr != 0.f) {  // Re z_k
+        dfacc z;
+        acc_zero(z);
+        acc_mac(z, re_of(lk), re_of(pk1));
+        acc_mac(z, im_of(lk), im_of(pk1));
+        acc_mac(z, df_neg(re_of(lk1)), re_of(pk));
+        acc_mac(z, df_neg(im_of(lk1)), im_of(pk));
+        const df zr = acc_get(z);
+        acc_mac(gacc, Fk, df_make(zr.h * cpr, zr.l * cpr));
+      }
+      if (cpi != 0.f) {  // -Im z_k
+        dfacc z;
+        acc_zero(z);
+        acc_mac(z, re_of(lk), im_of(pk1));
+        acc_mac(z, df_neg(im_of(lk)), re_of(pk1));
+        acc_mac(z, df_neg(im_of(lk1)), re_of(pk));
+        acc_mac(z, re_of(lk1), im_of(pk));
+        const df zi = acc_get(z);
+        acc_mac(gacc, Fk, df_make(-zi.h * cpi, -zi.l * cpi));
+      }
+      lk = lk1;
+    }
+  }
+  for (int k = 0; k < b; ++k) {  // psi <- U^dag psi
+    dfacc ar, ai;
+    acc_zero(ar);
+    acc_zero(ai);
+    for (int l = 0; l < b; ++l) cmac_conj<REALU>(ar, ai, Ub[l * b + k], stg[l * NTHREADS + tid]);
+    dst[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
+  }
+#pragma unroll 4
+  for (int l = 0; l < b; ++l) stg[l * NTHREADS + tid] = lam[sx[l * NTHREADS + tid]];
+  for (int k = 0; k < b; ++k) {  // lam <- U^dag lam
+    dfacc ar, ai;
+    acc_zero(ar);
+    acc_zero(ai);
+    for (int l = 0; l < b; ++l) cmac_conj<REALU>(ar, ai, Ub[l * b + k], stg[l * NTHREADS + tid]);
+    lam[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
+  }
+}
+
+// ------------------------------------------------------------ kernel
+
 template <int KIND, bool ADJ, bool REALU>
-__global__ void __launch_bounds__(NTHREADS) k_gate_block(const __grid_constant__ SectorDev S, const __grid_constant__ GateArg g,
-                                                         PoolDev P, const cdf* src, cdf* dst, cdf* lam,
-                                                         double* partial) {
+__global__ void __launch_bounds__(NTHREADS, 2)
+    k_gate_block(const __grid_constant__ SectorDev S, const __grid_constant__ GateArg g, PoolDev P, const cdf* src,
+                 cdf* dst, cdf* lam, double* partial) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int64_t Gs[LMAX][DMAX + 1];
   if (KIND == CVQ_BH) load_G(Gs, S);
-  const GateSmem sm = stage_gate(g, P, ADJ, smem);
   const TypeDesc& t = g.t;
+  cdf* sU = reinterpret_cast<cdf*>(smem);
+  BlockDesc* sB = reinterpret_cast<BlockDesc*>(sU + t.nu);
+  int2* sM = reinterpret_cast<int2*>(sB + t.nblocks);
+  float2* sF = reinterpret_cast<float2*>(sM + DMAX * DMAX);
+  cdf* stg = reinterpret_cast<cdf*>(smem + gate_tables_bytes(t));
+  int64_t* sx = reinterpret_cast<int64_t*>(stg + (size_t)t.bmax * NTHREADS);
+  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) sU[e] = g.U[e];
+  for (int e = threadIdx.x; e < t.nblocks; e += blockDim.x) sB[e] = P.blk[t.blk_base + e];
+  for (int e = threadIdx.x; e < t.nmem; e += blockDim.x) sM[e] = P.mem[t.mem_base + e];
+  if (ADJ)
+    for (int e = threadIdx.x; e < t.nf; e += blockDim.x) sF[e] = P.F[t.f_base + e];
+  __syncthreads();
   const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
+  const int j = t.single ? -1 : g.j;
   dfacc gacc;
   acc_zero(gacc);
-  const int nm = t.single ? 1 : 2;
-  const int j = t.single ? -1 : g.j;
-  const int64_t items = (KIND == CVQ_BKC) ? bkc_items(S, nm) : S.bh2_off[S.N + 1];
-  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (int64_t)gridDim.x * blockDim.x) {
-    int cls;
-    BkcIdx bidx;
-    BhIdx hidx;
-    if (KIND == CVQ_BKC) {
-      bkc_orbit(S, g.i, j, it, items, bidx.f0, cls);
-      bidx.si = S.stride[g.i];
-      bidx.sj = (j >= 0) ? S.stride[j] : 0;
-    } else {
-      hidx.w0 = bh_orbit(S, Gs, g.i, j, it, cls);
-      hidx.wR0 = bh_suffix(hidx.w0, S.L);
-      hidx.r0 = bh_rank(hidx.w0, S.L, S.N, Gs);
-      hidx.i = g.i;
-      hidx.j = j;
-      hidx.L = S.L;
-      hidx.G = Gs;
+  if (KIND == CVQ_BKC) {
+    const int64_t items = bkc_items(S, t.single ? 1 : 2);
+    BkcIdx idx;
+    idx.si = S.stride[g.i];
+    idx.sj = (j >= 0) ? S.stride[j] : 0;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+         it += (int64_t)gridDim.x * blockDim.x) {
+      int cls;
+      bkc_orbit(S, g.i, j, it, items, idx.f0, cls);
+      for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
+        const BlockDesc bd = sB[bi];
+        apply_block<ADJ, REALU>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src, dst, lam,
+                                stg, sx, gacc);
+      }
     }
-    for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
-      const BlockDesc bd = sm.blk[bi];
-      const cdf* Ub = sm.U + bd.u_off;
-      const int2* mem = sm.mem + bd.mem_off;
-      if (KIND == CVQ_BKC) {
-        if (ADJ) { CVQ_BLOCK_SWITCH(bd.size, (block_adj<BB, REALU>(Ub, mem, sm.F + bd.f_off, cpr, cpi, bidx, dst, lam, gacc))) }
-        else { CVQ_BLOCK_SWITCH(bd.size, (block_fwd<BB, REALU>(Ub, mem, bidx, src, dst))) }
-      } else {
-        if (ADJ) { CVQ_BLOCK_SWITCH(bd.size, (block_adj<BB, REALU>(Ub, mem, sm.F + bd.f_off, cpr, cpi, hidx, dst, lam, gacc))) }
-        else { CVQ_BLOCK_SWITCH(bd.size, (block_fwd<BB, REALU>(Ub, mem, hidx, src, dst))) }
+  } else {
+    // equal-work chunks (class M, orbits [u0, u1)) built on the host
+    for (int c = blockIdx.x; c < t.nchunks; c += gridDim.x) {
+      const int4 ch = P.chunks[t.chunk_base + c];
+      const int M = ch.x;
+      for (int64_t u = ch.y + threadIdx.x; u < ch.z; u += blockDim.x) {
+        const BhIdx idx = bh_idx_of(S, Gs, g.i, j, bh_orbit_of_class(S, Gs, g.i, j, M, u));
+        for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
+          const BlockDesc bd = sB[bi];
+          apply_block<ADJ, REALU>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src, dst,
+                                  lam, stg, sx, gacc);
+        }
       }
     }
   }
@@ -289,7 +273,6 @@ __global__ void __launch_bounds__(NTHREADS) k_gate_block(const __grid_constant__
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
   }
 }
-
 
 // Launch of the block kernel of one gate (REALU chosen from the gate type).
 template <int KIND, bool ADJ>

@@ -94,11 +94,6 @@ void launch_block(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* sr
 template <int KIND, bool ADJ>
 void set_block_smem_limit(int bytes);
 
-static size_t gate_smem_bytes(const TypeDesc& t) {
-  return (size_t)t.nu * sizeof(cdf) + (size_t)t.nblocks * sizeof(BlockDesc) + (size_t)(DMAX * DMAX) * sizeof(int2) +
-         (size_t)(DMAX * DMAX) * sizeof(float2);
-}
-
 template <bool ADJ>
 static cudaError_t launch_gate_impl(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* src, cdf* dst,
                                     cdf* lam, double* partial, cudaStream_t st) {
@@ -106,15 +101,16 @@ static cudaError_t launch_gate_impl(const SectorDev& S, const GateArg& g, PoolDe
   // 2 * (1^2 + ... + 15^2) + 16^2 = 2736 block entries and at most 64 blocks.
   constexpr int kMaxNu = 2816, kMaxBlocks = 64;
   if (g.t.diag || g.t.nu > kMaxNu || g.t.nblocks > kMaxBlocks) return cudaErrorInvalidValue;
+  // the largest gate (cutoff 16) needs ~150 KB: tables plus 256 staging columns of 16 entries
+  constexpr int kMaxSmem = 200 * 1024;
+  const size_t sm = gate_smem_bytes(g.t);
+  if (sm > (size_t)kMaxSmem) return cudaErrorInvalidValue;
   static bool attr_set = false;  // one opt-in to the largest dynamic shared memory a gate can need
   if (!attr_set) {
-    const int mx = (int)(kMaxNu * sizeof(cdf) + kMaxBlocks * sizeof(BlockDesc) + DMAX * DMAX * sizeof(int2) +
-                         DMAX * DMAX * sizeof(float2));
-    set_block_smem_limit<CVQ_BH, ADJ>(mx);
-    set_block_smem_limit<CVQ_BKC, ADJ>(mx);
+    set_block_smem_limit<CVQ_BH, ADJ>(kMaxSmem);
+    set_block_smem_limit<CVQ_BKC, ADJ>(kMaxSmem);
     attr_set = true;
   }
-  const size_t sm = gate_smem_bytes(g.t);
   if (S.kind == CVQ_BH) launch_block<CVQ_BH, ADJ>(S, g, P, src, dst, lam, partial, sm, st);
   else launch_block<CVQ_BKC, ADJ>(S, g, P, src, dst, lam, partial, sm, st);
   return cudaGetLastError();
