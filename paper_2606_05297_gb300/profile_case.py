@@ -41,6 +41,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--warm", type=int, default=0, help="unprofiled repetitions before cudaProfilerStart")
+    ap.add_argument("--kernels", action="store_true", help="print per-kernel event timings of the profiled range")
     a = ap.parse_args()
     import torch
     from paper_2606_05297_gb300 import build, cvq
@@ -57,6 +58,8 @@ def main():
         cvq.screen_pool(s, p, psi0, ws=ws)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()  # profiled range, for profilers started with --profile-from-start off
+    if a.kernels:
+        cvq.profile_start(1 << 16)
     t0 = time.perf_counter()
     for _ in range(a.reps):
         E, g = cvq.energy_and_grad(s, p, ids, th, psi0, ws=ws)
@@ -64,6 +67,11 @@ def main():
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     torch.cuda.profiler.stop()
+    if a.kernels:
+        for name, st in sorted(cvq.profile_stop().items(), key=lambda kv: -kv[1]["ms"]):
+            us = st["ms"] * 1e3 / st["launches"]
+            print(f"  {name:16s} {st['launches']:6d} launches {us:9.1f} us/launch "
+                  f"{st['bytes'] / st['ms'] / 1e6:8.1f} GB/s {st['flops'] / st['ms'] / 1e9:7.2f} TFLOP/s")
     print(f"{a.workload}: dim={s.dim} depth={a.depth} reps={a.reps} E={E.item():.12f} "
           f"|g|={g.abs().max().item():.6e} {dt / a.reps * 1e3:.2f} ms/rep")
 
