@@ -52,8 +52,10 @@ __host__ __device__ __forceinline__ uint64_t occ_shift(uint64_t w, int r, int de
 
 // Lexicographic rank of a composition of N (combinatorial number system):
 // rank = sum_{k < L-1} G[L-1-k][R_k] - G[L-1-k][R_{k+1}],  R_k = n_k + ... + n_{L-1}.
-__host__ __device__ __forceinline__ int64_t bh_rank(uint64_t w, int L, int N, const int64_t (*G)[DMAX + 1]) {
-  int64_t r = 0;
+// T is the table's integer type (int32 suffices for L, D <= 16: C(30, 15) < 2^31).
+template <class T>
+__host__ __device__ __forceinline__ T bh_rank(uint64_t w, int L, int N, const T (*G)[DMAX + 1]) {
+  T r = 0;
   int R = N;
   for (int k = 0; k < L - 1; ++k) {
     const int n = occ_get(w, k);
@@ -76,11 +78,12 @@ __host__ __device__ __forceinline__ uint64_t bh_suffix(uint64_t w, int L) {
 
 // Rank change when w is moved by (+dr on mode r, -dr on mode s): only the terms
 // of positions min(r,s)..max(r,s) change; wR holds the suffix sums of w.
-__host__ __device__ __forceinline__ int64_t bh_move_delta(uint64_t w, uint64_t wR, int r, int s, int dr, int L,
-                                                 const int64_t (*G)[DMAX + 1]) {
+template <class T>
+__host__ __device__ __forceinline__ T bh_move_delta(uint64_t w, uint64_t wR, int r, int s, int dr, int L,
+                                                   const T (*G)[DMAX + 1]) {
   int lo = r, hi = s, dlo = dr;
   if (s < r) { lo = s; hi = r; dlo = -dr; }
-  int64_t d = 0;
+  T d = 0;
   const int top = (hi < L - 1) ? hi : L - 2;
   for (int k = lo; k <= top; ++k) {
     const int p = L - 1 - k;
@@ -94,13 +97,14 @@ __host__ __device__ __forceinline__ int64_t bh_move_delta(uint64_t w, uint64_t w
 
 // Inverse of bh_rank for a chain of Lc modes holding Nc bosons; the tuple is
 // written to consecutive nibbles starting at nibble 0, its suffix sums to *wR.
-__host__ __device__ __forceinline__ uint64_t bh_unrank(int64_t x, int Lc, int Nc, const int64_t (*G)[DMAX + 1],
-                                              uint64_t* wR = nullptr) {
+template <class T>
+__host__ __device__ __forceinline__ uint64_t bh_unrank(T x, int Lc, int Nc, const T (*G)[DMAX + 1],
+                                                       uint64_t* wR = nullptr) {
   uint64_t w = 0, sR = 0;
   int R = Nc;
   for (int k = 0; k < Lc - 1; ++k) {
     const int p = Lc - 1 - k;
-    const int64_t base = G[p][R];
+    const T base = G[p][R];
     int n = 0;
     while (n < R && x >= base - G[p][R - n - 1]) ++n;
     x -= base - G[p][R - n];
@@ -113,6 +117,35 @@ __host__ __device__ __forceinline__ uint64_t bh_unrank(int64_t x, int Lc, int Nc
     sR |= (uint64_t)R << (4 * (Lc - 1));
   }
   if (wR) *wR = sR;
+  return w;
+}
+
+// Next composition in lexicographic order (same number of parts and sum),
+// packed in nibbles 0..Lc-1; false if w is the last one.  The rightmost part
+// p < Lc-1 with a nonzero sum after it grows by one and the parts after it
+// become (0, ..., 0, that sum - 1).
+__host__ __device__ __forceinline__ bool comp_next(uint64_t& w, int Lc) {
+  int S = 0, p;
+  for (p = Lc - 2; p >= 0; --p) {
+    S += occ_get(w, p + 1);
+    if (S > 0) break;
+  }
+  if (p < 0) return false;
+  w &= (4 * (p + 1) >= 64) ? ~0ull : ((1ull << (4 * (p + 1))) - 1);
+  w += 1ull << (4 * p);
+  w |= (uint64_t)(S - 1) << (4 * (Lc - 1));
+  return true;
+}
+
+// Insert two empty nibbles at modes lo < hi: the packed tuple of the other
+// L - 2 modes becomes a full tuple with n_lo = n_hi = 0.
+__host__ __device__ __forceinline__ uint64_t spread2(uint64_t wo, int lo, int hi) {
+  const uint64_t m1 = (lo == 0) ? 0ull : ((1ull << (4 * lo)) - 1);
+  const int mid = hi - lo - 1;
+  const uint64_t m2 = (mid <= 0) ? 0ull : ((1ull << (4 * mid)) - 1);
+  uint64_t w = wo & m1;
+  w |= ((wo >> (4 * lo)) & m2) << (4 * (lo + 1));
+  if (hi + 1 < 16) w |= (wo >> (4 * (hi - 1))) << (4 * (hi + 1));
   return w;
 }
 
@@ -262,10 +295,11 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;  // valid in thread 0
 }
 
-__device__ __forceinline__ void load_G(int64_t (*Gs)[DMAX + 1], const SectorDev& S) {
+template <class T>
+__device__ __forceinline__ void load_G(T (*Gs)[DMAX + 1], const SectorDev& S) {
   const int64_t* src = &S.tab->G[0][0];
-  int64_t* dst = &Gs[0][0];
-  for (int t = threadIdx.x; t < LMAX * (DMAX + 1); t += blockDim.x) dst[t] = src[t];
+  T* dst = &Gs[0][0];
+  for (int t = threadIdx.x; t < LMAX * (DMAX + 1); t += blockDim.x) dst[t] = (T)src[t];
 }
 
 }  // namespace cvq

@@ -21,15 +21,17 @@ struct BkcIdx {  // member (a, b) of an orbit with base f0: (f0 + a s_i + b s_j)
   __host__ __device__ __forceinline__ int64_t operator()(int2 m) const { return (f0 + m.x * si + m.y * sj) >> 1; }
 };
 
-struct BhIdx {   // member (a, M - a): rank of member (0, M) plus the rank change of moving a bosons j -> i
+template <class T>
+struct BhIdxT {  // member (a, M - a): rank of member (0, M) plus the rank change of moving a bosons j -> i
   uint64_t w0, wR0;
-  int64_t r0;
+  T r0;
   int i, j, L;
-  const int64_t (*G)[DMAX + 1];
+  const T (*G)[DMAX + 1];
   __host__ __device__ __forceinline__ int64_t operator()(int2 m) const {
-    return m.x ? r0 + bh_move_delta(w0, wR0, i, j, m.x, L, G) : r0;
+    return (int64_t)(m.x ? r0 + bh_move_delta(w0, wR0, i, j, m.x, L, G) : r0);
   }
 };
+using BhIdx = BhIdxT<int64_t>;
 
 // ------------------------------------------------------------ complex df helpers
 
@@ -50,6 +52,22 @@ __device__ __forceinline__ void cmac_conj(dfacc& ar, dfacc& ai, cdf u, cdf v) { 
   if (!REALU) {
     acc_mac(ar, im_of(u), im_of(v));
     acc_mac(ai, df_neg(im_of(u)), re_of(v));
+  }
+}
+
+// One product of a block-unitary entry with an amplitude when the entry is
+// real (even k - l, or a real generator) or purely imaginary (odd k - l):
+// 2 df products instead of 4.  CONJ uses conj(u).
+template <bool REALU, bool CONJ>
+__device__ __forceinline__ void cmac_cb(dfacc& ar, dfacc& ai, cdf u, cdf v, int odd) {
+  if (REALU || !odd) {
+    const df a = re_of(u);
+    acc_mac(ar, a, re_of(v));
+    acc_mac(ai, a, im_of(v));
+  } else {  // u = i b: u v = -b v.im + i b v.re
+    const df b = CONJ ? df_neg(im_of(u)) : im_of(u);
+    acc_mac(ar, df_neg(b), im_of(v));
+    acc_mac(ai, b, re_of(v));
   }
 }
 
@@ -120,9 +138,10 @@ __host__ __device__ __forceinline__ uint64_t bh_orbit(const SectorDev& S, const 
   return bh_orbit_of_class(S, G, i, j, M, t - S.bh2_off[M]);
 }
 
-__device__ __forceinline__ BhIdx bh_idx_of(const SectorDev& S, const int64_t (*G)[DMAX + 1], int i, int j,
-                                           uint64_t w0) {
-  BhIdx h;
+template <class T>
+__device__ __forceinline__ BhIdxT<T> bh_idx_of(const SectorDev& S, const T (*G)[DMAX + 1], int i, int j,
+                                               uint64_t w0) {
+  BhIdxT<T> h;
   h.w0 = w0;
   h.wR0 = bh_suffix(w0, S.L);
   h.r0 = bh_rank(w0, S.L, S.N, G);
@@ -160,7 +179,7 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
       dfacc ar, ai;
       acc_zero(ar);
       acc_zero(ai);
-      for (int l = 0; l < b; ++l) cmac<REALU>(ar, ai, Ub[k * b + l], stg[l * NTHREADS + tid]);
+      for (int l = 0; l < b; ++l) cmac_cb<REALU, false>(ar, ai, Ub[k * b + l], stg[l * NTHREADS + tid], (k ^ l) & 1);
       dst[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
     }
     return;
@@ -198,7 +217,7 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
     dfacc ar, ai;
     acc_zero(ar);
     acc_zero(ai);
-    for (int l = 0; l < b; ++l) cmac_conj<REALU>(ar, ai, Ub[l * b + k], stg[l * NTHREADS + tid]);
+    for (int l = 0; l < b; ++l) cmac_cb<REALU, true>(ar, ai, Ub[l * b + k], stg[l * NTHREADS + tid], (k ^ l) & 1);
     dst[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
   }
 #pragma unroll 4
@@ -207,7 +226,7 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
     dfacc ar, ai;
     acc_zero(ar);
     acc_zero(ai);
-    for (int l = 0; l < b; ++l) cmac_conj<REALU>(ar, ai, Ub[l * b + k], stg[l * NTHREADS + tid]);
+    for (int l = 0; l < b; ++l) cmac_cb<REALU, true>(ar, ai, Ub[l * b + k], stg[l * NTHREADS + tid], (k ^ l) & 1);
     lam[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
   }
 }
@@ -219,7 +238,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     k_gate_block(const __grid_constant__ SectorDev S, const __grid_constant__ GateArg g, PoolDev P, const cdf* src,
                  cdf* dst, cdf* lam, double* partial) {
   extern __shared__ __align__(16) char smem[];
-  __shared__ int64_t Gs[LMAX][DMAX + 1];
+  __shared__ int32_t Gs[LMAX][DMAX + 1];  // BH ranks fit in 32 bits for L, D <= 16
   if (KIND == CVQ_BH) load_G(Gs, S);
   const TypeDesc& t = g.t;
   cdf* sU = reinterpret_cast<cdf*>(smem);
@@ -254,17 +273,28 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       }
     }
   } else {
-    // equal-work chunks (class M, orbits [u0, u1)) built on the host
+    // Equal-work chunks (class M, orbits [u0, u1)) built on the host; each
+    // thread takes a contiguous run of the chunk's orbits and steps from one
+    // outer composition to the next instead of unranking every orbit.
+    const int lo = min(g.i, j), hi = max(g.i, j);
     for (int c = blockIdx.x; c < t.nchunks; c += gridDim.x) {
       const int4 ch = P.chunks[t.chunk_base + c];
       const int M = ch.x;
-      for (int64_t u = ch.y + threadIdx.x; u < ch.z; u += blockDim.x) {
-        const BhIdx idx = bh_idx_of(S, Gs, g.i, j, bh_orbit_of_class(S, Gs, g.i, j, M, u));
+      const int run = (ch.z - ch.y + NTHREADS - 1) / NTHREADS;
+      int u = ch.y + threadIdx.x * run;
+      const int uend = min(u + run, ch.z);
+      if (u >= uend) continue;
+      uint64_t wo = bh_unrank<int32_t>(u, S.L - 2, S.N - M, Gs);
+      for (;;) {
+        const uint64_t w0 = spread2(wo, lo, hi) | ((uint64_t)M << (4 * j));
+        const BhIdxT<int32_t> idx = bh_idx_of<int32_t>(S, Gs, g.i, j, w0);
         for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
           const BlockDesc bd = sB[bi];
           apply_block<ADJ, REALU>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src, dst,
                                   lam, stg, sx, gacc);
         }
+        if (++u >= uend) break;
+        comp_next(wo, S.L - 2);
       }
     }
   }

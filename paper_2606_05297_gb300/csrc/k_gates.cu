@@ -72,7 +72,12 @@ __global__ void k_build(const __grid_constant__ BuildArgs a, const TypeDesc* __r
         re += xr * vl.x + xi * vl.y;                                               // * conj(vl)
         im += xi * vl.x - xr * vl.y;
       }
-      if (t.realu) im = 0.0;  // the generator is real: exp(theta A) is real orthogonal
+      // Every generator here has phases that are multiples of pi/2 and a
+      // zero-diagonal tridiagonal block, so exp(theta A) has purely real entries
+      // (real generator) or real entries at even k - l and imaginary ones at odd
+      // k - l; the other component is zero up to rounding and is set to zero.
+      if (t.realu || ((k - l) & 1) == 0) im = 0.0;
+      else re = 0.0;
       Ug[bd.u_off + e] = make_cdf(df_from_double(re), df_from_double(im));
     }
     __syncthreads();

@@ -108,6 +108,31 @@ static void check_bh(int L, int N) {
         }
       }
   }
+  // lexicographic successor of compositions, and the nibble spread used by the gate kernels
+  for (int Lc = 0; Lc <= L; ++Lc) {
+    for (int R = 0; R <= N; ++R) {
+      std::vector<std::vector<int>> c;
+      std::vector<int> cc(Lc);
+      if (Lc > 0) enum_tuples(Lc, N + 1, c, cc, 0, keep_sum, R);
+      if (Lc == 0 && R != 0) continue;
+      if (Lc == 0) c.push_back({});
+      uint64_t w = bh_unrank<int64_t>(0, Lc, R, G);
+      for (size_t k = 0; k < c.size(); ++k) {
+        CHECK(w == pack(c[k]), "comp order Lc=%d R=%d k=%zu", Lc, R, k);
+        const bool more = comp_next(w, Lc);
+        CHECK(more == (k + 1 < c.size()), "comp_next end Lc=%d R=%d", Lc, R);
+      }
+    }
+  }
+  for (int lo = 0; lo < L; ++lo)
+    for (int hi = lo + 1; hi < L; ++hi) {
+      std::vector<int> o(L - 2);
+      for (int k = 0; k < L - 2; ++k) o[k] = (k * 7 + 3) % (N + 1);
+      std::vector<int> full;
+      int k = 0;
+      for (int r = 0; r < L; ++r) full.push_back((r == lo || r == hi) ? 0 : o[k++]);
+      CHECK(spread2(pack(o), lo, hi) == pack(full), "spread2 L=%d lo=%d hi=%d", L, lo, hi);
+    }
   // two-mode gate orbits: every index covered once
   for (int i = 0; i < L; ++i)
     for (int j = 0; j < L; ++j) {
