@@ -223,8 +223,11 @@ __host__ __device__ __forceinline__ size_t gate_tables_bytes(const TypeDesc& t) 
   return (b + 15) & ~(size_t)15;
 }
 
-__host__ __device__ __forceinline__ size_t gate_smem_bytes(const TypeDesc& t) {
-  return gate_tables_bytes(t) + (size_t)NTHREADS * t.bmax * (sizeof(cdf) + sizeof(int64_t));
+// Bose-Hubbard kernels also cache the members' sector indices (costly to
+// recompute); Kitaev-chain indices are recomputed from the orbit base.
+__host__ __device__ __forceinline__ size_t gate_smem_bytes(const TypeDesc& t, int kind) {
+  return gate_tables_bytes(t) +
+         (size_t)NTHREADS * t.bmax * (sizeof(cdf) + (kind == CVQ_BH ? sizeof(int64_t) : 0));
 }
 
 // Per-call list of gates for the unitary build kernel (passed by value).

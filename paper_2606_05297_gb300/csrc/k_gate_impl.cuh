@@ -162,16 +162,18 @@ namespace cvq {
 // term sum_k F_k Re(cp z_k), z_k = conj(lam_k) psi_{k+1} - lam_{k+1} conj(psi_k)
 // (the tridiagonal generator A[k][k+1] = cp F_k, A[k+1][k] = -conj(cp) F_k),
 // then psi <- U^dag psi and lam <- U^dag lam.
-template <bool ADJ, bool REALU, class IDX>
+template <bool ADJ, bool REALU, bool CACHE, class IDX>
 __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__ Ub, const int2* __restrict__ mem,
                                             const float2* __restrict__ F, const float cpr, const float cpi,
                                             const IDX& idx, const cdf* src, cdf* dst, cdf* lam, cdf* stg,
                                             int64_t* sx, dfacc& gacc) {
   const int tid = threadIdx.x;
+  // sector index of member l: cached in shared memory (CACHE) or recomputed
+  auto X = [&](int l) -> int64_t { return CACHE ? sx[l * NTHREADS + tid] : idx(mem[l]); };
 #pragma unroll 4
   for (int l = 0; l < b; ++l) {
     const int64_t x = idx(mem[l]);
-    sx[l * NTHREADS + tid] = x;
+    if (CACHE) sx[l * NTHREADS + tid] = x;
     stg[l * NTHREADS + tid] = src[x];
   }
   if (!ADJ) {
@@ -180,14 +182,14 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
       acc_zero(ar);
       acc_zero(ai);
       for (int l = 0; l < b; ++l) cmac_cb<REALU, false>(ar, ai, Ub[k * b + l], stg[l * NTHREADS + tid], (k ^ l) & 1);
-      dst[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
+      dst[X(k)] = make_cdf(acc_get(ar), acc_get(ai));
     }
     return;
   }
   if (b > 1) {
-    cdf lk = lam[sx[tid]];
+    cdf lk = lam[X(0)];
     for (int k = 0; k + 1 < b; ++k) {
-      const cdf lk1 = lam[sx[(k + 1) * NTHREADS + tid]];
+      const cdf lk1 = lam[X(k + 1)];
       const cdf pk = stg[k * NTHREADS + tid], pk1 = stg[(k + 1) * NTHREADS + tid];
       const df Fk = df_make(F[k].x, F[k].y);
       if (cpr != 0.f) {  // Re z_k
@@ -218,16 +220,16 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
     acc_zero(ar);
     acc_zero(ai);
     for (int l = 0; l < b; ++l) cmac_cb<REALU, true>(ar, ai, Ub[l * b + k], stg[l * NTHREADS + tid], (k ^ l) & 1);
-    dst[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
+    dst[X(k)] = make_cdf(acc_get(ar), acc_get(ai));
   }
 #pragma unroll 4
-  for (int l = 0; l < b; ++l) stg[l * NTHREADS + tid] = lam[sx[l * NTHREADS + tid]];
+  for (int l = 0; l < b; ++l) stg[l * NTHREADS + tid] = lam[X(l)];
   for (int k = 0; k < b; ++k) {  // lam <- U^dag lam
     dfacc ar, ai;
     acc_zero(ar);
     acc_zero(ai);
     for (int l = 0; l < b; ++l) cmac_cb<REALU, true>(ar, ai, Ub[l * b + k], stg[l * NTHREADS + tid], (k ^ l) & 1);
-    lam[sx[k * NTHREADS + tid]] = make_cdf(acc_get(ar), acc_get(ai));
+    lam[X(k)] = make_cdf(acc_get(ar), acc_get(ai));
   }
 }
 
@@ -268,8 +270,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       bkc_orbit(S, g.i, j, it, items, idx.f0, cls);
       for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
         const BlockDesc bd = sB[bi];
-        apply_block<ADJ, REALU>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src, dst, lam,
-                                stg, sx, gacc);
+        apply_block<ADJ, REALU, false>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src, dst,
+                                       lam, stg, sx, gacc);
       }
     }
   } else {
@@ -290,8 +292,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         const BhIdxT<int32_t> idx = bh_idx_of<int32_t>(S, Gs, g.i, j, w0);
         for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
           const BlockDesc bd = sB[bi];
-          apply_block<ADJ, REALU>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src, dst,
-                                  lam, stg, sx, gacc);
+          apply_block<ADJ, REALU, true>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src,
+                                        dst, lam, stg, sx, gacc);
         }
         if (++u >= uend) break;
         comp_next(wo, S.L - 2);

@@ -108,7 +108,7 @@ static cudaError_t launch_gate_impl(const SectorDev& S, const GateArg& g, PoolDe
   if (g.t.diag || g.t.nu > kMaxNu || g.t.nblocks > kMaxBlocks) return cudaErrorInvalidValue;
   // the largest gate (cutoff 16) needs ~150 KB: tables plus 256 staging columns of 16 entries
   constexpr int kMaxSmem = 200 * 1024;
-  const size_t sm = gate_smem_bytes(g.t);
+  const size_t sm = gate_smem_bytes(g.t, S.kind);
   if (sm > (size_t)kMaxSmem) return cudaErrorInvalidValue;
   static bool attr_set = false;  // one opt-in to the largest dynamic shared memory a gate can need
   if (!attr_set) {
