@@ -174,6 +174,58 @@ int cvq_lanczos_step(const cvq_sector *s, const cvq_c128 *v_prev, const cvq_c128
 int cvq_op_cost(const cvq_sector *s, const cvq_pool *p, int op, double *fwd_bytes, double *fwd_flops,
                 double *adj_bytes, double *adj_flops);
 
+/* State features for the learned proposal (ranking pool operators before the
+ * exact Eq. (grad) screen; the learned proposal extends Sec. IV.B): for the
+ * state psi (dim amplitudes, device, not necessarily normalised) writes
+ *   out_dev[r]               = <psi| n_r |psi>,          r = 0..L-1
+ *   out_dev[L + r]           = <psi| n_r^2 |psi>,
+ *   out_dev[2L + 2p], [+1]   = Re, Im <psi| a_i^dag a_j |psi>, (i, j) = (pair_i[p], pair_j[p]),
+ * p = 0..npairs-1 (host arrays, i != j, 0 <= npairs <= 240).  The truncated
+ * ladder rules of Sec. II.A apply.  workspace: >= cvq_features_workspace_bytes.
+ * Errors: EINVAL, ECUDA. */
+int cvq_features_workspace_bytes(const cvq_sector *s, int npairs, size_t *bytes);
+int cvq_features(const cvq_sector *s, const cvq_c128 *psi, const int *pair_i, const int *pair_j, int npairs,
+                 double *out_dev, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Learned proposal scorer (extends Sec. IV.B's operator selection): an MLP
+ * that maps one pool operator's input features (in_dim = 32 floats) to a
+ * score, 32 -> 256 -> 256 -> 1 with ReLU.  Weights are kept as fp32 master
+ * copies and used as bf16 (round to nearest even) in every product; all sums
+ * accumulate in fp32.  The parameter vector (74,497 floats) is laid out as
+ * W1[256][32], b1[256], W2[256][256], b2[256], w3[256], b3.
+ *   cvq_mlp_create: He-initialised weights from `seed`, room for max_rows rows
+ *     (allocates; synchronises).
+ *   cvq_mlp_forward: scores_dev[r] for the rows of X_dev (row-major, rows x 32,
+ *     device); keeps the activations for cvq_mlp_backward.
+ *   cvq_mlp_backward: gradients of sum_r dscores_dev[r] * score_r with respect
+ *     to every parameter (overwrites the gradient buffer), for the rows of the
+ *     last forward call.
+ *   cvq_mlp_listwise_loss: for nlists lists (device offsets
+ *     list_off_dev[0..nlists], rows list_off[l]..list_off[l+1]) of scores and
+ *     target probabilities, loss_dev[l] = -sum p log softmax(s) and
+ *     dscores_dev = softmax(s) - p; an empty list gives loss 0.  No
+ *     allocation, no synchronisation.
+ *   cvq_mlp_adam_step: one Adam step (lr, beta1 = 0.9, beta2 = 0.999,
+ *     eps = 1e-8, bias-corrected for step t >= 1) on the master weights, then
+ *     refreshes the bf16 copies.
+ *   cvq_mlp_get / cvq_mlp_set: copy parameters (or, get only, gradients with
+ *     which = 1) between the model and a host float array of 74,497 entries;
+ *     set also zeroes the Adam moments and refreshes the bf16 copies.  Both
+ *     synchronise the device.
+ * Forward, backward and Adam run on `stream` without allocating or
+ * synchronising; one model must not be used from two streams at once.
+ * Errors: EINVAL (sizes), ENOMEM, ECUDA. */
+typedef struct cvq_mlp cvq_mlp;
+int cvq_mlp_create(int in_dim, int hidden, int max_rows, uint64_t seed, cvq_mlp **out);
+void cvq_mlp_destroy(cvq_mlp *m);
+int cvq_mlp_forward(cvq_mlp *m, const float *X_dev, int rows, float *scores_dev, void *stream);
+int cvq_mlp_backward(cvq_mlp *m, const float *X_dev, int rows, const float *dscores_dev, void *stream);
+int cvq_mlp_listwise_loss(const float *scores_dev, const float *targets_dev, const int *list_off_dev, int nlists,
+                          float *dscores_dev, float *loss_dev, void *stream);
+int cvq_mlp_adam_step(cvq_mlp *m, float lr, int t, void *stream);
+int cvq_mlp_get(const cvq_mlp *m, int which, float *host, size_t n);
+int cvq_mlp_set(cvq_mlp *m, const float *host, size_t n);
+
 /* Pool screen for callers that cannot allocate device memory.  The paper has
  * no counterpart to this call: it exists for code that must not call
  * cudaMalloc when it screens -- code running while a stream is captured into a

@@ -45,10 +45,12 @@ extern "C" const char* cvq_last_error(void) { return g_err.c_str(); }
 // ------------------------------------------------------------------ profiling
 
 enum KernelKind {
-  KK_APPLY_H, KK_SCREEN, KK_GATE, KK_GATE_DIAG, KK_ADJ, KK_ADJ_DIAG, KK_BUILD, KK_REDUCE, KK_LANCZOS, KK_CONVERT, KK_COUNT
+  KK_APPLY_H, KK_SCREEN, KK_GATE, KK_GATE_DIAG, KK_ADJ, KK_ADJ_DIAG, KK_BUILD, KK_REDUCE, KK_LANCZOS, KK_CONVERT,
+  KK_FEATURES, KK_MLP, KK_COUNT
 };
 static const char* const kKindName[KK_COUNT] = {"apply_H", "screen", "gate_block", "gate_diag", "adjoint_block",
-                                                "adjoint_diag", "build_unitaries", "reduce", "lanczos", "convert"};
+                                                "adjoint_diag", "build_unitaries", "reduce", "lanczos", "convert",
+                                                "features", "mlp"};
 
 struct ProfRec {
   int kind;
@@ -1012,4 +1014,54 @@ const GateArg* internal_pool_ops(const cvq_pool* p, const cvq_sector** sec, int*
 
 int internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
+// Event-pair timing for launches made outside this file (the scorer MLP).
+int internal_prof_mlp_begin(cudaStream_t st, double bytes, double flops) {
+  if (!g_prof_on) return -1;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on || g_prof_n >= g_prof.size()) return -1;
+  const int idx = (int)g_prof_n++;
+  g_prof[idx].kind = KK_MLP;
+  g_prof[idx].bytes = bytes;
+  g_prof[idx].flops = flops;
+  cudaEventRecord(g_prof[idx].a, st);
+  return idx;
+}
+
+void internal_prof_end(int idx, cudaStream_t st) {
+  if (idx >= 0) cudaEventRecord(g_prof[idx].b, st);
+}
+
 }  // namespace cvq
+
+// ------------------------------------------------------------------ features
+
+extern "C" int cvq_features_workspace_bytes(const cvq_sector* s, int npairs, size_t* bytes) {
+  if (!s || !bytes) return fail(CVQ_EINVAL, "null argument");
+  if (npairs < 0 || npairs > 240) return fail(CVQ_EINVAL, "npairs %d outside [0, 240]", npairs);
+  *bytes = al256((size_t)(2 * s->S.L + 2 * npairs) * NBLK * sizeof(double));
+  return CVQ_OK;
+}
+
+extern "C" int cvq_features(const cvq_sector* s, const cvq_c128* psi, const int* pair_i, const int* pair_j,
+                            int npairs, double* out_dev, void* ws, size_t wsb, void* stream) {
+  if (!s || !psi || !out_dev || (npairs > 0 && (!pair_i || !pair_j))) return fail(CVQ_EINVAL, "null argument");
+  size_t need = 0;
+  if (int rc = cvq_features_workspace_bytes(s, npairs, &need)) return rc;
+  if (!ws || ((uintptr_t)ws & 255)) return fail(CVQ_EINVAL, "workspace NULL or not 256-byte aligned");
+  if (wsb < need) return fail(CVQ_EINVAL, "workspace of %zu bytes, %zu needed", wsb, need);
+  for (int p = 0; p < npairs; ++p)
+    if (pair_i[p] < 0 || pair_i[p] >= s->S.L || pair_j[p] < 0 || pair_j[p] >= s->S.L || pair_i[p] == pair_j[p])
+      return fail(CVQ_EINVAL, "feature pair %d = (%d, %d) invalid", p, pair_i[p], pair_j[p]);
+  cudaStream_t st = (cudaStream_t)stream;
+  double* partial = (double*)ws;
+  const int rows = 2 * s->S.L + 2 * npairs;
+  {
+    ProfScope ps(KK_FEATURES, st, 16.0 * (double)s->S.dim * (1 + npairs), (double)s->S.dim * (4.0 * s->S.L + 8.0 * npairs));
+    CVQ_CUDA(launch_features(s->S, (const double2*)psi, pair_i, pair_j, npairs, partial, st), "features");
+  }
+  {
+    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * rows, (double)NBLK * rows);
+    CVQ_CUDA(launch_reduce(partial, rows, NBLK, 1.0, out_dev, st), "reduce features");
+  }
+  return CVQ_OK;
+}

@@ -275,6 +275,9 @@ cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* 
                             double* partial, bool adjoint, cudaStream_t st);
 cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const cdf* psi,
                           const cdf* sigma, double* partial, cudaStream_t st);
+// State features (<n_r>, <n_r^2>, <a_i^dag a_j>) as (2L + 2 npairs) rows of partials.
+cudaError_t launch_features(const SectorDev& S, const double2* psi, const int* pi, const int* pj, int npairs,
+                            double* partial, cudaStream_t st);
 // Lanczos on complex128 vectors: w <- w - alpha v - beta_prev v_prev with
 // partial sums of ||w||^2, then v_next = w / ||w||.
 cudaError_t launch_lanczos_update(const SectorDev& S, const double2* v_prev, const double2* v, double2* w,

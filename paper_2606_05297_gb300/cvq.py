@@ -276,3 +276,99 @@ def screen_subset_noalloc(sector: Sector, pool: Pool, psi, subset, out=None, str
     _check(lib().cvq_screen_subset_noalloc(sector.h, pool.h, _ptr(psi), sa, n, _ptr(out), _stream(stream)),
            "cvq_screen_subset_noalloc")
     return out[:n]
+
+
+def features(sector: Sector, psi, pairs=(), out=None, stream=None):
+    """<n_r>, <n_r^2> per mode and Re/Im <a_i^dag a_j> per (i, j) in pairs (device float64 vector
+    of length 2L + 2 len(pairs))."""
+    import torch
+    L = sector.L
+    npairs = len(pairs)
+    lib().cvq_features_workspace_bytes.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_size_t)]
+    lib().cvq_features.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int,
+                                   C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+    b = C.c_size_t()
+    _check(lib().cvq_features_workspace_bytes(sector.h, npairs, C.byref(b)), "cvq_features_workspace_bytes")
+    ws = torch.empty(int(b.value), dtype=torch.uint8, device=psi.device)
+    if out is None:
+        out = torch.empty(2 * L + 2 * npairs, dtype=torch.float64, device=psi.device)
+    pi = (C.c_int * max(npairs, 1))(*[int(p[0]) for p in pairs])
+    pj = (C.c_int * max(npairs, 1))(*[int(p[1]) for p in pairs])
+    _check(lib().cvq_features(sector.h, _ptr(psi), pi, pj, npairs, _ptr(out), _ptr(ws), C.c_size_t(ws.numel()),
+                              _stream(stream)), "cvq_features")
+    return out
+
+
+MLP_IN, MLP_HIDDEN, MLP_NPARAM = 32, 256, 74497
+
+
+def _mlp_sigs(L):
+    vp, f32p = C.c_void_p, C.POINTER(C.c_float)
+    L.cvq_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(vp)]
+    L.cvq_mlp_destroy.argtypes = [vp]
+    L.cvq_mlp_destroy.restype = None
+    L.cvq_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.cvq_mlp_backward.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.cvq_mlp_listwise_loss.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp]
+    L.cvq_mlp_adam_step.argtypes = [vp, C.c_float, C.c_int, vp]
+    L.cvq_mlp_get.argtypes = [vp, C.c_int, f32p, C.c_size_t]
+    L.cvq_mlp_set.argtypes = [vp, f32p, C.c_size_t]
+    return L
+
+
+class Scorer:
+    """The proposal scorer (32 -> 256 -> 256 -> 1, bf16 weights, fp32 sums) on the current device.
+    Inputs and outputs are device float32 tensors."""
+
+    def __init__(self, max_rows: int, seed: int = 0):
+        L = _mlp_sigs(lib())
+        h = C.c_void_p()
+        _check(L.cvq_mlp_create(MLP_IN, MLP_HIDDEN, int(max_rows), int(seed) & (2 ** 64 - 1), C.byref(h)),
+               "cvq_mlp_create")
+        self.h, self.max_rows, self.t = h, int(max_rows), 0
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.cvq_mlp_destroy(self.h)
+            self.h = None
+
+    def forward(self, X, out=None, stream=None):
+        import torch
+        assert X.dtype == torch.float32 and X.is_contiguous() and X.shape[-1] == MLP_IN
+        if out is None:
+            out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(lib().cvq_mlp_forward(self.h, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)), "cvq_mlp_forward")
+        return out
+
+    def backward(self, X, dscores, stream=None):
+        _check(lib().cvq_mlp_backward(self.h, _ptr(X), int(X.shape[0]), _ptr(dscores), _stream(stream)),
+               "cvq_mlp_backward")
+
+    def adam_step(self, lr: float, stream=None):
+        self.t += 1
+        _check(lib().cvq_mlp_adam_step(self.h, C.c_float(lr), self.t, _stream(stream)), "cvq_mlp_adam_step")
+
+    def get(self, which: int = 0):
+        buf = np.empty(MLP_NPARAM, dtype=np.float32)
+        _check(lib().cvq_mlp_get(self.h, which, buf.ctypes.data_as(C.POINTER(C.c_float)), buf.size), "cvq_mlp_get")
+        return buf
+
+    def set(self, params):
+        buf = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().cvq_mlp_set(self.h, buf.ctypes.data_as(C.POINTER(C.c_float)), buf.size), "cvq_mlp_set")
+        self.t = 0
+
+
+def listwise_loss(scores, targets, list_off, dscores=None, loss=None, stream=None):
+    """Per-list softmax cross-entropy and d loss / d scores; list_off is a device int32 tensor of nlists + 1
+    offsets."""
+    import torch
+    L = _mlp_sigs(lib())
+    n = int(list_off.numel()) - 1
+    if dscores is None:
+        dscores = torch.empty_like(scores)
+    if loss is None:
+        loss = torch.empty(max(n, 0), dtype=torch.float32, device=scores.device)
+    _check(L.cvq_mlp_listwise_loss(_ptr(scores), _ptr(targets), _ptr(list_off), n, _ptr(dscores), _ptr(loss),
+                                   _stream(stream)), "cvq_mlp_listwise_loss")
+    return loss, dscores

@@ -282,3 +282,32 @@ def pool_for(model: Model) -> List[Op]:
 
 def initial_occupation(model: Model) -> List[int]:
     return mott_occupation(model.L, model.N) if model.kind == "bh" else vacuum_occupation(model.L)
+
+
+# ---------------------------------------------------------------- scorer inputs
+
+SCORER_SHAPES = [(256, 32), (256,), (256, 256), (256,), (256,), ()]
+
+
+def scorer_params(seed: int) -> np.ndarray:
+    """A float32 parameter vector of the proposal scorer (He-scaled normal
+    weights, small normal biases), in the order W1, b1, W2, b2, w3, b3."""
+    rng = np.random.default_rng(seed)
+    fan = [32, 1, 256, 1, 256, 1]
+    parts = []
+    for shape, f in zip(SCORER_SHAPES, fan):
+        n = int(np.prod(shape))
+        scale = math.sqrt(2.0 / f) if f > 1 else 0.1
+        parts.append(rng.standard_normal(n) * scale)
+    return np.concatenate(parts).astype(np.float32)
+
+
+def scorer_inputs(rows: int, seed: int) -> np.ndarray:
+    """Feature rows shaped like the proposal's inputs: a one-hot block, values
+    in [0, 1] and signed log-magnitudes."""
+    rng = np.random.default_rng(seed)
+    X = np.zeros((rows, 32), dtype=np.float32)
+    X[np.arange(rows), rng.integers(0, 8, rows)] = 1.0
+    X[:, 8:20] = rng.random((rows, 12))
+    X[:, 20:32] = rng.standard_normal((rows, 12)) * 3.0
+    return X
