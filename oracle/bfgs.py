@@ -16,7 +16,10 @@ C1, C2 = 1e-4, 0.9
 
 
 def _cubic_min(a, fa, ga, b, fb, gb):
-    """Minimiser of the cubic interpolating f and f' at a and b (N&W eq. 3.59)."""
+    """Minimiser of the cubic interpolating f and f' at a and b (N&W eq. 3.59);
+    None for a bracket of zero width, which has no interpolating cubic."""
+    if a == b:
+        return None
     d1 = ga + gb - 3.0 * (fa - fb) / (a - b)
     disc = d1 * d1 - ga * gb
     if disc < 0:

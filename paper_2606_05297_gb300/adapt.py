@@ -62,7 +62,10 @@ class BFGS:
 
     @staticmethod
     def _cubic(a, fa, da, b, fb, db):
-        # minimiser of the Hermite cubic through (a, fa, da) and (b, fb, db)
+        # minimiser of the Hermite cubic through (a, fa, da) and (b, fb, db);
+        # a zero-width bracket has none (the caller bisects)
+        if a == b:
+            return None
         t1 = da + db - 3.0 * (fa - fb) / (a - b)
         sq = t1 * t1 - da * db
         if sq < 0.0:
@@ -240,6 +243,10 @@ class Adapt:
         k, gmax = select(g)
         if gmax < grad_tol:
             return None
+        return self._grow(k, gmax, max_iter, t0)
+
+    def _grow(self, k, gmax, max_iter, t0):
+        """Append pool operator k with theta = 0 and re-minimise every parameter."""
         if len(self.ids) + 1 > self.n_max:
             raise RuntimeError("ansatz length exceeds the workspace")
         self.ids.append(k)

@@ -42,3 +42,19 @@ def test_selection_tie_rule():
     assert select([0.1, -2.0, 2.0, 1.0])[0] == 1
     assert select([0.1, 2.0 * (1 - 5e-10), -2.0])[0] == 1
     assert select([0.1, 2.0 * (1 - 5e-9), -2.0])[0] == 2
+
+
+def test_bfgs_line_search_at_the_step_cap():
+    """A far minimum makes the bracketing phase reach the largest step twice
+    (a zero-width bracket); both minimisers must bisect instead of dividing by
+    the bracket width, and still agree iterate for iterate."""
+    from oracle import bfgs as ob
+
+    def fg(x):
+        d = x - 1e4
+        return float(1e-6 * d @ d), 2e-6 * d
+
+    r = BFGS(fg).minimize(np.zeros(2), gtol=1e-9, max_iter=200)
+    o = ob.minimize(fg, np.zeros(2), gtol=1e-9, max_iter=200)
+    assert np.isfinite(r.f) and r.f < fg(np.zeros(2))[0]
+    assert np.array_equal(r.x, o["x"]) and r.nit == o["nit"]
