@@ -45,7 +45,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--instances", type=int, default=len(U_VALUES),
+                    help="use the first n of the U/J instances (profiling runs)")
     a = ap.parse_args()
+    if not 1 <= a.instances <= len(U_VALUES):
+        ap.error(f"--instances must be in [1, {len(U_VALUES)}]")
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
     return a
@@ -203,7 +207,7 @@ def run_ours(args):
     rank, ws, local = dist_init(args)
     stream = torch.cuda.current_stream()
     insts = []
-    for u in U_VALUES:
+    for u in U_VALUES[: args.instances]:
         m = W.c2_model(u)
         pool = W.bh_allpairs_pool(m.L)
         warm = W.hva_layer(m)
@@ -322,7 +326,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128 states)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "instances_per_rank": len(insts), "dim": insts[0].sector.dim,
+            "config": {"workload": WORKLOAD if len(insts) == len(U_VALUES) else
+                       WORKLOAD.replace("UJ1,3.4,10", "UJ" + ",".join(f"{u:g}" for u in U_VALUES[: len(insts)])),
+                       "instances_per_rank": len(insts), "dim": insts[0].sector.dim,
                        "pool": insts[0].K, "warm_start_gates": 36, "l2": "256 MB buffer written between steps",
                        "ansatz_len_mean": float(np.mean(ngates)), "bfgs_evals_per_iter_mean": float(np.mean(nfev)),
                        "dE_last": [abs(A.trace[-1]["E"] - A.E0) for A in insts], "parallelism": f"replicas x{ws}"},

@@ -226,6 +226,37 @@ int cvq_mlp_adam_step(cvq_mlp *m, float lr, int t, void *stream);
 int cvq_mlp_get(const cvq_mlp *m, int which, float *host, size_t n);
 int cvq_mlp_set(cvq_mlp *m, const float *host, size_t n);
 
+/* Batched engine (extends Sec. IV.B's per-instance evaluation to many
+ * Hamiltonian instances at once, e.g. a U/J sweep): the energy and adjoint
+ * gradient of every instance of the batch from one CUDA graph launch.
+ *   cvq_batch_create: n_inst sectors of one kind on the current device, each
+ *     with its pool (pools[i] built on sectors[i]); room for n_max gates per
+ *     instance.  Allocates 32 bytes per amplitude per instance plus the block
+ *     unitaries.  The sectors and pools must outlive the batch.
+ *   cvq_batch_set_ansatz: the ansatz of every instance, n_ops[i] in [-1,
+ *     n_max] (-1: instance left out), op ids packed instance after instance
+ *     (host), psi0[i] the device complex128 reference state of instance i
+ *     (kept by pointer).  Builds the work schedule (allocates, synchronises).
+ *   cvq_batch_set_schedule: work-item size in amplitudes (tile >= 256) and
+ *     CTAs per SM of every layer launch (1 or 2); rebuilds the schedule.
+ *   cvq_batch_energy_and_grad: theta_dev and grad_dev packed like the op ids,
+ *     E_dev[i] per instance (device, float64); instances left out are not
+ *     written.  The first call for a schedule (or for new buffer pointers)
+ *     captures the evaluation into a CUDA graph; later calls launch it on
+ *     `stream`.  Results are deterministic: every partial sum has its own
+ *     slot and the final sums run in a fixed order.
+ *   cvq_batch_info: kernels per evaluation, work items, layers and the
+ *     number of parameters.
+ * Errors: EINVAL (sizes, mixed kinds or devices, op ids), ENOMEM, ECUDA. */
+typedef struct cvq_batch cvq_batch;
+int cvq_batch_create(const cvq_sector *const *sectors, const cvq_pool *const *pools, int n_inst, int n_max,
+                     cvq_batch **out);
+void cvq_batch_destroy(cvq_batch *b);
+int cvq_batch_set_ansatz(cvq_batch *b, const int *n_ops, const int *op_ids, const cvq_c128 *const *psi0);
+int cvq_batch_set_schedule(cvq_batch *b, int64_t tile, int ctas_per_sm);
+int cvq_batch_energy_and_grad(cvq_batch *b, const double *theta_dev, double *E_dev, double *grad_dev, void *stream);
+int cvq_batch_info(const cvq_batch *b, int *kernels_per_eval, int *items, int *layers, int64_t *n_params);
+
 /* Pool screen for callers that cannot allocate device memory.  The paper has
  * no counterpart to this call: it exists for code that must not call
  * cudaMalloc when it screens -- code running while a stream is captured into a

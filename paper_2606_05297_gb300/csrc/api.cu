@@ -1014,6 +1014,26 @@ const GateArg* internal_pool_ops(const cvq_pool* p, const cvq_sector** sec, int*
 
 int internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 
+// Host-side view of a pool for the batched engine.
+int internal_pool_host(const cvq_pool* p, const cvq_sector** sec, const TypeDesc** types, int* ntypes,
+                       const int** op_type, const int** op_i, const int** op_j, int* K, PoolDev* P, int* ustride,
+                       const GateArg** ops_dev) {
+  if (!p) return fail(CVQ_EINVAL, "null pool");
+  *sec = p->sec;
+  *types = p->types.data();
+  *ntypes = (int)p->types.size();
+  *op_type = p->op_type.data();
+  *op_i = p->op_i.data();
+  *op_j = p->op_j.data();
+  *K = p->K;
+  *P = p->P;
+  *ustride = p->ustride;
+  *ops_dev = p->ops_dev;
+  return CVQ_OK;
+}
+
+int internal_sector_device(const cvq_sector* s) { return s ? s->device : -1; }
+
 // Event-pair timing for launches made outside this file (the scorer MLP).
 int internal_prof_mlp_begin(cudaStream_t st, double bytes, double flops) {
   if (!g_prof_on) return -1;

@@ -1,0 +1,459 @@
+// batch_api.cu -- host side of the batched engine (cvq_batch_*): per-instance
+// buffers, the layer and work-item schedule of one ansatz structure, the
+// final reduction plan, and the CUDA graph that replays one evaluation.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cvq_internal.cuh"
+#include "k_ham_impl.cuh"
+
+namespace cvq {
+int internal_fail(int code, const char* msg);
+const SectorDev* internal_sector(const cvq_sector* s);
+int internal_sector_device(const cvq_sector* s);
+int internal_pool_host(const cvq_pool* p, const cvq_sector** sec, const TypeDesc** types, int* ntypes,
+                       const int** op_type, const int** op_i, const int** op_j, int* K, PoolDev* P, int* ustride,
+                       const GateArg** ops_dev);
+}  // namespace cvq
+
+using namespace cvq;
+
+namespace {
+
+struct PoolView {
+  const cvq_sector* sec;
+  const TypeDesc* types;
+  int ntypes, K, ustride;
+  const int *op_type, *op_i, *op_j;
+  PoolDev P;
+  const GateArg* ops_dev;
+};
+
+int errf(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  return internal_fail(code, buf);
+}
+
+int cuda_err(cudaError_t e, const char* what) { return errf(CVQ_ECUDA, "%s: %s", what, cudaGetErrorString(e)); }
+
+#define BCUDA(call, what)                             \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_err(e_, what); \
+  } while (0)
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct cvq_batch {
+  int n = 0, kind = 0, device = 0, n_max = 0, sms = 0;
+  std::vector<PoolView> pv;
+  std::vector<SectorDev> S;
+  void* state = nullptr;  // psi, lam, U of every instance
+  std::vector<BInst> inst;
+  BInst* inst_d = nullptr;
+  // schedule knobs
+  int64_t tile = 32768;   // amplitudes per work item
+  int ctas_per_sm = 2;
+  // structure
+  bool have = false;
+  std::vector<int> n_ops, ids;  // host copy (rebuilds on schedule changes)
+  std::vector<const double2*> psi0;
+  void* plan = nullptr;         // ids, segments, items, reductions, gates, counters, partials
+  int* ids_d = nullptr;
+  BSeg* segs_d = nullptr;
+  BItem* items_d = nullptr;
+  BRed* red_d = nullptr;
+  int2* gates_d = nullptr;
+  int* counters_d = nullptr;
+  double* partial_d = nullptr;
+  std::vector<int> layer_off, layer_n;
+  std::vector<char> layer_adj;
+  int n_red = 0, n_gates = 0, n_items = 0, n_theta = 0;
+  size_t smem = 0;
+  // graph
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const double* g_theta = nullptr;
+  double *g_E = nullptr, *g_grad = nullptr;
+};
+
+namespace {
+
+void drop_graph(cvq_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+}
+
+// The segments of one instance: a block gate alone, or a run of consecutive
+// diagonal gates (at most BATCH_RUN, at most MAX_RUN_PAIRS cross-Kerr).
+std::vector<BSeg> segments_of(const PoolView& p, int inst, const int* ids, int n) {
+  std::vector<BSeg> v;
+  int k = 0;
+  while (k < n) {
+    BSeg s;
+    memset(&s, 0, sizeof s);
+    s.inst = inst;
+    s.k0 = k;
+    const TypeDesc& t0 = p.types[p.op_type[ids[k]]];
+    if (!t0.diag) {
+      s.m = 1;
+      v.push_back(s);
+      ++k;
+      continue;
+    }
+    s.isdiag = 1;
+    while (k + s.m < n && s.m < BATCH_RUN) {
+      const int op = ids[k + s.m];
+      const TypeDesc& t = p.types[p.op_type[op]];
+      if (!t.diag) break;
+      if (t.diag == 4) {
+        if (s.npair == MAX_RUN_PAIRS) break;
+        s.pi[s.npair] = p.op_i[op];
+        s.pj[s.npair] = p.op_j[op];
+        ++s.npair;
+      }
+      s.diag[s.m] = t.diag;
+      s.gi[s.m] = p.op_i[op];
+      s.gj[s.m] = p.op_j[op];
+      ++s.m;
+    }
+    v.push_back(s);
+    k += s.m;
+  }
+  return v;
+}
+
+// Work items of one segment (or of a whole-sector pass when seg < 0).
+void items_of(const cvq_batch* b, int inst, int seg, const BSeg* sg, int kind, std::vector<BItem>& out, int& slot,
+              int slots_per_item) {
+  const SectorDev& S = b->S[inst];
+  const PoolView& p = b->pv[inst];
+  auto push = [&](int64_t a, int64_t e) {
+    BItem it;
+    it.kind = kind;
+    it.inst = inst;
+    it.seg = seg;
+    it.slot = slot;
+    slot += slots_per_item;
+    it.a = a;
+    it.b = e;
+    out.push_back(it);
+  };
+  if (kind != BI_GATE) {
+    for (int64_t x = 0; x < S.dim; x += b->tile) push(x, std::min<int64_t>(S.dim, x + b->tile));
+    return;
+  }
+  // the pool operator of this block gate
+  const int op = b->ids[(size_t)b->inst[inst].ids_off + sg->k0];
+  const TypeDesc& t = p.types[p.op_type[op]];
+  if (S.kind == CVQ_BKC) {
+    const int nm = t.single ? 1 : 2;
+    int64_t items = 1, per_orbit = 1;
+    for (int r = 0; r < S.L - nm; ++r) items *= S.D;
+    for (int r = 0; r < nm; ++r) per_orbit *= S.D;
+    per_orbit = std::max<int64_t>(1, per_orbit / 2);
+    const int64_t orbits = std::max<int64_t>(NTHREADS, b->tile / per_orbit);
+    for (int64_t u = 0; u < items; u += orbits) push(u, std::min(items, u + orbits));
+  } else {
+    // consecutive equal-work chunks until the item holds about `tile` amplitudes
+    std::vector<int4> ch(t.nchunks);
+    if (t.nchunks) cudaMemcpy(ch.data(), p.P.chunks + t.chunk_base, sizeof(int4) * t.nchunks, cudaMemcpyDeviceToHost);
+    int64_t acc = 0, c0 = 0;
+    for (int c = 0; c < t.nchunks; ++c) {
+      acc += (int64_t)(ch[c].z - ch[c].y) * (ch[c].x + 1);
+      if (acc >= b->tile || c + 1 == t.nchunks) {
+        push(c0, c + 1);
+        c0 = c + 1;
+        acc = 0;
+      }
+    }
+  }
+}
+
+int build_plan(cvq_batch* b) {
+  drop_graph(b);
+  if (b->plan) cudaFree(b->plan);
+  b->plan = nullptr;
+  const int n = b->n;
+  // instance offsets into ids / theta / grad
+  int off = 0;
+  std::vector<std::vector<BSeg>> segs(n);
+  int smax = 0;
+  for (int i = 0; i < n; ++i) {
+    b->inst[i].ids_off = off;
+    b->inst[i].theta_off = off;
+    b->inst[i].psi0 = b->psi0[i];
+    if (b->n_ops[i] > 0) segs[i] = segments_of(b->pv[i], i, b->ids.data() + off, b->n_ops[i]);
+    smax = std::max(smax, (int)segs[i].size());
+    off += std::max(b->n_ops[i], 0);
+  }
+  b->n_theta = off;
+  std::vector<BSeg> seg_all;
+  std::vector<std::vector<int>> seg_id(n);
+  for (int i = 0; i < n; ++i)
+    for (auto& s : segs[i]) {
+      seg_id[i].push_back((int)seg_all.size());
+      seg_all.push_back(s);
+    }
+  // layers: conversion, smax forward, matvec, smax reverse
+  std::vector<std::vector<BItem>> layers(2 * smax + 2);
+  std::vector<char> adj(2 * smax + 2, 0);
+  std::vector<BRed> red;
+  int slot = 0, nosl = 0;
+  for (int i = 0; i < n; ++i)
+    if (b->n_ops[i] >= 0) items_of(b, i, -1, nullptr, BI_TODF, layers[0], nosl, 0);
+  for (int l = 0; l < smax; ++l)
+    for (int i = 0; i < n; ++i) {
+      if (l >= (int)segs[i].size()) continue;
+      const BSeg& s = segs[i][l];
+      items_of(b, i, seg_id[i][l], &s, s.isdiag ? BI_DIAG : BI_GATE, layers[1 + l], nosl, 0);
+    }
+  for (int i = 0; i < n; ++i) {
+    if (b->n_ops[i] < 0) continue;
+    const int s0 = slot;
+    const size_t before = layers[smax + 1].size();
+    items_of(b, i, -1, nullptr, BI_APPLYH, layers[smax + 1], slot, 1);
+    red.push_back({i, 1, s0, (int)(layers[smax + 1].size() - before), 1});
+  }
+  for (int r = 0; r < smax; ++r) {
+    const int l = smax + 2 + r;
+    adj[l] = 1;
+    for (int i = 0; i < n; ++i) {
+      const int ns = (int)segs[i].size();
+      if (r >= ns) continue;
+      const BSeg& s = segs[i][ns - 1 - r];
+      const int s0 = slot;
+      const size_t before = layers[l].size();
+      items_of(b, i, seg_id[i][ns - 1 - r], &s, s.isdiag ? BI_DIAG : BI_GATE, layers[l], slot, s.m);
+      const int cnt = (int)(layers[l].size() - before);
+      for (int q = 0; q < s.m; ++q) red.push_back({b->inst[i].theta_off + s.k0 + q, 0, s0 + q, cnt, s.m});
+    }
+  }
+  std::vector<int2> gates;
+  for (int i = 0; i < n; ++i)
+    for (auto& s : segs[i])
+      if (!s.isdiag) gates.push_back(make_int2(i, s.k0));
+  std::vector<BItem> items;
+  b->layer_off.clear();
+  b->layer_n.clear();
+  b->layer_adj.clear();
+  for (size_t l = 0; l < layers.size(); ++l) {
+    b->layer_off.push_back((int)items.size());
+    b->layer_n.push_back((int)layers[l].size());
+    b->layer_adj.push_back(adj[l]);
+    items.insert(items.end(), layers[l].begin(), layers[l].end());
+  }
+  b->n_items = (int)items.size();
+  b->n_red = (int)red.size();
+  b->n_gates = (int)gates.size();
+  // one device allocation for the whole plan
+  const size_t s_ids = a256(sizeof(int) * std::max<size_t>(1, b->ids.size()));
+  const size_t s_seg = a256(sizeof(BSeg) * std::max<size_t>(1, seg_all.size()));
+  const size_t s_it = a256(sizeof(BItem) * std::max<size_t>(1, items.size()));
+  const size_t s_red = a256(sizeof(BRed) * std::max<size_t>(1, red.size()));
+  const size_t s_g = a256(sizeof(int2) * std::max<size_t>(1, gates.size()));
+  const size_t s_c = a256(sizeof(int) * layers.size());
+  const size_t s_p = a256(sizeof(double) * std::max(1, slot));
+  BCUDA(cudaMalloc(&b->plan, s_ids + s_seg + s_it + s_red + s_g + s_c + s_p), "cudaMalloc of the batch plan");
+  char* q = (char*)b->plan;
+  b->ids_d = (int*)q;
+  q += s_ids;
+  b->segs_d = (BSeg*)q;
+  q += s_seg;
+  b->items_d = (BItem*)q;
+  q += s_it;
+  b->red_d = (BRed*)q;
+  q += s_red;
+  b->gates_d = (int2*)q;
+  q += s_g;
+  b->counters_d = (int*)q;
+  q += s_c;
+  b->partial_d = (double*)q;
+  if (!b->ids.empty()) BCUDA(cudaMemcpy(b->ids_d, b->ids.data(), sizeof(int) * b->ids.size(), cudaMemcpyHostToDevice), "copy ids");
+  if (!seg_all.empty()) BCUDA(cudaMemcpy(b->segs_d, seg_all.data(), sizeof(BSeg) * seg_all.size(), cudaMemcpyHostToDevice), "copy segments");
+  if (!items.empty()) BCUDA(cudaMemcpy(b->items_d, items.data(), sizeof(BItem) * items.size(), cudaMemcpyHostToDevice), "copy items");
+  if (!red.empty()) BCUDA(cudaMemcpy(b->red_d, red.data(), sizeof(BRed) * red.size(), cudaMemcpyHostToDevice), "copy reductions");
+  if (!gates.empty()) BCUDA(cudaMemcpy(b->gates_d, gates.data(), sizeof(int2) * gates.size(), cudaMemcpyHostToDevice), "copy gates");
+  BCUDA(cudaMemcpy(b->inst_d, b->inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice), "copy instances");
+  b->have = true;
+  return CVQ_OK;
+}
+
+int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
+  drop_graph(b);
+  cudaStream_t st = b->cap;
+  BCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = cudaMemsetAsync(b->counters_d, 0, sizeof(int) * b->layer_n.size(), st);
+  if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->ids_d, theta, st);
+  const int grid = b->sms * b->ctas_per_sm;
+  for (size_t l = 0; l < b->layer_n.size() && e == cudaSuccess; ++l)
+    e = launch_batch_layer(b->kind, b->layer_adj[l] != 0, grid, b->smem, b->inst_d, b->segs_d,
+                           b->items_d + b->layer_off[l], b->layer_n[l], b->counters_d + l, b->ids_d, theta,
+                           b->partial_d, st);
+  if (e == cudaSuccess) e = launch_batch_reduce(b->red_d, b->n_red, b->partial_d, E, grad, st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_err(e != cudaSuccess ? e : e2, "capture of the batch evaluation");
+  }
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return cuda_err(e, "graph instantiation");
+  }
+  b->g_theta = theta;
+  b->g_E = E;
+  b->g_grad = grad;
+  return CVQ_OK;
+}
+
+}  // namespace
+
+extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool* const* pools, int n_inst, int n_max,
+                                cvq_batch** out) {
+  if (!out || !sectors || !pools) return errf(CVQ_EINVAL, "null argument");
+  *out = nullptr;
+  if (n_inst < 1 || n_inst > 4096) return errf(CVQ_EINVAL, "n_inst %d outside [1, 4096]", n_inst);
+  if (n_max < 0 || n_max > MAX_GATES) return errf(CVQ_EINVAL, "n_max %d outside [0, %d]", n_max, MAX_GATES);
+  cvq_batch* b = new (std::nothrow) cvq_batch;
+  if (!b) return errf(CVQ_ENOMEM, "host allocation");
+  b->n = n_inst;
+  b->n_max = n_max;
+  b->pv.resize(n_inst);
+  b->S.resize(n_inst);
+  b->inst.resize(n_inst);
+  size_t total = 0;
+  std::vector<size_t> offs(n_inst);
+  size_t smem = std::max(sizeof(HSmem), (size_t)(LMAX * DMAX + MAX_RUN_PAIRS * DMAX * DMAX) * sizeof(cdf));
+  for (int i = 0; i < n_inst; ++i) {
+    PoolView& p = b->pv[i];
+    int rc = internal_pool_host(pools[i], &p.sec, &p.types, &p.ntypes, &p.op_type, &p.op_i, &p.op_j, &p.K, &p.P,
+                                &p.ustride, &p.ops_dev);
+    if (rc || p.sec != sectors[i]) {
+      delete b;
+      return rc ? rc : errf(CVQ_EINVAL, "pool %d belongs to another sector", i);
+    }
+    const SectorDev* S = internal_sector(sectors[i]);
+    if (!S) {
+      delete b;
+      return errf(CVQ_EINVAL, "null sector %d", i);
+    }
+    if (i == 0) {
+      b->kind = S->kind;
+      b->device = internal_sector_device(sectors[i]);
+    } else if (S->kind != b->kind || internal_sector_device(sectors[i]) != b->device) {
+      delete b;
+      return errf(CVQ_EINVAL, "instance %d differs in sector kind or device", i);
+    }
+    b->S[i] = *S;
+    for (int t = 0; t < p.ntypes; ++t)
+      if (!p.types[t].diag) smem = std::max(smem, gate_smem_bytes(p.types[t], S->kind));
+    offs[i] = total;
+    total += 2 * a256(sizeof(cdf) * (size_t)S->dim) + a256(sizeof(cdf) * (size_t)std::max(n_max, 1) * p.ustride);
+  }
+  if (smem > 200 * 1024) {
+    delete b;
+    return errf(CVQ_EINVAL, "gate tables need %zu bytes of shared memory", smem);
+  }
+  b->smem = smem;
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, b->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&b->state, total);
+  if (e == cudaSuccess) e = cudaMalloc(&b->inst_d, sizeof(BInst) * n_inst);
+  if (e == cudaSuccess) e = set_batch_smem_limit((int)smem);
+  if (e != cudaSuccess) {
+    cvq_batch_destroy(b);
+    return cuda_err(e, "batch allocation");
+  }
+  b->sms = prop.multiProcessorCount;
+  for (int i = 0; i < n_inst; ++i) {
+    BInst& I = b->inst[i];
+    memset(&I, 0, sizeof I);
+    I.S = b->S[i];
+    I.P = b->pv[i].P;
+    I.ops = b->pv[i].ops_dev;
+    char* q = (char*)b->state + offs[i];
+    I.psi = (cdf*)q;
+    q += a256(sizeof(cdf) * (size_t)I.S.dim);
+    I.lam = (cdf*)q;
+    q += a256(sizeof(cdf) * (size_t)I.S.dim);
+    I.U = (cdf*)q;
+    I.ustride = b->pv[i].ustride;
+  }
+  *out = b;
+  return CVQ_OK;
+}
+
+extern "C" void cvq_batch_destroy(cvq_batch* b) {
+  if (!b) return;
+  drop_graph(b);
+  if (b->plan) cudaFree(b->plan);
+  if (b->state) cudaFree(b->state);
+  if (b->inst_d) cudaFree(b->inst_d);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+extern "C" int cvq_batch_set_ansatz(cvq_batch* b, const int* n_ops, const int* op_ids, const cvq_c128* const* psi0) {
+  if (!b || !n_ops || !psi0) return errf(CVQ_EINVAL, "null argument");
+  size_t tot = 0;
+  for (int i = 0; i < b->n; ++i) {
+    if (n_ops[i] < -1 || n_ops[i] > b->n_max) return errf(CVQ_EINVAL, "n_ops[%d] = %d outside [-1, %d]", i, n_ops[i], b->n_max);
+    if (n_ops[i] >= 0 && !psi0[i]) return errf(CVQ_EINVAL, "psi0[%d] is NULL", i);
+    tot += std::max(n_ops[i], 0);
+  }
+  if (tot > 0 && !op_ids) return errf(CVQ_EINVAL, "null op_ids");
+  size_t o = 0;
+  for (int i = 0; i < b->n; ++i)
+    for (int k = 0; k < std::max(n_ops[i], 0); ++k, ++o)
+      if (op_ids[o] < 0 || op_ids[o] >= b->pv[i].K) return errf(CVQ_EINVAL, "op id %d of instance %d outside its pool", op_ids[o], i);
+  b->n_ops.assign(n_ops, n_ops + b->n);
+  b->ids.assign(op_ids, op_ids + tot);
+  b->psi0.resize(b->n);
+  for (int i = 0; i < b->n; ++i) b->psi0[i] = (const double2*)psi0[i];
+  return build_plan(b);
+}
+
+extern "C" int cvq_batch_set_schedule(cvq_batch* b, int64_t tile, int ctas_per_sm) {
+  if (!b) return errf(CVQ_EINVAL, "null argument");
+  if (tile < NTHREADS || tile > ((int64_t)1 << 30)) return errf(CVQ_EINVAL, "tile %lld outside [256, 2^30]", (long long)tile);
+  if (ctas_per_sm < 1 || ctas_per_sm > 2) return errf(CVQ_EINVAL, "ctas_per_sm must be 1 or 2");
+  b->tile = tile;
+  b->ctas_per_sm = ctas_per_sm;
+  return b->have ? build_plan(b) : CVQ_OK;
+}
+
+extern "C" int cvq_batch_energy_and_grad(cvq_batch* b, const double* theta_dev, double* E_dev, double* grad_dev,
+                                         void* stream) {
+  if (!b || !E_dev) return errf(CVQ_EINVAL, "null argument");
+  if (!b->have) return errf(CVQ_EINVAL, "cvq_batch_set_ansatz has not been called");
+  if (b->n_theta > 0 && (!theta_dev || !grad_dev)) return errf(CVQ_EINVAL, "null theta / grad");
+  if (!b->exec || b->g_theta != theta_dev || b->g_E != E_dev || b->g_grad != grad_dev)
+    if (int rc = capture(b, theta_dev, E_dev, grad_dev)) return rc;
+  BCUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "graph launch");
+  return CVQ_OK;
+}
+
+extern "C" int cvq_batch_info(const cvq_batch* b, int* kernels_per_eval, int* items, int* layers, int64_t* n_params) {
+  if (!b) return errf(CVQ_EINVAL, "null argument");
+  int nk = 0;
+  for (int n : b->layer_n) nk += n > 0;
+  if (kernels_per_eval) *kernels_per_eval = nk + (b->n_gates > 0) + (b->n_red > 0);
+  if (items) *items = b->n_items;
+  if (layers) *layers = (int)b->layer_n.size();
+  if (n_params) *n_params = b->n_theta;
+  return CVQ_OK;
+}

@@ -252,6 +252,51 @@ struct DiagRunArg {
   cdf TP[MAX_RUN_PAIRS][DMAX * DMAX];
 };
 
+// ------------------------------------------------------------- batched engine
+
+constexpr int BATCH_RUN = 8;  // diagonal gates per run in the batched engine
+enum BItemKind { BI_TODF = 0, BI_GATE = 1, BI_DIAG = 2, BI_APPLYH = 3 };
+
+// One instance of a batch: its sector, pool tables and device buffers.
+struct BInst {
+  SectorDev S;
+  PoolDev P;
+  const GateArg* ops;   // per pool operator (modes and generator structure)
+  cdf *psi, *lam, *U;   // df state, adjoint state, block unitaries (n_max x ustride)
+  const double2* psi0;  // reference state (complex128)
+  int ustride, ids_off, theta_off;
+};
+
+// One segment of one instance's ansatz: a block gate (m = 1) or a run of m
+// diagonal gates; the run's gate list uses the field names of DiagRunArg.
+struct BSeg {
+  int inst, k0, m, isdiag, npair;
+  int diag[BATCH_RUN], gi[BATCH_RUN], gj[BATCH_RUN];
+  int pi[MAX_RUN_PAIRS], pj[MAX_RUN_PAIRS];
+};
+
+// One work item: a range [a, b) of chunks (BH gate), orbits (BKC gate) or
+// sector indices (everything else) of one segment or instance; its partial
+// sums go to partial[slot ...].
+struct BItem {
+  int kind, inst, seg, slot;
+  int64_t a, b;
+};
+
+// One output of the final reduction.
+struct BRed {
+  int out, is_energy, slot0, count, stride;
+};
+
+cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, const int* ids, const double* theta,
+                               cudaStream_t st);
+cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const BInst* insts, const BSeg* segs,
+                               const BItem* items, int nitems, int* counter, const int* ids, const double* theta,
+                               double* partial, cudaStream_t st);
+cudaError_t set_batch_smem_limit(int bytes);
+cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, double* E, double* grad,
+                                cudaStream_t st);
+
 // Pool indices screened by one launch (passed by value).
 struct SubsetArg {
   int n;

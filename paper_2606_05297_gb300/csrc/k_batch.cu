@@ -1,0 +1,233 @@
+// k_batch.cu -- batched engine: the energy and adjoint gradient of many
+// Hamiltonian instances (sectors of uneven size, each with its own pool and
+// ansatz) evaluated together, as in a U/J sweep.
+//
+// One evaluation is a fixed sequence of layers: the conversion of every
+// instance's reference state, one layer per ansatz segment (block gate, or
+// run of diagonal gates) forward, the matvec lambda = H psi with the energy,
+// one layer per segment in reverse with the gradient partials, and a
+// fixed-order reduction.  Each layer is one persistent launch (a fixed grid
+// of CTAs) that pulls (instance, tile) work items from a device counter, so
+// small and large instances share the GPU within a layer; the layers follow
+// one another on the stream, which orders them without any in-kernel wait.
+// The host captures the whole sequence in a CUDA graph once per ansatz
+// structure and replays it for every theta.
+//
+// Work items are disjoint ranges of one segment of one instance (BH gates:
+// ranges of the pool type's equal-work chunks; everything else: ranges of
+// sector indices or orbits).  Each item leaves its partial sums in its own
+// slots, so every result is independent of which CTA ran which item.
+#include "cvq_internal.cuh"
+#include "k_diag_impl.cuh"
+#include "k_gate_impl.cuh"
+#include "k_ham_impl.cuh"
+
+namespace cvq {
+
+__global__ void __launch_bounds__(128) k_batch_build(const BInst* __restrict__ insts, const int2* __restrict__ gates,
+                                                     int ngates, const int* __restrict__ ids,
+                                                     const double* __restrict__ theta) {
+  const int g = blockIdx.x;
+  if (g >= ngates) return;
+  const int2 ik = gates[g];
+  const BInst& I = insts[ik.x];
+  const int op = ids[I.ids_off + ik.y];
+  const TypeDesc& t = I.ops[op].t;
+  if (t.diag) return;
+  __shared__ double2 ph[BMAX];
+  build_gate_unitaries(t, theta[I.theta_off + ik.y], I.P, I.U + (size_t)ik.y * I.ustride, ph);
+}
+
+// Shared state of one layer CTA.
+struct BShared {
+  SectorDev S;
+  TypeDesc t;
+  BSeg seg;
+  int item;
+  int gi, gj;
+};
+
+__device__ __forceinline__ void copy_words(void* dst, const void* src, int bytes) {
+  int* d = reinterpret_cast<int*>(dst);
+  const int* s = reinterpret_cast<const int*>(src);
+  for (int e = threadIdx.x; e < bytes / 4; e += blockDim.x) d[e] = s[e];
+}
+
+// Phase tables of a diagonal run from theta, in FP64 (as the single-instance
+// path builds them on the host).
+__device__ __forceinline__ void diag_tables(const BSeg& sg, const SectorDev& S, const double* th, cdf (*T)[DMAX],
+                                            cdf (*TP)[DMAX * DMAX]) {
+  const int D = S.D;
+  for (int e = threadIdx.x; e < LMAX * DMAX; e += blockDim.x) {
+    const int r = e / DMAX, n = e % DMAX;
+    double ang = 0.0;
+    for (int q = 0; q < sg.m; ++q) {
+      const int dg = sg.diag[q];
+      if (dg == 4 || sg.gi[q] != r) continue;
+      const int f = (dg == 1) ? n * n : (dg == 2) ? n * (n - 1) : n;
+      ang += th[q] * (double)f;
+    }
+    double s, c;
+    sincos(ang, &s, &c);
+    T[r][n] = make_cdf(df_from_double(c), df_from_double(s));
+  }
+  int p = 0;
+  for (int q = 0; q < sg.m; ++q) {
+    if (sg.diag[q] != 4) continue;
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+      const int u = e / D, v = e % D;
+      double s, c;
+      sincos(th[q] * (double)(u * v), &s, &c);
+      TP[p][e] = make_cdf(df_from_double(c), df_from_double(s));
+    }
+    ++p;
+  }
+}
+
+// One layer: items [0, nitems) of the layer's list, claimed in order from *counter.
+template <int KIND, bool ADJ>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    k_batch_layer(const BInst* __restrict__ insts, const BSeg* __restrict__ segs, const BItem* __restrict__ items,
+                  int nitems, int* counter, const int* __restrict__ ids, const double* __restrict__ theta,
+                  double* __restrict__ partial) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ BShared sh;
+  __shared__ int64_t G64[LMAX][DMAX + 1];
+  __shared__ int32_t G32[LMAX][DMAX + 1];
+  for (;;) {
+    if (threadIdx.x == 0) sh.item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int k = sh.item;
+    if (k >= nitems) break;
+    const BItem it = items[k];
+    const BInst& I = insts[it.inst];
+    copy_words(&sh.S, &I.S, sizeof(SectorDev));
+    if (it.kind != BI_TODF && it.kind != BI_APPLYH) copy_words(&sh.seg, &segs[it.seg], sizeof(BSeg));
+    __syncthreads();
+    const SectorDev& S = sh.S;
+    if (KIND == CVQ_BH) {
+      load_G(G64, S);
+      load_G(G32, S);
+    }
+    if (it.kind == BI_TODF) {
+      __syncthreads();
+      for (int64_t x = it.a + threadIdx.x; x < it.b; x += NTHREADS) {
+        const double2 v = I.psi0[x];
+        I.psi[x] = make_cdf(df_from_double(v.x), df_from_double(v.y));
+      }
+    } else if (it.kind == BI_APPLYH) {
+      HSmem& H = *reinterpret_cast<HSmem*>(smem);
+      load_htabs(H, S);
+      __syncthreads();
+      dfacc eacc;
+      acc_zero(eacc);
+      apply_H_range<KIND>(S, G64, H, I.psi, I.lam, it.a + threadIdx.x, it.b, NTHREADS, eacc);
+      const double s = block_sum(acc_to_double(eacc));
+      if (threadIdx.x == 0) partial[it.slot] = s;
+    } else if (it.kind == BI_DIAG) {
+      cdf(*T)[DMAX] = reinterpret_cast<cdf(*)[DMAX]>(smem);
+      cdf(*TP)[DMAX * DMAX] = reinterpret_cast<cdf(*)[DMAX * DMAX]>(smem + sizeof(cdf) * LMAX * DMAX);
+      const BSeg& sg = sh.seg;
+      diag_tables(sg, S, theta + I.theta_off + sg.k0, T, TP);
+      __syncthreads();
+      dfacc acc[BATCH_RUN];
+#pragma unroll
+      for (int q = 0; q < BATCH_RUN; ++q) acc_zero(acc[q]);
+      diag_run_range<KIND, ADJ, BATCH_RUN>(S, G64, T, TP, sg, I.psi, I.psi, I.lam, it.a + threadIdx.x, it.b, NTHREADS,
+                                           acc);
+      if (ADJ) {
+#pragma unroll
+        for (int q = 0; q < BATCH_RUN; ++q) {
+          if (q < sg.m) {
+            const double s = block_sum(acc_to_double(acc[q]));
+            if (threadIdx.x == 0) partial[it.slot + q] = s;
+          }
+        }
+      }
+    } else {  // BI_GATE
+      if (threadIdx.x == 0) {
+        const GateArg& ga = I.ops[ids[I.ids_off + sh.seg.k0]];
+        sh.gi = ga.i;
+        sh.gj = ga.t.single ? -1 : ga.j;
+      }
+      copy_words(&sh.t, &I.ops[ids[I.ids_off + segs[it.seg].k0]].t, sizeof(TypeDesc));
+      __syncthreads();
+      const TypeDesc& t = sh.t;
+      const GateSmem m = gate_smem(smem, t);
+      stage_gate<ADJ>(m, t, I.U + (size_t)sh.seg.k0 * I.ustride, I.P);
+      __syncthreads();
+      dfacc gacc;
+      acc_zero(gacc);
+      if (KIND == CVQ_BKC) {
+        if (t.realu)
+          bkc_gate_range<ADJ, true>(S, sh.gi, sh.gj, t, m, it.a + threadIdx.x, it.b, NTHREADS, I.psi, I.psi, I.lam,
+                                    gacc);
+        else
+          bkc_gate_range<ADJ, false>(S, sh.gi, sh.gj, t, m, it.a + threadIdx.x, it.b, NTHREADS, I.psi, I.psi, I.lam,
+                                     gacc);
+      } else {
+        for (int64_t c = it.a; c < it.b; ++c) {
+          const int4 ch = I.P.chunks[t.chunk_base + c];
+          if (t.realu) bh_gate_chunk<ADJ, true>(S, G32, sh.gi, sh.gj, t, m, ch, I.psi, I.psi, I.lam, gacc);
+          else bh_gate_chunk<ADJ, false>(S, G32, sh.gi, sh.gj, t, m, ch, I.psi, I.psi, I.lam, gacc);
+        }
+      }
+      if (ADJ) {
+        const double s = block_sum(acc_to_double(gacc));
+        if (threadIdx.x == 0) partial[it.slot] = s;
+      }
+    }
+    __syncthreads();  // the shared tables and item number are reused by the next item
+  }
+}
+
+// out = scale * sum of `count` partials from slot0 with `stride`, in order.
+__global__ void k_batch_reduce(const BRed* __restrict__ red, int n, const double* __restrict__ partial,
+                               double* __restrict__ E, double* __restrict__ grad) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const BRed d = red[r];
+  double v = 0.0;
+  for (int q = 0; q < d.count; ++q) v += partial[(size_t)d.slot0 + (size_t)q * d.stride];
+  if (d.is_energy) E[d.out] = v;
+  else grad[d.out] = 2.0 * v;
+}
+
+cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, const int* ids, const double* theta,
+                               cudaStream_t st) {
+  if (ngates <= 0) return cudaSuccess;
+  k_batch_build<<<ngates, 128, 0, st>>>(insts, gates, ngates, ids, theta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const BInst* insts, const BSeg* segs,
+                               const BItem* items, int nitems, int* counter, const int* ids, const double* theta,
+                               double* partial, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  if (kind == CVQ_BH) {
+    if (adj) k_batch_layer<CVQ_BH, true><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, partial);
+    else k_batch_layer<CVQ_BH, false><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, partial);
+  } else {
+    if (adj) k_batch_layer<CVQ_BKC, true><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, partial);
+    else k_batch_layer<CVQ_BKC, false><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, partial);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t set_batch_smem_limit(int bytes) {
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(k_batch_layer<CVQ_BH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_layer<CVQ_BH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_layer<CVQ_BKC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_layer<CVQ_BKC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, double* E, double* grad,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_batch_reduce<<<(n + 127) / 128, 128, 0, st>>>(red, n, partial, E, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace cvq

@@ -233,6 +233,127 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
   }
 }
 
+// ------------------------------------------------------------ gate pieces
+
+// Shared-memory carve-out of one gate: its block unitaries, block list,
+// members, generator factors (reverse only), then the per-thread staging
+// columns of amplitudes and sector indices.
+struct GateSmem {
+  cdf* U;
+  BlockDesc* B;
+  int2* M;
+  float2* F;
+  cdf* stg;
+  int64_t* sx;
+};
+
+__device__ __forceinline__ GateSmem gate_smem(char* smem, const TypeDesc& t) {
+  GateSmem m;
+  m.U = reinterpret_cast<cdf*>(smem);
+  m.B = reinterpret_cast<BlockDesc*>(m.U + t.nu);
+  m.M = reinterpret_cast<int2*>(m.B + t.nblocks);
+  m.F = reinterpret_cast<float2*>(m.M + DMAX * DMAX);
+  m.stg = reinterpret_cast<cdf*>(smem + gate_tables_bytes(t));
+  m.sx = reinterpret_cast<int64_t*>(m.stg + (size_t)t.bmax * NTHREADS);
+  return m;
+}
+
+// Copies one gate's tables into shared memory (the caller synchronises).
+template <bool ADJ>
+__device__ __forceinline__ void stage_gate(const GateSmem& m, const TypeDesc& t, const cdf* U, const PoolDev& P) {
+  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) m.U[e] = U[e];
+  for (int e = threadIdx.x; e < t.nblocks; e += blockDim.x) m.B[e] = P.blk[t.blk_base + e];
+  for (int e = threadIdx.x; e < t.nmem; e += blockDim.x) m.M[e] = P.mem[t.mem_base + e];
+  if (ADJ)
+    for (int e = threadIdx.x; e < t.nf; e += blockDim.x) m.F[e] = P.F[t.f_base + e];
+}
+
+// Kitaev chain: orbits it = first, first + step, ... < end of the gate on
+// modes (gi, gj) (gj < 0: single-mode).
+template <bool ADJ, bool REALU>
+__device__ __forceinline__ void bkc_gate_range(const SectorDev& S, int gi, int gj, const TypeDesc& t,
+                                               const GateSmem& m, int64_t first, int64_t end, int64_t step,
+                                               const cdf* src, cdf* dst, cdf* lam, dfacc& gacc) {
+  const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
+  const int64_t items = bkc_items(S, gj >= 0 ? 2 : 1);
+  BkcIdx idx;
+  idx.si = S.stride[gi];
+  idx.sj = (gj >= 0) ? S.stride[gj] : 0;
+  for (int64_t it = first; it < end; it += step) {
+    int cls;
+    bkc_orbit(S, gi, gj, it, items, idx.f0, cls);
+    for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
+      const BlockDesc bd = m.B[bi];
+      apply_block<ADJ, REALU, false>(bd.size, m.U + bd.u_off, m.M + bd.mem_off, m.F + bd.f_off, cpr, cpi, idx, src,
+                                     dst, lam, m.stg, m.sx, gacc);
+    }
+  }
+}
+
+// Bose-Hubbard: one equal-work chunk (class M, orbits [u0, u1)) of the
+// two-mode gate on (gi, gj); each thread takes a contiguous run of the
+// chunk's orbits and steps from one outer composition to the next instead of
+// unranking every orbit.
+template <bool ADJ, bool REALU>
+__device__ __forceinline__ void bh_gate_chunk(const SectorDev& S, const int32_t (*Gs)[DMAX + 1], int gi, int gj,
+                                              const TypeDesc& t, const GateSmem& m, int4 ch, const cdf* src,
+                                              cdf* dst, cdf* lam, dfacc& gacc) {
+  const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
+  const int lo = min(gi, gj), hi = max(gi, gj);
+  const int M = ch.x;
+  const int run = (ch.z - ch.y + NTHREADS - 1) / NTHREADS;
+  int u = ch.y + threadIdx.x * run;
+  const int uend = min(u + run, ch.z);
+  if (u >= uend) return;
+  uint64_t wo = bh_unrank<int32_t>(u, S.L - 2, S.N - M, Gs);
+  for (;;) {
+    const uint64_t w0 = spread2(wo, lo, hi) | ((uint64_t)M << (4 * gj));
+    const BhIdxT<int32_t> idx = bh_idx_of<int32_t>(S, Gs, gi, gj, w0);
+    for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
+      const BlockDesc bd = m.B[bi];
+      apply_block<ADJ, REALU, true>(bd.size, m.U + bd.u_off, m.M + bd.mem_off, m.F + bd.f_off, cpr, cpi, idx, src,
+                                    dst, lam, m.stg, m.sx, gacc);
+    }
+    if (++u >= uend) break;
+    comp_next(wo, S.L - 2);
+  }
+}
+
+// U_g = (W V) exp(i theta Lambda) (W V)^dag for every block of one gate,
+// formed in FP64 by the calling CTA and stored as df complex.  Every
+// generator here has phases that are multiples of pi/2 and a zero-diagonal
+// tridiagonal block, so exp(theta A) has purely real entries (real
+// generator) or real entries at even k - l and imaginary ones at odd k - l;
+// the other component is zero up to rounding and is set to zero.
+__device__ __forceinline__ void build_gate_unitaries(const TypeDesc& t, double th, const PoolDev& P, cdf* Ug,
+                                                     double2* ph) {
+  for (int bi = 0; bi < t.nblocks; ++bi) {
+    const BlockDesc bd = P.blk[t.blk_base + bi];
+    const int b = bd.size;
+    if (threadIdx.x < b) {
+      double s, c;
+      sincos(th * P.lam[t.lam_base + bd.ev_off + threadIdx.x], &s, &c);
+      ph[threadIdx.x] = make_double2(c, s);
+    }
+    __syncthreads();
+    const double2* Vb = reinterpret_cast<const double2*>(P.V) + t.v_base + bd.u_off;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+      const int k = e / b, l = e - k * b;
+      double re = 0.0, im = 0.0;
+      for (int q = 0; q < b; ++q) {
+        const double2 vk = Vb[k * b + q], vl = Vb[l * b + q], p = ph[q];
+        const double xr = vk.x * p.x - vk.y * p.y, xi = vk.x * p.y + vk.y * p.x;  // vk p
+        re += xr * vl.x + xi * vl.y;                                               // * conj(vl)
+        im += xi * vl.x - xr * vl.y;
+      }
+      if (t.realu || ((k - l) & 1) == 0) im = 0.0;
+      else re = 0.0;
+      Ug[bd.u_off + e] = make_cdf(df_from_double(re), df_from_double(im));
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ kernel
 
 template <int KIND, bool ADJ, bool REALU>
@@ -243,62 +364,18 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   __shared__ int32_t Gs[LMAX][DMAX + 1];  // BH ranks fit in 32 bits for L, D <= 16
   if (KIND == CVQ_BH) load_G(Gs, S);
   const TypeDesc& t = g.t;
-  cdf* sU = reinterpret_cast<cdf*>(smem);
-  BlockDesc* sB = reinterpret_cast<BlockDesc*>(sU + t.nu);
-  int2* sM = reinterpret_cast<int2*>(sB + t.nblocks);
-  float2* sF = reinterpret_cast<float2*>(sM + DMAX * DMAX);
-  cdf* stg = reinterpret_cast<cdf*>(smem + gate_tables_bytes(t));
-  int64_t* sx = reinterpret_cast<int64_t*>(stg + (size_t)t.bmax * NTHREADS);
-  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) sU[e] = g.U[e];
-  for (int e = threadIdx.x; e < t.nblocks; e += blockDim.x) sB[e] = P.blk[t.blk_base + e];
-  for (int e = threadIdx.x; e < t.nmem; e += blockDim.x) sM[e] = P.mem[t.mem_base + e];
-  if (ADJ)
-    for (int e = threadIdx.x; e < t.nf; e += blockDim.x) sF[e] = P.F[t.f_base + e];
+  const GateSmem m = gate_smem(smem, t);
+  stage_gate<ADJ>(m, t, g.U, P);
   __syncthreads();
-  const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
   const int j = t.single ? -1 : g.j;
   dfacc gacc;
   acc_zero(gacc);
   if (KIND == CVQ_BKC) {
-    const int64_t items = bkc_items(S, t.single ? 1 : 2);
-    BkcIdx idx;
-    idx.si = S.stride[g.i];
-    idx.sj = (j >= 0) ? S.stride[j] : 0;
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-         it += (int64_t)gridDim.x * blockDim.x) {
-      int cls;
-      bkc_orbit(S, g.i, j, it, items, idx.f0, cls);
-      for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
-        const BlockDesc bd = sB[bi];
-        apply_block<ADJ, REALU, false>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src, dst,
-                                       lam, stg, sx, gacc);
-      }
-    }
+    bkc_gate_range<ADJ, REALU>(S, g.i, j, t, m, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                               bkc_items(S, t.single ? 1 : 2), (int64_t)gridDim.x * blockDim.x, src, dst, lam, gacc);
   } else {
-    // Equal-work chunks (class M, orbits [u0, u1)) built on the host; each
-    // thread takes a contiguous run of the chunk's orbits and steps from one
-    // outer composition to the next instead of unranking every orbit.
-    const int lo = min(g.i, j), hi = max(g.i, j);
-    for (int c = blockIdx.x; c < t.nchunks; c += gridDim.x) {
-      const int4 ch = P.chunks[t.chunk_base + c];
-      const int M = ch.x;
-      const int run = (ch.z - ch.y + NTHREADS - 1) / NTHREADS;
-      int u = ch.y + threadIdx.x * run;
-      const int uend = min(u + run, ch.z);
-      if (u >= uend) continue;
-      uint64_t wo = bh_unrank<int32_t>(u, S.L - 2, S.N - M, Gs);
-      for (;;) {
-        const uint64_t w0 = spread2(wo, lo, hi) | ((uint64_t)M << (4 * j));
-        const BhIdxT<int32_t> idx = bh_idx_of<int32_t>(S, Gs, g.i, j, w0);
-        for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
-          const BlockDesc bd = sB[bi];
-          apply_block<ADJ, REALU, true>(bd.size, sU + bd.u_off, sM + bd.mem_off, sF + bd.f_off, cpr, cpi, idx, src,
-                                        dst, lam, stg, sx, gacc);
-        }
-        if (++u >= uend) break;
-        comp_next(wo, S.L - 2);
-      }
-    }
+    for (int c = blockIdx.x; c < t.nchunks; c += gridDim.x)
+      bh_gate_chunk<ADJ, REALU>(S, Gs, g.i, j, t, m, P.chunks[t.chunk_base + c], src, dst, lam, gacc);
   }
   if (ADJ) {
     const double s = block_sum(acc_to_double(gacc));

@@ -11,6 +11,8 @@
 // writes them back in place.  Runs of consecutive diagonal gates (K, R, CK,
 // n(n-1)) are one streaming phase multiply.
 #include "cvq_internal.cuh"
+#include "k_diag_impl.cuh"
+#include "k_gate_impl.cuh"
 
 namespace cvq {
 
@@ -42,46 +44,15 @@ cudaError_t launch_from_df(int64_t dim, const cdf* src, double2* dst, cudaStream
 
 // ------------------------------------------------------------ build
 
-// U_g = (W V) exp(i theta Lambda) (W V)^dag for every block of every gate g of
-// the call (one CTA per gate), formed in FP64 and stored as df complex.
+// Block unitaries of every gate g of the call (one CTA per gate).
 __global__ void k_build(const __grid_constant__ BuildArgs a, const TypeDesc* __restrict__ types, PoolDev P,
                         cdf* __restrict__ U) {
   const int g = blockIdx.x;
   if (g >= a.n) return;
   const TypeDesc& t = types[a.type_of[g]];
   if (t.diag) return;  // diagonal gates are applied from per-run phase tables
-  const double th = a.theta[g];
-  cdf* Ug = U + (size_t)g * a.ustride;
   __shared__ double2 ph[BMAX];
-  for (int bi = 0; bi < t.nblocks; ++bi) {
-    const BlockDesc bd = P.blk[t.blk_base + bi];
-    const int b = bd.size;
-    if (threadIdx.x < b) {
-      double s, c;
-      sincos(th * P.lam[t.lam_base + bd.ev_off + threadIdx.x], &s, &c);
-      ph[threadIdx.x] = make_double2(c, s);
-    }
-    __syncthreads();
-    const double2* Vb = reinterpret_cast<const double2*>(P.V) + t.v_base + bd.u_off;
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-      const int k = e / b, l = e - k * b;
-      double re = 0.0, im = 0.0;
-      for (int m = 0; m < b; ++m) {
-        const double2 vk = Vb[k * b + m], vl = Vb[l * b + m], p = ph[m];
-        const double xr = vk.x * p.x - vk.y * p.y, xi = vk.x * p.y + vk.y * p.x;  // vk p
-        re += xr * vl.x + xi * vl.y;                                               // * conj(vl)
-        im += xi * vl.x - xr * vl.y;
-      }
-      // Every generator here has phases that are multiples of pi/2 and a
-      // zero-diagonal tridiagonal block, so exp(theta A) has purely real entries
-      // (real generator) or real entries at even k - l and imaginary ones at odd
-      // k - l; the other component is zero up to rounding and is set to zero.
-      if (t.realu || ((k - l) & 1) == 0) im = 0.0;
-      else re = 0.0;
-      Ug[bd.u_off + e] = make_cdf(df_from_double(re), df_from_double(im));
-    }
-    __syncthreads();
-  }
+  build_gate_unitaries(t, a.theta[g], P, U + (size_t)g * a.ustride, ph);
 }
 
 cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_dev, PoolDev P, cdf* U, cudaStream_t st) {
@@ -130,25 +101,9 @@ cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P,
   return launch_gate_impl<true>(S, g, P, psi, psi, lam, partial, st);
 }
 
-// complex df multiply-accumulate helpers for the diagonal runs
-__device__ __forceinline__ void cmac_full(dfacc& ar, dfacc& ai, cdf u, cdf v) {  // += u v
-  acc_mac(ar, re_of(u), re_of(v));
-  acc_mac(ai, re_of(u), im_of(v));
-  acc_mac(ar, df_neg(im_of(u)), im_of(v));
-  acc_mac(ai, im_of(u), re_of(v));
-}
-
-__device__ __forceinline__ void cmac_conj_full(dfacc& ar, dfacc& ai, cdf u, cdf v) {  // += conj(u) v
-  acc_mac(ar, re_of(u), re_of(v));
-  acc_mac(ai, re_of(u), im_of(v));
-  acc_mac(ar, im_of(u), im_of(v));
-  acc_mac(ai, df_neg(im_of(u)), re_of(v));
-}
-
 // ------------------------------------------------------------ diagonal runs
 
-// psi[x] *= prod_r T[r][n_r] * prod_p TP[p][n_i D + n_j] with the per-run phase
-// tables built on the host in FP64.  Modes with n_r = 0 contribute exactly 1.
+// One run per launch, phase tables built on the host in FP64.
 template <int KIND, bool ADJ>
 __global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ SectorDev S, const __grid_constant__ DiagRunArg a,
                                                        const cdf* src, cdf* dst, cdf* lam, double* partial) {
@@ -163,63 +118,8 @@ __global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ S
   dfacc acc[MAX_RUN];
 #pragma unroll
   for (int k = 0; k < MAX_RUN; ++k) acc_zero(acc[k]);
-  const int L = S.L, D = S.D;
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t w = (KIND == CVQ_BKC) ? bkc_unrank(x, S) : bh_unrank(x, L, S.N, Gs);
-    df pr = df_make(1.f, 0.f), pi = df_make(0.f, 0.f);
-    for (int r = 0; r < L; ++r) {
-      const int n = occ_get(w, r);
-      if (n == 0) continue;
-      const cdf t = T[r][n];
-      const df nr = df_add(df_mul(pr, re_of(t)), df_neg(df_mul(pi, im_of(t))));
-      const df ni = df_add(df_mul(pr, im_of(t)), df_mul(pi, re_of(t)));
-      pr = nr;
-      pi = ni;
-    }
-    for (int p = 0; p < a.npair; ++p) {
-      const int v = occ_get(w, a.pi[p]) * D + occ_get(w, a.pj[p]);
-      const cdf t = TP[p][v];
-      const df nr = df_add(df_mul(pr, re_of(t)), df_neg(df_mul(pi, im_of(t))));
-      const df ni = df_add(df_mul(pr, im_of(t)), df_mul(pi, re_of(t)));
-      pr = nr;
-      pi = ni;
-    }
-    if (!ADJ) {
-      const cdf v = src[x];
-      dfacc ar, ai;
-      acc_zero(ar);
-      acc_zero(ai);
-      cmac_full(ar, ai, make_cdf(pr, pi), v);
-      dst[x] = make_cdf(acc_get(ar), acc_get(ai));
-    } else {
-      const cdf ps = dst[x], la = lam[x];
-      // Re(conj(la) * i f ps) = f * (la.im ps.re - la.re ps.im)
-      dfacc c;
-      acc_zero(c);
-      acc_mac(c, im_of(la), re_of(ps));
-      acc_mac(c, df_neg(re_of(la)), im_of(ps));
-      const df cv = acc_get(c);
-#pragma unroll
-      for (int k = 0; k < MAX_RUN; ++k) {
-        if (k < a.m) {
-          const int ni = occ_get(w, a.gi[k]);
-          const int dg = a.diag[k];
-          const int f = (dg == 1) ? ni * ni : (dg == 2) ? ni * (ni - 1) : (dg == 3) ? ni : ni * occ_get(w, a.gj[k]);
-          if (f) acc_macf(acc[k], cv, (float)f);
-        }
-      }
-      const cdf ph = make_cdf(pr, pi);
-      dfacc r1, i1, r2, i2;
-      acc_zero(r1);
-      acc_zero(i1);
-      acc_zero(r2);
-      acc_zero(i2);
-      cmac_conj_full(r1, i1, ph, ps);
-      cmac_conj_full(r2, i2, ph, la);
-      dst[x] = make_cdf(acc_get(r1), acc_get(i1));
-      lam[x] = make_cdf(acc_get(r2), acc_get(i2));
-    }
-  }
+  diag_run_range<KIND, ADJ, MAX_RUN>(S, Gs, T, TP, a, src, dst, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
+                            (int64_t)gridDim.x * blockDim.x, acc);
   if (ADJ) {
 #pragma unroll
     for (int k = 0; k < MAX_RUN; ++k) {

@@ -8,109 +8,22 @@
 // deterministic for a given sector.  The matvec and the screen work on df
 // states (df.cuh); the Lanczos update works on the caller's complex128 vectors.
 #include "cvq_internal.cuh"
+#include "k_ham_impl.cuh"
 
 namespace cvq {
-
-template <int KIND>
-__device__ __forceinline__ uint64_t unrank(int64_t x, const SectorDev& S, const int64_t (*G)[DMAX + 1], uint64_t* wR) {
-  if (KIND == CVQ_BKC) return bkc_unrank(x, S);
-  return bh_unrank(x, S.L, S.N, G, wR);
-}
-
-// Index of the tuple w (index x) moved by (dr on mode r, ds on mode s);
-// f is the BKC full index, wR the BH suffix sums.
-template <int KIND>
-__device__ __forceinline__ int64_t moved_index(int64_t x, uint64_t w, uint64_t wR, int64_t f, int r, int dr, int s,
-                                               int ds, const SectorDev& S, const int64_t (*G)[DMAX + 1]) {
-  if (KIND == CVQ_BKC) {
-    int64_t g = f + (int64_t)dr * S.stride[r];
-    if (s >= 0) g += (int64_t)ds * S.stride[s];
-    return g >> 1;
-  } else {
-    return x + bh_move_delta(w, wR, r, s, dr, S.L, G);  // number-conserving moves: ds = -dr
-  }
-}
 
 template <int KIND>
 __global__ void __launch_bounds__(NTHREADS) k_apply_H(const __grid_constant__ SectorDev S, const cdf* __restrict__ psi,
                                                       cdf* __restrict__ sigma, double* __restrict__ partial) {
   __shared__ int64_t Gs[LMAX][DMAX + 1];
-  __shared__ float2 dE[LMAX][DMAX];
-  __shared__ float2 P[4][DMAX][DMAX];
-  __shared__ float2 hop[LMAX], pair[LMAX];
+  __shared__ HSmem H;
   if (KIND == CVQ_BH) load_G(Gs, S);
-  {
-    const float2* a = &S.tab->diagE[0][0];
-    for (int e = threadIdx.x; e < LMAX * DMAX; e += blockDim.x) (&dE[0][0])[e] = a[e];
-    const float2* b = &S.tab->P[0][0][0];
-    for (int e = threadIdx.x; e < 4 * DMAX * DMAX; e += blockDim.x) (&P[0][0][0])[e] = b[e];
-    for (int e = threadIdx.x; e < LMAX; e += blockDim.x) {
-      hop[e] = S.tab->hop[e];
-      pair[e] = S.tab->pair[e];
-    }
-  }
+  load_htabs(H, S);
   __syncthreads();
-  const int L = S.L, Dm1 = S.D - 1;
   dfacc eacc;
   acc_zero(eacc);
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t wR = 0;
-    const uint64_t w = unrank<KIND>(x, S, Gs, &wR);
-    const int64_t f = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
-    const cdf p = psi[x];
-    dfacc dg;
-    acc_zero(dg);
-    for (int r = 0; r < L; ++r) {
-      const float2 e = dE[r][occ_get(w, r)];
-      acc_add(dg, df_make(e.x, e.y));
-    }
-    const df d = acc_get(dg);
-    dfacc ar, ai;
-    acc_zero(ar);
-    acc_zero(ai);
-    acc_mac(ar, d, re_of(p));
-    acc_mac(ai, d, im_of(p));
-    for (int b = 0; b < S.nb; ++b) {
-      const int r = b, s = (b + 1 == L) ? 0 : b + 1;
-      const int nr = occ_get(w, r), ns = occ_get(w, s);
-      const df h = df_make(hop[b].x, hop[b].y);
-      if (h.h != 0.f) {
-        if (ns >= 1 && nr < Dm1) {  // neighbour x + e_r - e_s: sqrt((n_r + 1) n_s)
-          const df c = df_mul(h, df_make(P[0][nr][ns].x, P[0][nr][ns].y));
-          const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, +1, s, -1, S, Gs)];
-          acc_mac(ar, c, re_of(q));
-          acc_mac(ai, c, im_of(q));
-        }
-        if (nr >= 1 && ns < Dm1) {  // neighbour x - e_r + e_s: sqrt(n_r (n_s + 1))
-          const df c = df_mul(h, df_make(P[1][nr][ns].x, P[1][nr][ns].y));
-          const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, -1, s, +1, S, Gs)];
-          acc_mac(ar, c, re_of(q));
-          acc_mac(ai, c, im_of(q));
-        }
-      }
-      if (KIND == CVQ_BKC) {
-        const df pc = df_make(pair[b].x, pair[b].y);
-        if (pc.h != 0.f) {
-          if (nr < Dm1 && ns < Dm1) {  // neighbour x + e_r + e_s (a_r a_s lowers it to x)
-            const df c = df_mul(pc, df_make(P[2][nr][ns].x, P[2][nr][ns].y));
-            const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, +1, s, +1, S, Gs)];
-            acc_mac(ar, c, re_of(q));
-            acc_mac(ai, c, im_of(q));
-          }
-          if (nr >= 1 && ns >= 1) {  // neighbour x - e_r - e_s
-            const df c = df_mul(pc, df_make(P[3][nr][ns].x, P[3][nr][ns].y));
-            const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, -1, s, -1, S, Gs)];
-            acc_mac(ar, c, re_of(q));
-            acc_mac(ai, c, im_of(q));
-          }
-        }
-      }
-    }
-    const df sr = acc_get(ar), si = acc_get(ai);
-    sigma[x] = make_cdf(sr, si);
-    acc_mac(eacc, re_of(p), sr);
-    acc_mac(eacc, im_of(p), si);
-  }
+  apply_H_range<KIND>(S, Gs, H, psi, sigma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
+                      (int64_t)gridDim.x * blockDim.x, eacc);
   if (partial) {
     const double s = block_sum(acc_to_double(eacc));
     if (threadIdx.x == 0) partial[blockIdx.x] = s;

@@ -372,3 +372,74 @@ def listwise_loss(scores, targets, list_off, dscores=None, loss=None, stream=Non
     _check(L.cvq_mlp_listwise_loss(_ptr(scores), _ptr(targets), _ptr(list_off), n, _ptr(dscores), _ptr(loss),
                                    _stream(stream)), "cvq_mlp_listwise_loss")
     return loss, dscores
+
+
+def _batch_sigs(L):
+    vp, ip = C.c_void_p, C.POINTER(C.c_int)
+    L.cvq_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int, C.POINTER(vp)]
+    L.cvq_batch_destroy.argtypes = [vp]
+    L.cvq_batch_destroy.restype = None
+    L.cvq_batch_set_ansatz.argtypes = [vp, ip, ip, C.POINTER(vp)]
+    L.cvq_batch_set_schedule.argtypes = [vp, C.c_int64, C.c_int]
+    L.cvq_batch_energy_and_grad.argtypes = [vp, vp, vp, vp, vp]
+    L.cvq_batch_info.argtypes = [vp, ip, ip, ip, C.POINTER(C.c_int64)]
+    return L
+
+
+class Batch:
+    """Batched energy and adjoint gradient of many instances (cvq_batch_*).
+    The sectors, pools and reference states must stay alive with the batch."""
+
+    def __init__(self, sectors: Sequence[Sector], pools: Sequence[Pool], n_max: int):
+        import torch
+        L = _batch_sigs(lib())
+        n = len(sectors)
+        self._keep = (list(sectors), list(pools))
+        sa = (C.c_void_p * n)(*[s.h.value if isinstance(s.h, C.c_void_p) else s.h for s in sectors])
+        pa = (C.c_void_p * n)(*[p.h.value if isinstance(p.h, C.c_void_p) else p.h for p in pools])
+        h = C.c_void_p()
+        _check(L.cvq_batch_create(sa, pa, n, int(n_max), C.byref(h)), "cvq_batch_create")
+        self.h, self.n, self.n_max = h, n, int(n_max)
+        self.E = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.theta = torch.zeros(max(1, n * self.n_max), dtype=torch.float64, device="cuda")
+        self.grad = torch.zeros_like(self.theta)
+        self.n_ops = [-1] * n
+        self.offsets = [0] * (n + 1)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.cvq_batch_destroy(self.h)
+            self.h = None
+
+    def set_ansatz(self, op_ids: Sequence[Optional[Sequence[int]]], psi0: Sequence):
+        """op_ids[i] is the ansatz of instance i (None leaves it out); psi0[i] its reference state."""
+        n_ops = [(-1 if ids is None else len(ids)) for ids in op_ids]
+        flat = [int(k) for ids in op_ids if ids is not None for k in ids]
+        na = (C.c_int * self.n)(*n_ops)
+        ia = (C.c_int * max(1, len(flat)))(*flat)
+        pa = (C.c_void_p * self.n)(*[(p.data_ptr() if p is not None else 0) for p in psi0])
+        self._psi0 = list(psi0)
+        _check(lib().cvq_batch_set_ansatz(self.h, na, ia, pa), "cvq_batch_set_ansatz")
+        self.n_ops = n_ops
+        off = [0]
+        for k in n_ops:
+            off.append(off[-1] + max(k, 0))
+        self.offsets = off
+
+    def set_schedule(self, tile: int, ctas_per_sm: int):
+        _check(lib().cvq_batch_set_schedule(self.h, int(tile), int(ctas_per_sm)), "cvq_batch_set_schedule")
+
+    def energy_and_grad(self, theta=None, stream=None):
+        """theta: device float64 vector packed like the op ids (None: use self.theta as filled by the caller).
+        Returns the device tensors (E[n], grad[packed])."""
+        if theta is not None:
+            self.theta[: theta.numel()].copy_(theta)
+        _check(lib().cvq_batch_energy_and_grad(self.h, _ptr(self.theta), _ptr(self.E), _ptr(self.grad),
+                                               _stream(stream)), "cvq_batch_energy_and_grad")
+        return self.E, self.grad[: self.offsets[-1]]
+
+    def info(self):
+        k, it, ly = C.c_int(), C.c_int(), C.c_int()
+        npar = C.c_int64()
+        _check(lib().cvq_batch_info(self.h, C.byref(k), C.byref(it), C.byref(ly), C.byref(npar)), "cvq_batch_info")
+        return dict(kernels_per_eval=k.value, items=it.value, layers=ly.value, params=npar.value)
