@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-c4", action="store_true", help="skip the batched 64-instance sweep measurement")
     ap.add_argument("--instances", type=int, default=len(U_VALUES),
                     help="use the first n of the U/J instances (profiling runs)")
     a = ap.parse_args()
@@ -321,6 +322,15 @@ def run_ours(args):
                           f"ADAPT iteration as 210 H applications (screen) + nfev={np.mean(nfev):.1f} x "
                           f"(2 x n={np.mean(ngates):.1f} gates + 1 H)")}
 
+    # ---- batched engine on the 64-instance sweep (outside the timed ADAPT region)
+    c4 = None
+    if rank == 0 and not args.no_c4:
+        from paper_2606_05297_gb300 import batched
+        c4 = batched.measure_c4(reps=3)
+        c4["workload"] = ("64 Bose-Hubbard instances, L ~ U{8..12}, N = L, U/J log-uniform [0.5, 20], PBC, "
+                          "all-pairs pool, HVA layer + 8 pool operators each; energy and adjoint gradient of every "
+                          "instance per evaluation")
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -333,6 +343,7 @@ def run_ours(args):
                        "ansatz_len_mean": float(np.mean(ngates)), "bfgs_evals_per_iter_mean": float(np.mean(nfev)),
                        "dE_last": [abs(A.trace[-1]["E"] - A.E0) for A in insts], "parallelism": f"replicas x{ws}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "c4_batched": c4,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in stats.items()},
         }
         print(json.dumps(line), flush=True)

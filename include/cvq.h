@@ -245,6 +245,10 @@ int cvq_mlp_set(cvq_mlp *m, const float *host, size_t n);
  *     captures the evaluation into a CUDA graph; later calls launch it on
  *     `stream`.  Results are deterministic: every partial sum has its own
  *     slot and the final sums run in a fixed order.
+ *   cvq_batch_set_active: active[i] = 0 pauses instance i (its items are
+ *     skipped and its outputs not written) without a new schedule or graph;
+ *     set_ansatz makes every instance with an ansatz active.  Synchronises
+ *     `stream`.
  *   cvq_batch_info: kernels per evaluation, work items, layers and the
  *     number of parameters.
  * Errors: EINVAL (sizes, mixed kinds or devices, op ids), ENOMEM, ECUDA. */
@@ -255,6 +259,7 @@ void cvq_batch_destroy(cvq_batch *b);
 int cvq_batch_set_ansatz(cvq_batch *b, const int *n_ops, const int *op_ids, const cvq_c128 *const *psi0);
 int cvq_batch_set_schedule(cvq_batch *b, int64_t tile, int ctas_per_sm);
 int cvq_batch_energy_and_grad(cvq_batch *b, const double *theta_dev, double *E_dev, double *grad_dev, void *stream);
+int cvq_batch_set_active(cvq_batch *b, const int *active, void *stream);
 int cvq_batch_info(const cvq_batch *b, int *kernels_per_eval, int *items, int *layers, int64_t *n_params);
 
 /* Pool screen for callers that cannot allocate device memory.  The paper has

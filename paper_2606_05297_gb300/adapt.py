@@ -56,8 +56,9 @@ class BFGS:
         self.nfev = 0
 
     def _eval(self, x):
+        # one evaluation, asked of whoever drives the generator
         self.nfev += 1
-        f, g = self.fg(x)
+        f, g = yield x
         return float(f), np.asarray(g, dtype=np.float64)
 
     @staticmethod
@@ -82,19 +83,19 @@ class BFGS:
 
         def phi(a):
             if a not in memo:
-                f, g = self._eval(x + a * p)
+                f, g = yield from self._eval(x + a * p)
                 memo[a] = (f, g, float(g @ p))
             return memo[a]
 
         def zoom(lo, hi):
             for _ in range(self.max_ls):
-                flo, _, dlo = phi(lo)
-                fhi, _, dhi = phi(hi)
+                flo, _, dlo = yield from phi(lo)
+                fhi, _, dhi = yield from phi(hi)
                 w = abs(hi - lo)
                 a = self._cubic(lo, flo, dlo, hi, fhi, dhi)
                 if a is None or not (min(lo, hi) + 0.1 * w <= a <= max(lo, hi) - 0.1 * w):
                     a = 0.5 * (lo + hi)
-                fa, _, da = phi(a)
+                fa, _, da = yield from phi(a)
                 if fa > f0 + self.c1 * a * d0 or fa >= flo:
                     hi = a
                 else:
@@ -105,34 +106,37 @@ class BFGS:
                     lo = a
                 if abs(hi - lo) < 1e-16 * max(1.0, abs(lo)):
                     break
-            flo = phi(lo)[0]
+            flo = (yield from phi(lo))[0]
             return lo if (lo > 0.0 and flo < f0) else None
 
         prev, a, fprev = 0.0, 1.0, f0
         found = None
         for it in range(self.max_ls):
-            fa, _, da = phi(a)
+            fa, _, da = yield from phi(a)
             if fa > f0 + self.c1 * a * d0 or (it > 0 and fa >= fprev):
-                found = zoom(prev, a)
+                found = yield from zoom(prev, a)
                 break
             if abs(da) <= -self.c2 * d0:
                 found = a
                 break
             if da >= 0.0:
-                found = zoom(a, prev)
+                found = yield from zoom(a, prev)
                 break
             prev, fprev = a, fa
             a = min(2.0 * a, self.step_max)
         if found is None:
             return None, f0, g0
-        f, g, _ = phi(found)
+        f, g, _ = yield from phi(found)
         return found, f, g
 
-    def minimize(self, x0, gtol: float, max_iter: int = 1000, Hinv0=None) -> OptResult:
+    def steps(self, x0, gtol: float, max_iter: int = 1000, Hinv0=None):
+        """The minimisation as a generator: it yields each point to evaluate,
+        takes (f, g) back through send(), and returns the OptResult.  Several
+        minimisations can then share one batched evaluation per round."""
         self.nfev = 0
         x = np.array(x0, dtype=np.float64)
         n = x.size
-        f, g = self._eval(x)
+        f, g = yield from self._eval(x)
         Hi = np.eye(n) if Hinv0 is None else np.array(Hinv0, dtype=np.float64)
         status, it = "max_iter", 0
         while it < max_iter:
@@ -143,7 +147,7 @@ class BFGS:
             if float(g @ p) >= 0.0:
                 Hi = np.eye(n)
                 p = -g
-            a, fn, gn = self._search(x, f, g, p)
+            a, fn, gn = yield from self._search(x, f, g, p)
             if a is None:
                 status = "line_search"
                 break
@@ -160,6 +164,15 @@ class BFGS:
         if np.max(np.abs(g), initial=0.0) < gtol:
             status = "gtol"
         return OptResult(x, f, g, it, self.nfev, Hi, status)
+
+    def minimize(self, x0, gtol: float, max_iter: int = 1000, Hinv0=None) -> OptResult:
+        gen = self.steps(x0, gtol, max_iter, Hinv0)
+        try:
+            x = next(gen)
+            while True:
+                x = gen.send(self.fg(x))
+        except StopIteration as stop:
+            return stop.value
 
 
 # ---------------------------------------------------------------- selection

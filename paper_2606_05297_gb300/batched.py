@@ -1,0 +1,242 @@
+"""Batched ADAPT over many Hamiltonian instances (a U/J sweep) on one GPU.
+
+Every instance runs the plain method of Sec. IV.B (screen, select the largest
+|g|, append, re-minimise with BFGS), but the energy-and-gradient evaluations
+of all instances share one batched graph launch per round: each instance's
+BFGS is a generator that yields the point it wants evaluated, and one round
+evaluates every pending point at once (cvq_batch_energy_and_grad).
+Instances whose minimisation has finished are paused in the batch, so the
+graph is captured once per ansatz structure.
+
+The work-item size and CTAs per SM of the batched launches are chosen by
+`autotune`, which times every candidate schedule on the batch itself.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import cvq
+from .adapt import BFGS, OptResult, select
+from .workloads import Model, Op
+
+TILES = (4096, 16384, 65536, 262144)
+CTAS = (1, 2)
+_TUNED: Dict[tuple, tuple] = {}
+
+
+def time_eval(batch: "cvq.Batch", reps: int = 3) -> float:
+    """Mean milliseconds of one batched evaluation (CUDA events, after one warm-up)."""
+    import torch
+    batch.energy_and_grad()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        batch.energy_and_grad()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune(batch: "cvq.Batch", sectors, tiles=TILES, ctas=CTAS, reps: int = 3, cache: bool = True) -> dict:
+    """Time every (tile, CTAs per SM) schedule on the batch's current ansatz
+    and keep the fastest.  Results are cached per set of sector sizes."""
+    key = (tuple(sorted(s.dim for s in sectors)),)
+    if cache and key in _TUNED:
+        tile, c = _TUNED[key]
+        batch.set_schedule(tile, c)
+        return dict(tile=tile, ctas_per_sm=c, cached=True)
+    best, table = None, []
+    for tile in tiles:
+        for c in ctas:
+            batch.set_schedule(tile, c)
+            ms = time_eval(batch, reps)
+            table.append((tile, c, ms))
+            if best is None or ms < best[2]:
+                best = (tile, c, ms)
+    batch.set_schedule(best[0], best[1])
+    _TUNED[key] = (best[0], best[1])
+    return dict(tile=best[0], ctas_per_sm=best[1], ms=best[2], table=table, cached=False)
+
+
+class BatchedAdapt:
+    """Lockstep CV-ADAPT-VQE on n instances with one shared batched engine."""
+
+    def __init__(self, models: Sequence[Model], pool_ops: Sequence[Sequence[Op]], init_occ: Sequence[Sequence[int]],
+                 warm_ops: Sequence[Sequence[Op]] = None, warm_theta: Sequence[Sequence[float]] = None,
+                 n_max: int = 160, tune: bool = True):
+        import torch
+        self.torch = torch
+        n = len(models)
+        warm_ops = warm_ops or [[] for _ in range(n)]
+        warm_theta = warm_theta or [[] for _ in range(n)]
+        self.models = list(models)
+        self.K = [len(p) for p in pool_ops]
+        self.sectors = [cvq.Sector(m) for m in models]
+        self.pools = [cvq.Pool(s, list(p) + list(w)) for s, p, w in zip(self.sectors, pool_ops, warm_ops)]
+        self.psi0 = [s.basis_state(o) for s, o in zip(self.sectors, init_occ)]
+        self.ids: List[List[int]] = [list(range(K, K + len(w))) for K, w in zip(self.K, warm_ops)]
+        self.theta = [np.array(t, dtype=np.float64) for t in warm_theta]
+        self.n_max = n_max
+        self.batch = cvq.Batch(self.sectors, self.pools, n_max)
+        self.ws = [s.workspace(p, n_max) for s, p in zip(self.sectors, self.pools)]
+        self.done = [False] * n
+        self.trace: List[list] = [[] for _ in range(n)]
+        self.rounds = 0
+        self.evals = 0
+        self.tune = tune
+        self.tuned = None
+        self._host = torch.empty(n * n_max + n, dtype=torch.float64, pin_memory=True)
+
+    # ---------------------------------------------------------------- evaluations
+
+    def _structure(self):
+        self.batch.set_ansatz([None if self.done[i] else self.ids[i] for i in range(len(self.ids))], self.psi0)
+        if self.tune and self.tuned is None:
+            self._load_theta({i: self.theta[i] for i in range(len(self.ids)) if not self.done[i]})
+            self.tuned = autotune(self.batch, self.sectors)
+
+    def _load_theta(self, xs: Dict[int, np.ndarray]):
+        off = self.batch.offsets
+        h = self._host[: off[-1]].numpy()
+        for i, x in xs.items():
+            h[off[i]:off[i + 1]] = x
+        self.batch.theta[: off[-1]].copy_(self._host[: off[-1]], non_blocking=True)
+
+    def lockstep(self, gens: Dict[int, object]) -> Dict[int, OptResult]:
+        """Drive several BFGS generators; every round evaluates all pending
+        points with one batched launch."""
+        torch = self.torch
+        xs = {}
+        res = {}
+        for i, g in gens.items():
+            xs[i] = next(g)
+        n = len(self.ids)
+        off = self.batch.offsets
+        while xs:
+            self.batch.set_active([i in xs for i in range(n)])
+            self._load_theta(xs)
+            E, G = self.batch.energy_and_grad()
+            hE = E.cpu().numpy()
+            hG = G.cpu().numpy()
+            self.rounds += 1
+            self.evals += len(xs)
+            for i in list(xs):
+                try:
+                    xs[i] = gens[i].send((float(hE[i]), hG[off[i]:off[i + 1]].copy()))
+                except StopIteration as stop:
+                    res[i] = stop.value
+                    del xs[i]
+        return res
+
+    def optimise_warm_start(self, gtol: float = 1e-9, max_iter: int = 1000):
+        self._structure()
+        gens = {i: BFGS(None).steps(self.theta[i], gtol=gtol, max_iter=max_iter)
+                for i in range(len(self.ids)) if len(self.ids[i])}
+        for i, r in self.lockstep(gens).items():
+            self.theta[i] = r.x
+            self.trace[i].append(dict(kind="warm", E=r.f, nfev=r.nfev, nit=r.nit, status=r.status))
+
+    def step(self, grad_tol: float = 1e-6, max_iter: int = 1000):
+        """One ADAPT iteration on every instance that has not converged.
+        Returns the number of instances that grew."""
+        grown = {}
+        for i in range(len(self.ids)):
+            if self.done[i]:
+                continue
+            psi = cvq.apply_ansatz(self.sectors[i], self.pools[i], self.ids[i], self.theta[i], self.psi0[i],
+                                   ws=self.ws[i])
+            g = cvq.screen_pool(self.sectors[i], self.pools[i], psi, subset=list(range(self.K[i])),
+                                ws=self.ws[i])[: self.K[i]].cpu().numpy()
+            k, gmax = select(g)
+            if gmax < grad_tol or len(self.ids[i]) + 1 > self.n_max:
+                self.done[i] = True
+                continue
+            self.ids[i].append(k)
+            self.theta[i] = np.append(self.theta[i], 0.0)
+            grown[i] = (k, gmax)
+        if not grown:
+            return 0
+        self._structure()
+        gens = {i: BFGS(None).steps(self.theta[i], gtol=min(1e-6, gm * 1e-5), max_iter=max_iter)
+                for i, (_, gm) in grown.items()}
+        for i, r in self.lockstep(gens).items():
+            self.theta[i] = r.x
+            self.trace[i].append(dict(kind="adapt", op=grown[i][0], gmax=grown[i][1], E=r.f, nfev=r.nfev, nit=r.nit,
+                                      status=r.status, n=len(self.ids[i])))
+        return len(grown)
+
+
+def c4_batch_inputs(seed: int = 0, count: int = 64, extra_ops: int = 8):
+    """The 64-instance sweep with an HVA warm-start layer plus `extra_ops`
+    seeded pool operators per instance, for throughput measurements."""
+    from . import workloads as W
+    insts = W.c4_instances(seed, count)
+    rng = np.random.default_rng(seed + 1)
+    out = []
+    for m in insts:
+        pool = W.bh_allpairs_pool(m.L)
+        warm = W.hva_layer(m)
+        ids = list(range(len(pool), len(pool) + len(warm))) + [int(k) for k in rng.integers(0, len(pool), extra_ops)]
+        th = np.concatenate([W.warm_start_thetas(len(warm), 0), rng.uniform(-0.2, 0.2, extra_ops)])
+        out.append((m, pool + warm, ids, th))
+    return out
+
+
+def measure_c4(reps: int = 5, seed: int = 0, count: int = 64, extra_ops: int = 8, sequential: bool = True) -> dict:
+    """Throughput of energy-and-gradient evaluations over the 64-instance sweep:
+    one batched graph launch per evaluation of every instance, against the
+    same evaluations issued instance by instance through cvq_energy_and_grad.
+    Device-resident inputs; CUDA events on the launching stream."""
+    import torch
+    data = c4_batch_inputs(seed, count, extra_ops)
+    sectors = [cvq.Sector(m) for m, _, _, _ in data]
+    pools = [cvq.Pool(s, ops) for s, (_, ops, _, _) in zip(sectors, data)]
+    psi0 = [s.basis_state(_mott(m)) for s, (m, _, _, _) in zip(sectors, data)]
+    n_max = max(len(ids) for _, _, ids, _ in data)
+    b = cvq.Batch(sectors, pools, n_max)
+    b.set_ansatz([ids for _, _, ids, _ in data], psi0)
+    flat = np.concatenate([th for _, _, _, th in data])
+    b.theta[: flat.size].copy_(torch.from_numpy(flat))
+    tuned = autotune(b, sectors, cache=False)
+    ms_batch = time_eval(b, reps)
+    info = b.info()
+    amps = sum(s.dim for s in sectors)
+    gates = sum(len(ids) for _, _, ids, _ in data)
+    out = dict(instances=count, amplitudes=amps, params=int(flat.size), ms_per_eval_batched=ms_batch,
+               evals_per_s_batched=count * 1e3 / ms_batch, schedule=dict(tile=tuned["tile"],
+                                                                           ctas_per_sm=tuned["ctas_per_sm"]),
+               kernels_per_eval=info["kernels_per_eval"], items=info["items"], layers=info["layers"],
+               gate_amplitudes_per_s_batched=sum(s.dim * len(ids) for s, (_, _, ids, _) in zip(sectors, data)) * 2e3
+               / ms_batch, total_gates=gates)
+    if sequential:
+        E = torch.empty(count, dtype=torch.float64, device="cuda")
+        G = torch.empty(flat.size, dtype=torch.float64, device="cuda")
+        wss = [s.workspace(p, len(ids)) for s, p, (_, _, ids, _) in zip(sectors, pools, data)]
+        offs = np.concatenate([[0], np.cumsum([len(ids) for _, _, ids, _ in data])])
+
+        def loop():
+            for i, (s, p, (m, _, ids, th)) in enumerate(zip(sectors, pools, data)):
+                cvq.energy_and_grad(s, p, ids, th, psi0[i], E=E[i:i + 1], grad=G[offs[i]:offs[i + 1]], ws=wss[i])
+
+        loop()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            loop()
+        e1.record()
+        e1.synchronize()
+        ms_seq = e0.elapsed_time(e1) / reps
+        Eb, Gb = b.energy_and_grad()
+        out.update(ms_per_eval_sequential=ms_seq, evals_per_s_sequential=count * 1e3 / ms_seq,
+                   speedup=ms_seq / ms_batch,
+                   max_abs_diff_E=float((Eb - E).abs().max()), max_abs_diff_grad=float((Gb - G).abs().max()))
+    return out
+
+
+def _mott(m):
+    from .workloads import mott_occupation
+    return mott_occupation(m.L, m.N)

@@ -75,6 +75,8 @@ struct cvq_batch {
   BRed* red_d = nullptr;
   int2* gates_d = nullptr;
   int* counters_d = nullptr;
+  int* active_d = nullptr;                 // per instance: 1 = evaluated
+  std::vector<std::vector<int4>> chunks;   // host copy of every BH pool's chunk schedule
   double* partial_d = nullptr;
   std::vector<int> layer_off, layer_n;
   std::vector<char> layer_adj;
@@ -166,8 +168,7 @@ void items_of(const cvq_batch* b, int inst, int seg, const BSeg* sg, int kind, s
     for (int64_t u = 0; u < items; u += orbits) push(u, std::min(items, u + orbits));
   } else {
     // consecutive equal-work chunks until the item holds about `tile` amplitudes
-    std::vector<int4> ch(t.nchunks);
-    if (t.nchunks) cudaMemcpy(ch.data(), p.P.chunks + t.chunk_base, sizeof(int4) * t.nchunks, cudaMemcpyDeviceToHost);
+    const int4* ch = b->chunks[inst].data() + t.chunk_base;
     int64_t acc = 0, c0 = 0;
     for (int c = 0; c < t.nchunks; ++c) {
       acc += (int64_t)(ch[c].z - ch[c].y) * (ch[c].x + 1);
@@ -223,7 +224,7 @@ int build_plan(cvq_batch* b) {
     const int s0 = slot;
     const size_t before = layers[smax + 1].size();
     items_of(b, i, -1, nullptr, BI_APPLYH, layers[smax + 1], slot, 1);
-    red.push_back({i, 1, s0, (int)(layers[smax + 1].size() - before), 1});
+    red.push_back({i, i, 1, s0, (int)(layers[smax + 1].size() - before), 1});
   }
   for (int r = 0; r < smax; ++r) {
     const int l = smax + 2 + r;
@@ -236,7 +237,7 @@ int build_plan(cvq_batch* b) {
       const size_t before = layers[l].size();
       items_of(b, i, seg_id[i][ns - 1 - r], &s, s.isdiag ? BI_DIAG : BI_GATE, layers[l], slot, s.m);
       const int cnt = (int)(layers[l].size() - before);
-      for (int q = 0; q < s.m; ++q) red.push_back({b->inst[i].theta_off + s.k0 + q, 0, s0 + q, cnt, s.m});
+      for (int q = 0; q < s.m; ++q) red.push_back({i, b->inst[i].theta_off + s.k0 + q, 0, s0 + q, cnt, s.m});
     }
   }
   std::vector<int2> gates;
@@ -263,8 +264,9 @@ int build_plan(cvq_batch* b) {
   const size_t s_red = a256(sizeof(BRed) * std::max<size_t>(1, red.size()));
   const size_t s_g = a256(sizeof(int2) * std::max<size_t>(1, gates.size()));
   const size_t s_c = a256(sizeof(int) * layers.size());
+  const size_t s_a = a256(sizeof(int) * n);
   const size_t s_p = a256(sizeof(double) * std::max(1, slot));
-  BCUDA(cudaMalloc(&b->plan, s_ids + s_seg + s_it + s_red + s_g + s_c + s_p), "cudaMalloc of the batch plan");
+  BCUDA(cudaMalloc(&b->plan, s_ids + s_seg + s_it + s_red + s_g + s_c + s_a + s_p), "cudaMalloc of the batch plan");
   char* q = (char*)b->plan;
   b->ids_d = (int*)q;
   q += s_ids;
@@ -278,6 +280,8 @@ int build_plan(cvq_batch* b) {
   q += s_g;
   b->counters_d = (int*)q;
   q += s_c;
+  b->active_d = (int*)q;
+  q += s_a;
   b->partial_d = (double*)q;
   if (!b->ids.empty()) BCUDA(cudaMemcpy(b->ids_d, b->ids.data(), sizeof(int) * b->ids.size(), cudaMemcpyHostToDevice), "copy ids");
   if (!seg_all.empty()) BCUDA(cudaMemcpy(b->segs_d, seg_all.data(), sizeof(BSeg) * seg_all.size(), cudaMemcpyHostToDevice), "copy segments");
@@ -285,6 +289,9 @@ int build_plan(cvq_batch* b) {
   if (!red.empty()) BCUDA(cudaMemcpy(b->red_d, red.data(), sizeof(BRed) * red.size(), cudaMemcpyHostToDevice), "copy reductions");
   if (!gates.empty()) BCUDA(cudaMemcpy(b->gates_d, gates.data(), sizeof(int2) * gates.size(), cudaMemcpyHostToDevice), "copy gates");
   BCUDA(cudaMemcpy(b->inst_d, b->inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice), "copy instances");
+  std::vector<int> act(n);
+  for (int i = 0; i < n; ++i) act[i] = b->n_ops[i] >= 0;
+  BCUDA(cudaMemcpy(b->active_d, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "copy active flags");
   b->have = true;
   return CVQ_OK;
 }
@@ -294,13 +301,13 @@ int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
   cudaStream_t st = b->cap;
   BCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t e = cudaMemsetAsync(b->counters_d, 0, sizeof(int) * b->layer_n.size(), st);
-  if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->ids_d, theta, st);
+  if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->ids_d, theta, b->active_d, st);
   const int grid = b->sms * b->ctas_per_sm;
   for (size_t l = 0; l < b->layer_n.size() && e == cudaSuccess; ++l)
     e = launch_batch_layer(b->kind, b->layer_adj[l] != 0, grid, b->smem, b->inst_d, b->segs_d,
                            b->items_d + b->layer_off[l], b->layer_n[l], b->counters_d + l, b->ids_d, theta,
-                           b->partial_d, st);
-  if (e == cudaSuccess) e = launch_batch_reduce(b->red_d, b->n_red, b->partial_d, E, grad, st);
+                           b->active_d, b->partial_d, st);
+  if (e == cudaSuccess) e = launch_batch_reduce(b->red_d, b->n_red, b->partial_d, b->active_d, E, grad, st);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(st, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -379,6 +386,17 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
     return cuda_err(e, "batch allocation");
   }
   b->sms = prop.multiProcessorCount;
+  b->chunks.resize(n_inst);
+  for (int i = 0; i < n_inst && b->kind == CVQ_BH; ++i) {
+    int nch = 0;
+    for (int t = 0; t < b->pv[i].ntypes; ++t) nch = std::max(nch, b->pv[i].types[t].chunk_base + b->pv[i].types[t].nchunks);
+    b->chunks[i].resize(nch);
+    if (nch) e = cudaMemcpy(b->chunks[i].data(), b->pv[i].P.chunks, sizeof(int4) * nch, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      cvq_batch_destroy(b);
+      return cuda_err(e, "copy of the chunk schedules");
+    }
+  }
   for (int i = 0; i < n_inst; ++i) {
     BInst& I = b->inst[i];
     memset(&I, 0, sizeof I);
@@ -444,6 +462,20 @@ extern "C" int cvq_batch_energy_and_grad(cvq_batch* b, const double* theta_dev, 
   if (!b->exec || b->g_theta != theta_dev || b->g_E != E_dev || b->g_grad != grad_dev)
     if (int rc = capture(b, theta_dev, E_dev, grad_dev)) return rc;
   BCUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "graph launch");
+  return CVQ_OK;
+}
+
+extern "C" int cvq_batch_set_active(cvq_batch* b, const int* active, void* stream) {
+  if (!b || !active) return errf(CVQ_EINVAL, "null argument");
+  if (!b->have) return errf(CVQ_EINVAL, "cvq_batch_set_ansatz has not been called");
+  std::vector<int> a(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    if (active[i] && b->n_ops[i] < 0) return errf(CVQ_EINVAL, "instance %d has no ansatz", i);
+    a[i] = active[i] ? 1 : 0;
+  }
+  BCUDA(cudaMemcpyAsync(b->active_d, a.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, (cudaStream_t)stream),
+        "copy active flags");
+  BCUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronise");
   return CVQ_OK;
 }
 

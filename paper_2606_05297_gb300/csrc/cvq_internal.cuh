@@ -285,17 +285,17 @@ struct BItem {
 
 // One output of the final reduction.
 struct BRed {
-  int out, is_energy, slot0, count, stride;
+  int inst, out, is_energy, slot0, count, stride;
 };
 
 cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, const int* ids, const double* theta,
-                               cudaStream_t st);
+                               const int* active, cudaStream_t st);
 cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const BInst* insts, const BSeg* segs,
                                const BItem* items, int nitems, int* counter, const int* ids, const double* theta,
-                               double* partial, cudaStream_t st);
+                               const int* active, double* partial, cudaStream_t st);
 cudaError_t set_batch_smem_limit(int bytes);
-cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, double* E, double* grad,
-                                cudaStream_t st);
+cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, const int* active, double* E,
+                                double* grad, cudaStream_t st);
 
 // Pool indices screened by one launch (passed by value).
 struct SubsetArg {

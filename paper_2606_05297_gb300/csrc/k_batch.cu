@@ -26,10 +26,11 @@ namespace cvq {
 
 __global__ void __launch_bounds__(128) k_batch_build(const BInst* __restrict__ insts, const int2* __restrict__ gates,
                                                      int ngates, const int* __restrict__ ids,
-                                                     const double* __restrict__ theta) {
+                                                     const double* __restrict__ theta, const int* __restrict__ active) {
   const int g = blockIdx.x;
   if (g >= ngates) return;
   const int2 ik = gates[g];
+  if (!active[ik.x]) return;
   const BInst& I = insts[ik.x];
   const int op = ids[I.ids_off + ik.y];
   const TypeDesc& t = I.ops[op].t;
@@ -89,7 +90,7 @@ template <int KIND, bool ADJ>
 __global__ void __launch_bounds__(NTHREADS, 2)
     k_batch_layer(const BInst* __restrict__ insts, const BSeg* __restrict__ segs, const BItem* __restrict__ items,
                   int nitems, int* counter, const int* __restrict__ ids, const double* __restrict__ theta,
-                  double* __restrict__ partial) {
+                  const int* __restrict__ active, double* __restrict__ partial) {
   extern __shared__ __align__(16) char smem[];
   __shared__ BShared sh;
   __shared__ int64_t G64[LMAX][DMAX + 1];
@@ -100,6 +101,10 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const int k = sh.item;
     if (k >= nitems) break;
     const BItem it = items[k];
+    if (!active[it.inst]) {  // instance paused for this evaluation: skip the item
+      __syncthreads();
+      continue;
+    }
     const BInst& I = insts[it.inst];
     copy_words(&sh.S, &I.S, sizeof(SectorDev));
     if (it.kind != BI_TODF && it.kind != BI_APPLYH) copy_words(&sh.seg, &segs[it.seg], sizeof(BSeg));
@@ -183,10 +188,11 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 
 // out = scale * sum of `count` partials from slot0 with `stride`, in order.
 __global__ void k_batch_reduce(const BRed* __restrict__ red, int n, const double* __restrict__ partial,
-                               double* __restrict__ E, double* __restrict__ grad) {
+                               const int* __restrict__ active, double* __restrict__ E, double* __restrict__ grad) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const BRed d = red[r];
+  if (!active[d.inst]) return;
   double v = 0.0;
   for (int q = 0; q < d.count; ++q) v += partial[(size_t)d.slot0 + (size_t)q * d.stride];
   if (d.is_energy) E[d.out] = v;
@@ -194,22 +200,22 @@ __global__ void k_batch_reduce(const BRed* __restrict__ red, int n, const double
 }
 
 cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, const int* ids, const double* theta,
-                               cudaStream_t st) {
+                               const int* active, cudaStream_t st) {
   if (ngates <= 0) return cudaSuccess;
-  k_batch_build<<<ngates, 128, 0, st>>>(insts, gates, ngates, ids, theta);
+  k_batch_build<<<ngates, 128, 0, st>>>(insts, gates, ngates, ids, theta, active);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const BInst* insts, const BSeg* segs,
                                const BItem* items, int nitems, int* counter, const int* ids, const double* theta,
-                               double* partial, cudaStream_t st) {
+                               const int* active, double* partial, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
   if (kind == CVQ_BH) {
-    if (adj) k_batch_layer<CVQ_BH, true><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, partial);
-    else k_batch_layer<CVQ_BH, false><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, partial);
+    if (adj) k_batch_layer<CVQ_BH, true><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, active, partial);
+    else k_batch_layer<CVQ_BH, false><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, active, partial);
   } else {
-    if (adj) k_batch_layer<CVQ_BKC, true><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, partial);
-    else k_batch_layer<CVQ_BKC, false><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, partial);
+    if (adj) k_batch_layer<CVQ_BKC, true><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, active, partial);
+    else k_batch_layer<CVQ_BKC, false><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, theta, active, partial);
   }
   return cudaGetLastError();
 }
@@ -223,10 +229,10 @@ cudaError_t set_batch_smem_limit(int bytes) {
   return e;
 }
 
-cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, double* E, double* grad,
-                                cudaStream_t st) {
+cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, const int* active, double* E,
+                                double* grad, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_batch_reduce<<<(n + 127) / 128, 128, 0, st>>>(red, n, partial, E, grad);
+  k_batch_reduce<<<(n + 127) / 128, 128, 0, st>>>(red, n, partial, active, E, grad);
   return cudaGetLastError();
 }
 

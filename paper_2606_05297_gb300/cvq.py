@@ -383,6 +383,7 @@ def _batch_sigs(L):
     L.cvq_batch_set_schedule.argtypes = [vp, C.c_int64, C.c_int]
     L.cvq_batch_energy_and_grad.argtypes = [vp, vp, vp, vp, vp]
     L.cvq_batch_info.argtypes = [vp, ip, ip, ip, C.POINTER(C.c_int64)]
+    L.cvq_batch_set_active.argtypes = [vp, ip, vp]
     return L
 
 
@@ -425,6 +426,10 @@ class Batch:
         for k in n_ops:
             off.append(off[-1] + max(k, 0))
         self.offsets = off
+
+    def set_active(self, active: Sequence[bool], stream=None):
+        a = (C.c_int * self.n)(*[int(bool(v)) for v in active])
+        _check(lib().cvq_batch_set_active(self.h, a, _stream(stream)), "cvq_batch_set_active")
 
     def set_schedule(self, tile: int, ctas_per_sm: int):
         _check(lib().cvq_batch_set_schedule(self.h, int(tile), int(ctas_per_sm)), "cvq_batch_set_schedule")

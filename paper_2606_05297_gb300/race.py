@@ -1,0 +1,126 @@
+"""Learned-proposal ADAPT against plain full-screen ADAPT on the same GPU.
+
+    python -m paper_2606_05297_gb300.race [--L 10 --d 6] [--max-ops 40]
+
+1. Trace collection: plain ADAPT runs on the Bose-Hubbard L=4 chain (Mott
+   start), the L=12 periodic chain at U/J = 3.4 and the Kitaev chain with
+   Kerr at L=8, d=8 (vacuum start) store one training list per iteration;
+   the scorer is trained on them with the project's own kernels.
+2. E0 of the target instance (Kitaev chain with Kerr, t=1, Delta=0.6,
+   K=0.3, open chain) by Lanczos on the device.
+3. Both arms from the same warm start: plain full-screen ADAPT, and learned
+   ADAPT (exact screen of the scorer's top k, full screen every
+   `full_every` iterations, online training on every full screen).  Each
+   arm records wall time and |E - E0| after every iteration and the time at
+   which |E - E0| first drops below 1e-1, 1e-2, ..., 1e-6.
+
+Prints one JSON object.  Trace sizes can be reduced with --trace-ops and the
+source instances with --small-traces.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+THRESHOLDS = (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6)
+
+
+def trace_sources(small: bool):
+    from . import workloads as W
+    c1 = W.c1_model()
+    c2 = W.bose_hubbard(6, 6, J=1.0, U=3.4, periodic=True) if small else W.c2_model(3.4)
+    c3 = W.kitaev_kerr(5, 4, t=1.0, Delta=0.5, K=0.1) if small else W.c3_model(0, K=0.1)
+    out = []
+    for m, warm in ((c1, True), (c2, True), (c3, False)):
+        ops = W.hva_layer(m) if warm else []
+        out.append((m, W.pool_for(m), W.initial_occupation(m), ops, W.warm_start_thetas(len(ops), 0)))
+    return out
+
+
+def run_arm(make, E0, max_ops, grad_tol=1e-6):
+    a = make()
+    t0 = time.perf_counter()
+    a.optimise_warm_start()
+    hist = []
+    reached = {}
+    for it in range(max_ops):
+        rec = a.step(grad_tol=grad_tol)
+        t = time.perf_counter() - t0
+        if rec is None:
+            break
+        dE = abs(rec["E"] - E0)
+        hist.append(dict(it=it + 1, t=t, dE=dE, op=rec["op"], nfev=rec["nfev"]))
+        for th in THRESHOLDS:
+            if dE < th and str(th) not in reached:
+                reached[str(th)] = dict(seconds=t, iterations=it + 1)
+        if dE < THRESHOLDS[-1]:
+            break
+    return a, hist, reached, time.perf_counter() - t0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", type=int, default=10)
+    ap.add_argument("--d", type=int, default=6)
+    ap.add_argument("--max-ops", type=int, default=40)
+    ap.add_argument("--trace-ops", type=int, default=20)
+    ap.add_argument("--small-traces", action="store_true")
+    ap.add_argument("--top-k", type=int, default=8)
+    ap.add_argument("--full-every", type=int, default=5)
+    ap.add_argument("--train-steps", type=int, default=300)
+    a = ap.parse_args(argv)
+
+    import torch
+    from . import adapt, cvq, learned
+    from . import workloads as W
+
+    t0 = time.perf_counter()
+    scorer = cvq.Scorer(65536, seed=1)
+    tr = learned.Trainer(scorer, lr=1e-3)
+    for (m, pool, occ, wops, wth) in trace_sources(a.small_traces):
+        learned.collect_traces(m, pool, occ, tr, warm_ops=wops, warm_theta=wth, max_ops=a.trace_ops, top_k=a.top_k)
+    losses = tr.train(a.train_steps)
+    t_train = time.perf_counter() - t0
+
+    m = W.kitaev_kerr(a.L, a.d, t=1.0, Delta=0.6, K=0.3, periodic=False)
+    pool = W.bkc_kerr_pool(a.L)
+    occ = W.vacuum_occupation(a.L)
+    warm = W.hva_layer(m)
+    wth = W.warm_start_thetas(len(warm), 0)
+    sec = cvq.Sector(m)
+    E0 = adapt.ground_energy(sec)
+    del sec
+    torch.cuda.empty_cache()
+
+    plain, h_plain, r_plain, t_plain = run_arm(
+        lambda: adapt.Adapt(m, pool, occ, warm, wth, n_max=a.max_ops + len(warm) + 1), E0, a.max_ops)
+    del plain
+    torch.cuda.empty_cache()
+    la, h_learn, r_learn, t_learn = run_arm(
+        lambda: learned.LearnedAdapt(m, pool, occ, scorer, trainer=tr, top_k=a.top_k, full_every=a.full_every,
+                                     train_steps=20, warm_ops=warm, warm_theta=wth,
+                                     n_max=a.max_ops + len(warm) + 1), E0, a.max_ops)
+    st = la.stats
+    out = dict(
+        target=dict(model=f"kitaev_kerr open L={a.L} d={a.d} t=1 Delta=0.6 K=0.3", dim=int(la.sector.dim),
+                    pool=len(pool), E0=E0, warm_start_gates=len(warm)),
+        training=dict(lists=len(tr.X), rows=tr.rows(), loss_first=losses[0] if losses else None,
+                      loss_last=losses[-1] if losses else None, seconds=t_train,
+                      sources="Bose-Hubbard L=4 (Mott), " + ("L=6" if a.small_traces else "L=12") +
+                              " PBC U/J=3.4, Kitaev+Kerr " + ("L=5 d=4" if a.small_traces else "L=8 d=8")),
+        plain=dict(seconds=t_plain, iterations=len(h_plain), dE_final=h_plain[-1]["dE"] if h_plain else None,
+                   reached=r_plain, exact_gradients=len(h_plain) * len(pool), history=h_plain),
+        learned=dict(seconds=t_learn, iterations=len(h_learn), dE_final=h_learn[-1]["dE"] if h_learn else None,
+                     reached=r_learn, exact_gradients=st.exact_gradients, full_screens=st.full_screens,
+                     subset_screens=st.subset_screens, judged=st.judged, hits=st.hits,
+                     mean_regret=float(np.mean(st.regret)) if st.regret else None, history=h_learn),
+        top_k=a.top_k, full_every=a.full_every)
+    print(json.dumps(out), flush=True)
+    return out
+
+
+if __name__ == "__main__":
+    main()
