@@ -154,6 +154,20 @@ int cvq_energy_and_grad(const cvq_sector *s, const cvq_pool *p, const int *op_id
                         const cvq_c128 *psi0, double *E_dev, double *grad_dev, void *workspace,
                         size_t workspace_bytes, void *stream);
 
+/* cvq_energy_and_grad with checkpointed forward states, for large sectors
+ * and deep ansatze: during the forward sweep psi is stored before the first
+ * segment (a block gate or a run of diagonal gates) whose first gate index
+ * reaches every, 2 every, ...; the reverse sweep replaces its recomputed psi
+ * by the stored copy at each of those points, so rounding drift of
+ * psi <- U^dag psi is bounded by `every` gates.  ckpt: device buffer of at
+ * least cvq_checkpoint_bytes(s, n, every) bytes, 256-byte aligned (may be
+ * NULL when that is 0).  Errors as cvq_energy_and_grad, plus EINVAL for
+ * every < 1 or a short checkpoint buffer. */
+int cvq_checkpoint_bytes(const cvq_sector *s, int n, int every, size_t *bytes);
+int cvq_energy_and_grad_ckpt(const cvq_sector *s, const cvq_pool *p, const int *op_ids, const double *theta, int n,
+                             const cvq_c128 *psi0, double *E_dev, double *grad_dev, int every, void *ckpt,
+                             size_t ckpt_bytes, void *workspace, size_t workspace_bytes, void *stream);
+
 /* One step of the Lanczos recurrence used for the exact ground energy E0
  * that defines Delta E = |E - E0| (Sec. IV.B stopping rule; exact
  * diagonalisation there).  Before the call the caller has w = H v and

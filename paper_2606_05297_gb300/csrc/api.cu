@@ -896,11 +896,26 @@ static void diag_run_arg(const cvq_sector* s, const cvq_pool* p, const int* ids,
     for (int nn = 0; nn < DMAX; ++nn) a.T[r][nn] = cdf_of(std::cos(ang[r][nn]), std::sin(ang[r][nn]));
 }
 
+// Checkpointed forward states: before the first segment whose first gate index
+// reaches j * every (j = 1, 2, ...), psi is copied to slot j - 1 of buf.
+struct Ckpt {
+  cdf* buf = nullptr;
+  int every = 0;
+  std::vector<int> seg_of;  // segment index at which each slot was taken
+};
+
 // U_n ... U_1 applied in place to the df state psi.
 static int forward_sweep(const cvq_sector* s, const cvq_pool* p, const int* ids, const double* theta, int n,
-                         const cdf* U, cdf* psi, cudaStream_t st) {
+                         const cdf* U, cdf* psi, cudaStream_t st, Ckpt* ck = nullptr) {
   const double dim = (double)s->S.dim;
-  for (const Seg& g : segments(p, ids, n)) {
+  const std::vector<Seg> segs = segments(p, ids, n);
+  for (size_t si = 0; si < segs.size(); ++si) {
+    const Seg& g = segs[si];
+    if (ck && si > 0 && g.k0 >= (int)(ck->seg_of.size() + 1) * ck->every) {
+      CVQ_CUDA(cudaMemcpyAsync(ck->buf + ck->seg_of.size() * (size_t)s->S.dim, psi, sizeof(cdf) * (size_t)s->S.dim,
+                               cudaMemcpyDeviceToDevice, st), "checkpoint copy");
+      ck->seg_of.push_back((int)si);
+    }
     if (g.diag) {
       DiagRunArg a;
       diag_run_arg(s, p, ids, theta, g, a);
@@ -931,9 +946,40 @@ extern "C" int cvq_apply_ansatz(const cvq_sector* s, const cvq_pool* p, const in
   return from_df(s, psi, psi_out, st);
 }
 
+static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
+                           const cvq_c128* psi0, double* E_dev, double* grad_dev, void* ws, size_t wsb,
+                           void* stream, Ckpt* ck);
+
 extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta,
                                    int n, const cvq_c128* psi0, double* E_dev, double* grad_dev, void* ws, size_t wsb,
                                    void* stream) {
+  return energy_and_grad(s, p, op_ids, theta, n, psi0, E_dev, grad_dev, ws, wsb, stream, nullptr);
+}
+
+extern "C" int cvq_checkpoint_bytes(const cvq_sector* s, int n, int every, size_t* bytes) {
+  if (!s || !bytes) return fail(CVQ_EINVAL, "null argument");
+  if (n < 0 || n > MAX_GATES || every < 1) return fail(CVQ_EINVAL, "need 0 <= n <= %d and every >= 1", MAX_GATES);
+  *bytes = (size_t)(n > 0 ? (n - 1) / every : 0) * (size_t)s->S.dim * sizeof(cdf);
+  return CVQ_OK;
+}
+
+extern "C" int cvq_energy_and_grad_ckpt(const cvq_sector* s, const cvq_pool* p, const int* op_ids,
+                                        const double* theta, int n, const cvq_c128* psi0, double* E_dev,
+                                        double* grad_dev, int every, void* ckpt, size_t ckpt_bytes, void* ws,
+                                        size_t wsb, void* stream) {
+  size_t need = 0;
+  if (int rc = cvq_checkpoint_bytes(s, n, every, &need)) return rc;
+  if (need > 0 && (!ckpt || ((uintptr_t)ckpt & 255))) return fail(CVQ_EINVAL, "checkpoint buffer NULL or not 256-byte aligned");
+  if (ckpt_bytes < need) return fail(CVQ_EINVAL, "checkpoint buffer of %zu bytes, %zu needed", ckpt_bytes, need);
+  Ckpt ck;
+  ck.buf = (cdf*)ckpt;
+  ck.every = every;
+  return energy_and_grad(s, p, op_ids, theta, n, psi0, E_dev, grad_dev, ws, wsb, stream, &ck);
+}
+
+static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
+                           const cvq_c128* psi0, double* E_dev, double* grad_dev, void* ws, size_t wsb,
+                           void* stream, Ckpt* ck) {
   if (!s || !p || !psi0 || !E_dev || (n > 0 && !grad_dev)) return fail(CVQ_EINVAL, "null argument");
   if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
   Layout l;
@@ -945,7 +991,7 @@ extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const
   double* partial = (double*)((char*)ws + l.partial);
   if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
   if (int rc = to_df(s, psi0, psi, st)) return rc;
-  if (int rc = forward_sweep(s, p, op_ids, theta, n, U, psi, st)) return rc;
+  if (int rc = forward_sweep(s, p, op_ids, theta, n, U, psi, st, ck)) return rc;
   double* pE = partial + (size_t)n * NBLK;
   if (int rc = run_apply_H(s, psi, lam, pE, st)) return rc;
   {
@@ -954,8 +1000,9 @@ extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const
   }
   const std::vector<Seg> segs = segments(p, op_ids, n);
   const double dim = (double)s->S.dim;
-  for (auto it = segs.rbegin(); it != segs.rend(); ++it) {
-    const Seg& g = *it;
+  int slot = ck ? (int)ck->seg_of.size() - 1 : -1;
+  for (int si = (int)segs.size() - 1; si >= 0; --si) {
+    const Seg& g = segs[si];
     if (g.diag) {
       DiagRunArg a;
       diag_run_arg(s, p, op_ids, theta, g, a);
@@ -966,6 +1013,11 @@ extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const
       const OpCost c = op_cost(s, p, op_ids[g.k0]);
       ProfScope ps(KK_ADJ, st, c.ab, c.af);
       CVQ_CUDA(launch_gate_adjoint(s->S, ga, p->P, psi, lam, partial + (size_t)g.k0 * NBLK, st), "adjoint gate");
+    }
+    if (slot >= 0 && ck->seg_of[slot] == si) {  // psi is now the state before segment si: restore the stored copy
+      CVQ_CUDA(cudaMemcpyAsync(psi, ck->buf + (size_t)slot * (size_t)s->S.dim, sizeof(cdf) * (size_t)s->S.dim,
+                               cudaMemcpyDeviceToDevice, st), "checkpoint restore");
+      --slot;
     }
   }
   {

@@ -448,3 +448,28 @@ class Batch:
         npar = C.c_int64()
         _check(lib().cvq_batch_info(self.h, C.byref(k), C.byref(it), C.byref(ly), C.byref(npar)), "cvq_batch_info")
         return dict(kernels_per_eval=k.value, items=it.value, layers=ly.value, params=npar.value)
+
+
+def energy_and_grad_ckpt(sector: Sector, pool: Pool, op_ids, theta, psi0, every: int, E=None, grad=None, ws=None,
+                         ckpt=None, stream=None):
+    """cvq_energy_and_grad with forward states checkpointed every `every` gates (see the header)."""
+    import torch
+    L = lib()
+    L.cvq_checkpoint_bytes.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+    L.cvq_energy_and_grad_ckpt.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                           C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                           C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]
+    n, ids, th = _ids_theta(op_ids, theta)
+    if E is None:
+        E = torch.empty(1, dtype=torch.float64, device=psi0.device)
+    if grad is None:
+        grad = torch.empty(max(n, 1), dtype=torch.float64, device=psi0.device)
+    ws, wsb = _ws(sector, pool, n, ws)
+    need = C.c_size_t()
+    _check(L.cvq_checkpoint_bytes(sector.h, n, int(every), C.byref(need)), "cvq_checkpoint_bytes")
+    if ckpt is None:
+        ckpt = torch.empty(max(int(need.value), 1), dtype=torch.uint8, device=psi0.device)
+    _check(L.cvq_energy_and_grad_ckpt(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n, _ptr(psi0),
+                                      _ptr(E), _ptr(grad), int(every), _ptr(ckpt), ckpt.numel(), _ptr(ws), wsb,
+                                      _stream(stream)), "cvq_energy_and_grad_ckpt")
+    return E, grad[:n]
