@@ -184,7 +184,9 @@ int cvq_lanczos_step(const cvq_sector *s, const cvq_c128 *v_prev, const cvq_c128
 /* Algorithmic cost of one application of pool element `op` on the whole
  * sector: bytes (amplitudes read + written, 16 B each) and flops (a complex
  * multiply-add counts 8) of the forward gate and of its reverse step in
- * cvq_energy_and_grad (gradient term + U^dag on psi and lambda).  Host only. */
+ * cvq_energy_and_grad (gradient term + U^dag on psi and lambda).  Blocks of
+ * one member (zero generator: the gate is the identity there) are not
+ * counted; the kernels skip them.  Host only. */
 int cvq_op_cost(const cvq_sector *s, const cvq_pool *p, int op, double *fwd_bytes, double *fwd_flops,
                 double *adj_bytes, double *adj_flops);
 

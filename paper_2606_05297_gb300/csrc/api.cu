@@ -488,6 +488,9 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
     const double target = std::max(total / (4.0 * NBLK), 1.0);
     t.chunk_base = (int)pb.chunks.size();
     for (int M = 0; M < t.nclass; ++M) {
+      int bm = 0;
+      for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) bm = std::max(bm, pb.blk[t.blk_base + bi].size);
+      if (bm < 2) continue;  // only one-member blocks: the gate is the identity on this class
       const int64_t cnt = S.bh2_off[M + 1] - S.bh2_off[M];
       if (cnt > INT32_MAX) return fail(CVQ_EINVAL, "too many orbits in one class");
       const int64_t per = NTHREADS * std::max<int64_t>(1, std::llround(target / (w[M] * NTHREADS)));
@@ -656,7 +659,9 @@ static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
     c.af = 24.0 * dim;
     return c;
   }
-  double ff = 0.0, af = 0.0;
+  // Blocks of one member have a zero generator: the gate is the identity there
+  // and the kernels skip them, so they count neither bytes nor flops.
+  double ff = 0.0, af = 0.0, amps = 0.0;
   for (int cls = 0; cls < t.nclass; ++cls) {
     double orbits;
     if (S.kind == CVQ_BH) {
@@ -670,12 +675,16 @@ static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
     double bf = 0.0, baf = 0.0;
     for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
       const int b = p->blk_size[t.blk_base + bi];
+      if (b < 2) continue;
       bf += 8.0 * b * b;
       baf += 8.0 * (2.0 * b * b + 3.0 * b - 2.0);
+      amps += orbits * b;
     }
     ff += orbits * bf;
     af += orbits * baf;
   }
+  c.fb = 32.0 * amps;
+  c.ab = 64.0 * amps;
   c.ff = ff;
   c.af = af;
   return c;

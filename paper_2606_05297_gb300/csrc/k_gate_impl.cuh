@@ -284,6 +284,7 @@ __device__ __forceinline__ void bkc_gate_range(const SectorDev& S, int gi, int g
     bkc_orbit(S, gi, gj, it, items, idx.f0, cls);
     for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
       const BlockDesc bd = m.B[bi];
+      if (bd.size < 2) continue;  // zero generator: identity, no gradient term
       apply_block<ADJ, REALU, false>(bd.size, m.U + bd.u_off, m.M + bd.mem_off, m.F + bd.f_off, cpr, cpi, idx, src,
                                      dst, lam, m.stg, m.sx, gacc);
     }
@@ -311,6 +312,7 @@ __device__ __forceinline__ void bh_gate_chunk(const SectorDev& S, const int32_t 
     const BhIdxT<int32_t> idx = bh_idx_of<int32_t>(S, Gs, gi, gj, w0);
     for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
       const BlockDesc bd = m.B[bi];
+      if (bd.size < 2) continue;  // zero generator: identity, no gradient term
       apply_block<ADJ, REALU, true>(bd.size, m.U + bd.u_off, m.M + bd.mem_off, m.F + bd.f_off, cpr, cpi, idx, src,
                                     dst, lam, m.stg, m.sx, gacc);
     }
