@@ -1015,7 +1015,21 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
     if (g.diag) {
       DiagRunArg a;
       diag_run_arg(s, p, op_ids, theta, g, a);
-      ProfScope ps(KK_ADJ_DIAG, st, 64.0 * dim, dim * (8.0 * s->S.L + 8.0 * a.npair + 24.0 + 4.0 * g.m));
+      // gradients of gates DIAG_ACC.. at the run's output state, before the reverse pass undoes the phases
+      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_ACC) {
+        DiagGradArg ga;
+        memset(&ga, 0, sizeof ga);
+        ga.m = std::min(DIAG_ACC, g.m - q0);
+        for (int q = 0; q < ga.m; ++q) {
+          ga.diag[q] = a.diag[q0 + q];
+          ga.gi[q] = a.gi[q0 + q];
+          ga.gj[q] = a.gj[q0 + q];
+        }
+        ProfScope ps(KK_ADJ_DIAG, st, 32.0 * dim, dim * (16.0 + 4.0 * ga.m));
+        CVQ_CUDA(launch_diag_grad(s->S, ga, psi, lam, partial + (size_t)(g.k0 + q0) * NBLK, st), "diagonal-run gradients");
+      }
+      ProfScope ps(KK_ADJ_DIAG, st, 64.0 * dim,
+                   dim * (8.0 * s->S.L + 8.0 * a.npair + 24.0 + 4.0 * std::min(g.m, DIAG_ACC)));
       CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, lam, partial + (size_t)g.k0 * NBLK, true, st), "adjoint diagonal run");
     } else {
       const GateArg ga = gate_arg(p, op_ids[g.k0], U + (size_t)g.k0 * p->ustride);

@@ -244,6 +244,7 @@ struct BuildArgs {
 // per cross-Kerr gate (built on the host in FP64, passed by value).  The
 // reverse pass forms every gradient of the run from the same (psi, lambda).
 constexpr int MAX_RUN = 32, MAX_RUN_PAIRS = 4;
+constexpr int DIAG_ACC = 8;  // gradient accumulators of one diagonal-run reverse pass
 struct DiagRunArg {
   int m, npair;
   int diag[MAX_RUN], gi[MAX_RUN], gj[MAX_RUN];   // per gate: f type (1..4) and modes
@@ -316,6 +317,13 @@ cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_dev, Po
 cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* src, cdf* dst, cudaStream_t st);
 cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial,
                                 cudaStream_t st);
+// Gradient-only pass over up to DIAG_ACC gates of a diagonal run (their f type and modes).
+struct DiagGradArg {
+  int m;
+  int diag[DIAG_ACC], gi[DIAG_ACC], gj[DIAG_ACC];
+};
+cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf* psi, const cdf* lam, double* partial,
+                             cudaStream_t st);
 cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
                             double* partial, bool adjoint, cudaStream_t st);
 cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const cdf* psi,

@@ -92,4 +92,31 @@ __device__ __forceinline__ void diag_run_range(const SectorDev& S, const int64_t
   }
 }
 
+// Gradient terms only, at a run's output state, for gates beyond the
+// accumulators of the reverse pass: acc[k] += Re(conj(lam) i f_k psi) over
+// x = x0, x0 + step, ... < x1 (no table, no write).
+template <int KIND, int NACC, class A>
+__device__ __forceinline__ void diag_grad_range(const SectorDev& S, const int64_t (*Gs)[DMAX + 1], const A& a,
+                                                const cdf* __restrict__ psi, const cdf* __restrict__ lam, int64_t x0,
+                                                int64_t x1, int64_t step, dfacc (&acc)[NACC]) {
+  for (int64_t x = x0; x < x1; x += step) {
+    const uint64_t w = (KIND == CVQ_BKC) ? bkc_unrank(x, S) : bh_unrank(x, S.L, S.N, Gs);
+    const cdf ps = psi[x], la = lam[x];
+    dfacc c;
+    acc_zero(c);
+    acc_mac(c, im_of(la), re_of(ps));
+    acc_mac(c, df_neg(re_of(la)), im_of(ps));
+    const df cv = acc_get(c);
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) {
+      if (k < a.m) {
+        const int ni = occ_get(w, a.gi[k]);
+        const int dg = a.diag[k];
+        const int f = (dg == 1) ? ni * ni : (dg == 2) ? ni * (ni - 1) : (dg == 3) ? ni : ni * occ_get(w, a.gj[k]);
+        if (f) acc_macf(acc[k], cv, (float)f);
+      }
+    }
+  }
+}
+
 }  // namespace cvq

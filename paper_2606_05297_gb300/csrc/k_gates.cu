@@ -115,20 +115,50 @@ __global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ S
   for (int e = threadIdx.x; e < a.npair * DMAX * DMAX; e += blockDim.x)
     TP[e / (DMAX * DMAX)][e % (DMAX * DMAX)] = a.TP[e / (DMAX * DMAX)][e % (DMAX * DMAX)];
   __syncthreads();
-  dfacc acc[MAX_RUN];
+  // Reverse: gradients of the run's first DIAG_ACC gates; the host launches
+  // k_diag_grad beforehand for the rest.
+  dfacc acc[DIAG_ACC];
 #pragma unroll
-  for (int k = 0; k < MAX_RUN; ++k) acc_zero(acc[k]);
-  diag_run_range<KIND, ADJ, MAX_RUN>(S, Gs, T, TP, a, src, dst, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
-                            (int64_t)gridDim.x * blockDim.x, acc);
+  for (int k = 0; k < DIAG_ACC; ++k) acc_zero(acc[k]);
+  diag_run_range<KIND, ADJ, DIAG_ACC>(S, Gs, T, TP, a, src, dst, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                      S.dim, (int64_t)gridDim.x * blockDim.x, acc);
   if (ADJ) {
 #pragma unroll
-    for (int k = 0; k < MAX_RUN; ++k) {
+    for (int k = 0; k < DIAG_ACC; ++k) {
       if (k < a.m) {
         const double s = block_sum(acc_to_double(acc[k]));
         if (threadIdx.x == 0) partial[(size_t)k * NBLK + blockIdx.x] = s;
       }
     }
   }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS) k_diag_grad(const __grid_constant__ SectorDev S,
+                                                        const __grid_constant__ DiagGradArg a, const cdf* psi,
+                                                        const cdf* lam, double* partial) {
+  __shared__ int64_t Gs[LMAX][DMAX + 1];
+  if (KIND == CVQ_BH) load_G(Gs, S);
+  __syncthreads();
+  dfacc acc[DIAG_ACC];
+#pragma unroll
+  for (int k = 0; k < DIAG_ACC; ++k) acc_zero(acc[k]);
+  diag_grad_range<KIND, DIAG_ACC>(S, Gs, a, psi, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
+                                  (int64_t)gridDim.x * blockDim.x, acc);
+#pragma unroll
+  for (int k = 0; k < DIAG_ACC; ++k) {
+    if (k < a.m) {
+      const double s = block_sum(acc_to_double(acc[k]));
+      if (threadIdx.x == 0) partial[(size_t)k * NBLK + blockIdx.x] = s;
+    }
+  }
+}
+
+cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf* psi, const cdf* lam, double* partial,
+                             cudaStream_t st) {
+  if (S.kind == CVQ_BH) k_diag_grad<CVQ_BH><<<NBLK, NTHREADS, 0, st>>>(S, a, psi, lam, partial);
+  else k_diag_grad<CVQ_BKC><<<NBLK, NTHREADS, 0, st>>>(S, a, psi, lam, partial);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
