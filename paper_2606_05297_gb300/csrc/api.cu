@@ -1,6 +1,7 @@
 // api.cu -- the C-ABI of libcvq.so (include/cvq.h): sector indexer and
 // Hamiltonian tables, pool builder with per-block eigendecompositions, and the
 // entry points that enqueue the kernels.
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -600,24 +601,27 @@ extern "C" void cvq_destroy_pool(cvq_pool* p) {
 // ------------------------------------------------------------------ workspace
 
 struct Layout {
-  size_t psi, lam, U, partial, total;
+  size_t psi, lam, U, partial, z, total;
 };
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // psi and lambda (df states, 16 B per amplitude), per-call block unitaries
-// (n x ustride df complex), reduction partials ((max(n, K) + 1) x NBLK).
+// (n x ustride df complex), reduction partials ((max(n, 5K) + 1) x NBLK: the
+// screen keeps two rows per distinct shift, at most 2K of them, and one per
+// diagonal function), and the screen's reduced shift sums (5K + 1).
 static Layout layout(const cvq_sector* s, const cvq_pool* p, int n_max) {
   Layout l;
   const size_t dim = (size_t)s->S.dim;
   const int K = p ? p->K : 0;
   const int ust = p ? p->ustride : PHASE_TABLE;
-  const int nred = std::max(std::max(n_max, K), 1) + 1;
+  const int nred = std::max(std::max(n_max, 5 * K), 1) + 1;
   l.psi = 0;
   l.lam = al256(l.psi + dim * sizeof(cdf));
   l.U = al256(l.lam + dim * sizeof(cdf));
   l.partial = al256(l.U + (size_t)std::max(n_max, 0) * ust * sizeof(cdf));
-  l.total = al256(l.partial + (size_t)nred * NBLK * sizeof(double));
+  l.z = al256(l.partial + (size_t)nred * NBLK * sizeof(double));
+  l.total = al256(l.z + (size_t)(5 * K + 1) * sizeof(double));
   return l;
 }
 
@@ -784,26 +788,71 @@ extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq
     sub.n = p->K;
     for (int k = 0; k < p->K; ++k) sub.idx[k] = k;
   }
+  // distinct shifts (canonical: lower mode first) and diagonal functions
+  static thread_local ScreenArg sa;
+  static thread_local ScreenMap sm;
+  sa.nsh = sa.ndg = 0;
+  sm.n = sub.n;
+  std::map<std::array<int, 4>, int> shift_id, diag_id;
+  auto shift = [&](int i, int di, int j, int dj) {
+    if (j >= 0 && j < i) {
+      std::swap(i, j);
+      std::swap(di, dj);
+    }
+    if (j < 0) dj = 0;
+    const std::array<int, 4> key{i, di, j, dj};
+    auto it = shift_id.find(key);
+    if (it != shift_id.end()) return it->second;
+    sa.sh[sa.nsh] = make_int4(i, di, j, dj);
+    shift_id[key] = sa.nsh;
+    return sa.nsh++;
+  };
+  for (int k = 0; k < sub.n; ++k) {
+    const int op = sub.idx[k];
+    const TypeDesc& t = p->types[p->op_type[op]];
+    const int i = p->op_i[op], j = t.single ? -1 : p->op_j[op];
+    sm.cp[k] = make_double2(t.cp_re, t.cp_im);
+    if (t.diag) {
+      const std::array<int, 4> key{t.diag, i, t.diag == 4 ? j : -1, 0};
+      auto it = diag_id.find(key);
+      int d;
+      if (it != diag_id.end()) {
+        d = it->second;
+      } else {
+        if (sa.ndg == MAX_DIAGF) return fail(CVQ_EINVAL, "more than %d distinct diagonal generators", MAX_DIAGF);
+        d = sa.ndg++;
+        sa.dg[d] = make_int4(key[0], key[1], key[2], 0);
+        diag_id[key] = d;
+      }
+      sm.e[k] = make_int4(1, d, 0, 0);
+    } else {
+      const int sp = shift(i, t.di, j, t.dj), sn = shift(i, -t.di, j, -t.dj);
+      sm.e[k] = make_int4(0, sp, sn, 0);
+    }
+  }
   Layout l;
   if (int rc = check_ws(s, p, 0, ws, wsb, l)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   cdf* vpsi = (cdf*)((char*)ws + l.psi);
   cdf* vsig = (cdf*)((char*)ws + l.lam);
   double* partial = (double*)((char*)ws + l.partial);
+  double* z = (double*)((char*)ws + l.z);
   if (int rc = to_df(s, psi, vpsi, st)) return rc;
   if (int rc = run_apply_H(s, vpsi, vsig, nullptr, st)) return rc;
+  const int rows = 2 * sa.nsh + sa.ndg;
   {
-    // per screened element and amplitude: the generator row (2 complex MACs, or 1
-    // for a diagonal generator) and its overlap with sigma (1 complex MAC)
-    double fl = 0.0;
-    for (int k = 0; k < sub.n; ++k) fl += (double)s->S.dim * (p->types[p->op_type[sub.idx[k]]].diag ? 16.0 : 24.0);
-    ProfScope ps(KK_SCREEN, st, 32.0 * (double)s->S.dim, fl);
-    CVQ_CUDA(launch_screen(s->S, p->ops_dev, sub, vpsi, vsig, partial, st), "screen");
+    // per chunk of shifts one pass over sigma, and per shift one neighbour read of psi
+    const double dim = (double)s->S.dim;
+    const int chunks = (sa.nsh + SCREEN_CHUNK - 1) / SCREEN_CHUNK + (sa.ndg + SCREEN_CHUNK - 1) / SCREEN_CHUNK;
+    const double fl = dim * (48.0 * sa.nsh + 8.0 * sa.ndg);
+    ProfScope ps(KK_SCREEN, st, 16.0 * dim * (chunks + sa.nsh + (sa.ndg ? 1 : 0)), fl);
+    CVQ_CUDA(launch_screen(s->S, sa, vpsi, vsig, partial, st), "screen");
   }
   {
-    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * sub.n, (double)NBLK * sub.n);
-    CVQ_CUDA(launch_reduce(partial, sub.n, NBLK, 2.0, grad_dev, st), "reduce");
+    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * rows, (double)NBLK * rows);
+    CVQ_CUDA(launch_reduce(partial, rows, NBLK, 1.0, z, st), "reduce");
   }
+  CVQ_CUDA(launch_screen_epilogue(sm, sa.nsh, z, grad_dev, st), "screen epilogue");
   return CVQ_OK;
 }
 

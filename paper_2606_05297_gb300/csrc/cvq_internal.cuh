@@ -304,6 +304,22 @@ struct SubsetArg {
   int idx[MAX_GATES];
 };
 
+// The distinct ladder shifts and diagonal functions of a screened subset.
+constexpr int SCREEN_CHUNK = 8, MAX_SHIFTS = 2 * MAX_GATES, MAX_DIAGF = 256;
+struct ScreenArg {
+  int nsh, ndg;
+  int4 sh[MAX_SHIFTS];  // (i, di, j, dj); j < 0 for a single-mode move
+  int4 dg[MAX_DIAGF];   // (f type 1..4 as TypeDesc::diag, i, j, 0)
+};
+
+// Per screened element: e = (1 diagonal / 0 shift pair, plus-shift or
+// diagonal index, minus-shift index, 0) and c_plus.
+struct ScreenMap {
+  int n;
+  int4 e[MAX_GATES];
+  double2 cp[MAX_GATES];
+};
+
 // ------------------------------------------------------------- launchers
 // All launchers enqueue on `stream` and return the launch status.  States
 // (cdf*) are df complex; the C ABI's complex128 buffers go through
@@ -326,8 +342,9 @@ cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf
                              cudaStream_t st);
 cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
                             double* partial, bool adjoint, cudaStream_t st);
-cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const cdf* psi,
-                          const cdf* sigma, double* partial, cudaStream_t st);
+cudaError_t launch_screen(const SectorDev& S, const ScreenArg& a, const cdf* psi, const cdf* sigma, double* partial,
+                          cudaStream_t st);
+cudaError_t launch_screen_epilogue(const ScreenMap& m, int nsh, const double* z, double* grad, cudaStream_t st);
 // State features (<n_r>, <n_r^2>, <a_i^dag a_j>) as (2L + 2 npairs) rows of partials.
 cudaError_t launch_features(const SectorDev& S, const double2* psi, const int* pi, const int* pj, int npairs,
                             double* partial, cudaStream_t st);

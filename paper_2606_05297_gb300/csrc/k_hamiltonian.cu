@@ -38,16 +38,22 @@ cudaError_t launch_apply_H(const SectorDev& S, const cdf* psi, cdf* sigma, doubl
 
 // ------------------------------------------------------------ screen
 
-// c times a df, exact when c is 0, +-1 or a power of two (all c_plus here)
-__device__ __forceinline__ df df_scale(df a, float c) { return df_make(a.h * c, a.l * c); }
-
-// Row rule of a pool generator: (A psi)[x] = cp F(x, x+m) psi[x+m]
-// - conj(cp) F(x, x-m) psi[x-m] for the move m = (di on mode i, dj on mode j),
-// or i f(n(x)) psi[x] for a diagonal generator.  Per element the kernel
-// accumulates Re sum_x conj(sigma[x]) (A psi)[x].
+// Pool screen, Eq. (grad): for a generator A = cp G - conj(cp) G^dag whose
+// ladder string G moves x by delta (and G^dag by -delta),
+//   Re <sigma|A psi> = Re(cp Z_delta) - Re(conj(cp) Z_{-delta}),
+//   Z_delta = sum_x F_delta(x) conj(sigma[x]) psi[x + delta],
+// with F_delta(x) the ladder factor of the move; for a diagonal generator
+// A = i f(n), Re <sigma|A psi> = sum_x f(x) Re(conj(sigma[x]) i psi[x]).
+// Every pool element that moves by the same delta (both phases of a beam
+// splitter or squeezer, for instance) shares one Z, so the kernel streams
+// one neighbour read per distinct shift instead of two per element.  Shifts
+// are taken SCREEN_CHUNK at a time: a chunk's accumulators stay in registers
+// while each CTA walks its share of the sector, then leave one partial per CTA
+// (rows 2s and 2s + 1 for Re and Im of shift s, row 2 nsh + d for diagonal
+// function d).
 template <int KIND>
-__global__ void __launch_bounds__(NTHREADS) k_screen(const __grid_constant__ SectorDev S, const GateArg* __restrict__ pool,
-                                                     const __grid_constant__ SubsetArg sub, const cdf* __restrict__ psi,
+__global__ void __launch_bounds__(NTHREADS) k_screen(const __grid_constant__ SectorDev S,
+                                                     const __grid_constant__ ScreenArg a, const cdf* __restrict__ psi,
                                                      const cdf* __restrict__ sigma, double* __restrict__ partial) {
   __shared__ int64_t Gs[LMAX][DMAX + 1];
   __shared__ float2 sq[DMAX][5];
@@ -55,75 +61,104 @@ __global__ void __launch_bounds__(NTHREADS) k_screen(const __grid_constant__ Sec
   for (int e = threadIdx.x; e < DMAX * 5; e += blockDim.x) (&sq[0][0])[e] = (&S.tab->sq[0][0])[e];
   __syncthreads();
   const int L = S.L, Dm1 = S.D - 1;
-  for (int k = 0; k < sub.n; ++k) {
-    const GateArg& op = pool[sub.idx[k]];
-    const int i = op.i, j = op.t.single ? -1 : op.j;
-    const int di = op.t.di, dj = op.t.dj, dg = op.t.diag;
-    const float cpr = (float)op.t.cp_re, cpi = (float)op.t.cp_im;
-    dfacc acc;
-    acc_zero(acc);
+  const int nc_sh = (a.nsh + SCREEN_CHUNK - 1) / SCREEN_CHUNK, nc_dg = (a.ndg + SCREEN_CHUNK - 1) / SCREEN_CHUNK;
+  for (int c = 0; c < nc_sh + nc_dg; ++c) {
+    const bool isdg = c >= nc_sh;
+    const int base = (isdg ? c - nc_sh : c) * SCREEN_CHUNK;
+    const int cnt = min(SCREEN_CHUNK, (isdg ? a.ndg : a.nsh) - base);
+    dfacc zr[SCREEN_CHUNK], zi[SCREEN_CHUNK];
+#pragma unroll
+    for (int k = 0; k < SCREEN_CHUNK; ++k) {
+      acc_zero(zr[k]);
+      acc_zero(zi[k]);
+    }
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x) {
       uint64_t wR = 0;
       const uint64_t w = unrank<KIND>(x, S, Gs, &wR);
       const cdf s = sigma[x];
-      const int ni = occ_get(w, i);
-      if (dg) {
-        const int f = (dg == 1) ? ni * ni : (dg == 2) ? ni * (ni - 1) : (dg == 3) ? ni : ni * occ_get(w, j);
-        if (f) {
-          const cdf p = psi[x];
-          dfacc c;  // Re(conj(s) * i f p) = f (s.im p.re - s.re p.im)
-          acc_zero(c);
-          acc_mac(c, im_of(s), re_of(p));
-          acc_mac(c, df_neg(re_of(s)), im_of(p));
-          acc_macf(acc, acc_get(c), (float)f);
+      if (isdg) {
+        const cdf p = psi[x];
+        dfacc cc;  // Re(conj(s) i p) = s.im p.re - s.re p.im
+        acc_zero(cc);
+        acc_mac(cc, im_of(s), re_of(p));
+        acc_mac(cc, df_neg(re_of(s)), im_of(p));
+        const df cv = acc_get(cc);
+#pragma unroll
+        for (int k = 0; k < SCREEN_CHUNK; ++k) {
+          if (k < cnt) {
+            const int4 d = a.dg[base + k];
+            const int ni = occ_get(w, d.y);
+            const int f = (d.x == 1) ? ni * ni : (d.x == 2) ? ni * (ni - 1) : (d.x == 3) ? ni : ni * occ_get(w, d.z);
+            if (f) acc_macf(zr[k], cv, (float)f);
+          }
         }
         continue;
       }
-      const int nj = (j >= 0) ? occ_get(w, j) : 0;
-      const int64_t f = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
-      if (ni + di >= 0 && ni + di <= Dm1 && (j < 0 || (nj + dj >= 0 && nj + dj <= Dm1))) {
-        df F = df_make(sq[ni][di + 2].x, sq[ni][di + 2].y);
-        if (j >= 0) F = df_mul(F, df_make(sq[nj][dj + 2].x, sq[nj][dj + 2].y));
-        const cdf q = psi[moved_index<KIND>(x, w, wR, f, i, di, j, dj, S, Gs)];
-        dfacc z;  // Re(cp conj(s) q)
-        acc_zero(z);
-        if (cpr != 0.f) {
-          acc_mac(z, df_scale(re_of(s), cpr), re_of(q));
-          acc_mac(z, df_scale(im_of(s), cpr), im_of(q));
-        }
-        if (cpi != 0.f) {
-          acc_mac(z, df_scale(re_of(s), -cpi), im_of(q));
-          acc_mac(z, df_scale(im_of(s), cpi), re_of(q));
-        }
-        acc_mac(acc, F, acc_get(z));
-      }
-      if (ni - di >= 0 && ni - di <= Dm1 && (j < 0 || (nj - dj >= 0 && nj - dj <= Dm1))) {
-        df F = df_make(sq[ni][2 - di].x, sq[ni][2 - di].y);
-        if (j >= 0) F = df_mul(F, df_make(sq[nj][2 - dj].x, sq[nj][2 - dj].y));
-        const cdf q = psi[moved_index<KIND>(x, w, wR, f, i, -di, j, -dj, S, Gs)];
-        dfacc z;  // Re(-conj(cp) conj(s) q)
-        acc_zero(z);
-        if (cpr != 0.f) {
-          acc_mac(z, df_scale(re_of(s), -cpr), re_of(q));
-          acc_mac(z, df_scale(im_of(s), -cpr), im_of(q));
-        }
-        if (cpi != 0.f) {
-          acc_mac(z, df_scale(re_of(s), -cpi), im_of(q));
-          acc_mac(z, df_scale(im_of(s), cpi), re_of(q));
-        }
-        acc_mac(acc, F, acc_get(z));
+      const int64_t fx = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
+#pragma unroll
+      for (int k = 0; k < SCREEN_CHUNK; ++k) {
+        if (k >= cnt) continue;
+        const int4 h = a.sh[base + k];  // (i, di, j, dj), j < 0: single mode
+        const int ni = occ_get(w, h.x), nj = (h.z >= 0) ? occ_get(w, h.z) : 0;
+        if (ni + h.y < 0 || ni + h.y > Dm1 || (h.z >= 0 && (nj + h.w < 0 || nj + h.w > Dm1))) continue;
+        df F = df_make(sq[ni][h.y + 2].x, sq[ni][h.y + 2].y);
+        if (h.z >= 0) F = df_mul(F, df_make(sq[nj][h.w + 2].x, sq[nj][h.w + 2].y));
+        const cdf q = psi[moved_index<KIND>(x, w, wR, fx, h.x, h.y, h.z, h.w, S, Gs)];
+        dfacc tr, ti;  // conj(s) q
+        acc_zero(tr);
+        acc_zero(ti);
+        acc_mac(tr, re_of(s), re_of(q));
+        acc_mac(tr, im_of(s), im_of(q));
+        acc_mac(ti, re_of(s), im_of(q));
+        acc_mac(ti, df_neg(im_of(s)), re_of(q));
+        acc_mac(zr[k], F, acc_get(tr));
+        acc_mac(zi[k], F, acc_get(ti));
       }
     }
-    const double r = block_sum(acc_to_double(acc));
-    if (threadIdx.x == 0) partial[(size_t)k * NBLK + blockIdx.x] = r;
+#pragma unroll
+    for (int k = 0; k < SCREEN_CHUNK; ++k) {
+      if (k >= cnt) continue;
+      if (isdg) {
+        const double r = block_sum(acc_to_double(zr[k]));
+        if (threadIdx.x == 0) partial[(size_t)(2 * a.nsh + base + k) * NBLK + blockIdx.x] = r;
+      } else {
+        const double r = block_sum(acc_to_double(zr[k]));
+        const double i = block_sum(acc_to_double(zi[k]));
+        if (threadIdx.x == 0) {
+          partial[(size_t)(2 * (base + k)) * NBLK + blockIdx.x] = r;
+          partial[(size_t)(2 * (base + k) + 1) * NBLK + blockIdx.x] = i;
+        }
+      }
+    }
   }
 }
 
-cudaError_t launch_screen(const SectorDev& S, const GateArg* pool_ops, const SubsetArg& sub, const cdf* psi,
-                          const cdf* sigma, double* partial, cudaStream_t st) {
-  if (sub.n <= 0) return cudaSuccess;
-  if (S.kind == CVQ_BH) k_screen<CVQ_BH><<<NBLK, NTHREADS, 0, st>>>(S, pool_ops, sub, psi, sigma, partial);
-  else k_screen<CVQ_BKC><<<NBLK, NTHREADS, 0, st>>>(S, pool_ops, sub, psi, sigma, partial);
+// g_k = 2 [Re(cp Z_+) - Re(conj(cp) Z_-)], or 2 D_d for a diagonal generator.
+__global__ void k_screen_epilogue(const __grid_constant__ ScreenMap m, int nsh, const double* __restrict__ z,
+                                  double* __restrict__ grad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.n) return;
+  const int4 e = m.e[k];
+  const double2 cp = m.cp[k];
+  if (e.x) {
+    grad[k] = 2.0 * z[2 * nsh + e.y];
+  } else {
+    const double pr = z[2 * e.y], pi = z[2 * e.y + 1], mr = z[2 * e.z], mi = z[2 * e.z + 1];
+    grad[k] = 2.0 * ((cp.x * pr - cp.y * pi) - (cp.x * mr + cp.y * mi));
+  }
+}
+
+cudaError_t launch_screen(const SectorDev& S, const ScreenArg& a, const cdf* psi, const cdf* sigma, double* partial,
+                          cudaStream_t st) {
+  if (a.nsh + a.ndg <= 0) return cudaSuccess;
+  if (S.kind == CVQ_BH) k_screen<CVQ_BH><<<NBLK, NTHREADS, 0, st>>>(S, a, psi, sigma, partial);
+  else k_screen<CVQ_BKC><<<NBLK, NTHREADS, 0, st>>>(S, a, psi, sigma, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_screen_epilogue(const ScreenMap& m, int nsh, const double* z, double* grad, cudaStream_t st) {
+  if (m.n <= 0) return cudaSuccess;
+  k_screen_epilogue<<<(m.n + 127) / 128, 128, 0, st>>>(m, nsh, z, grad);
   return cudaGetLastError();
 }
 
