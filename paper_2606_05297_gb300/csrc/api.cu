@@ -862,12 +862,14 @@ static int prepare_gates(const cvq_sector*, const cvq_pool* p, const int* op_ids
   if (n > 0 && (!op_ids || !theta)) return fail(CVQ_EINVAL, "null op_ids / theta");
   BuildArgs a;
   a.n = n;
+  a.maxblk = 0;
   a.ustride = p->ustride;
   for (int k = 0; k < n; ++k) {
     if (op_ids[k] < 0 || op_ids[k] >= p->K) return fail(CVQ_EINVAL, "op_ids[%d] = %d outside the pool", k, op_ids[k]);
     if (!std::isfinite(theta[k])) return fail(CVQ_EINVAL, "theta[%d] is not finite", k);
     a.type_of[k] = p->op_type[op_ids[k]];
     a.theta[k] = theta[k];
+    if (!p->types[a.type_of[k]].diag) a.maxblk = std::max(a.maxblk, p->types[a.type_of[k]].nblocks);
   }
   ProfScope ps(KK_BUILD, st, 0.0, 0.0);
   CVQ_CUDA(launch_build_gates(a, p->types_dev, p->P, U, st), "build gates");

@@ -82,6 +82,7 @@ struct cvq_batch {
   std::vector<char> layer_adj;
   int n_red = 0, n_gates = 0, n_items = 0, n_theta = 0;
   size_t smem = 0;
+  int maxblk = 0;  // most blocks of any block-gate type of the batch's pools
   // graph
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -301,7 +302,7 @@ int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
   cudaStream_t st = b->cap;
   BCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
   cudaError_t e = cudaMemsetAsync(b->counters_d, 0, sizeof(int) * b->layer_n.size(), st);
-  if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->ids_d, theta, b->active_d, st);
+  if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
   const int grid = b->sms * b->ctas_per_sm;
   for (size_t l = 0; l < b->layer_n.size() && e == cudaSuccess; ++l)
     e = launch_batch_layer(b->kind, b->layer_adj[l] != 0, grid, b->smem, b->inst_d, b->segs_d,
@@ -366,7 +367,10 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
     }
     b->S[i] = *S;
     for (int t = 0; t < p.ntypes; ++t)
-      if (!p.types[t].diag) smem = std::max(smem, gate_smem_bytes(p.types[t], S->kind));
+      if (!p.types[t].diag) {
+        smem = std::max(smem, gate_smem_bytes(p.types[t], S->kind));
+        b->maxblk = std::max(b->maxblk, p.types[t].nblocks);
+      }
     offs[i] = total;
     total += 2 * a256(sizeof(cdf) * (size_t)S->dim) + a256(sizeof(cdf) * (size_t)std::max(n_max, 1) * p.ustride);
   }

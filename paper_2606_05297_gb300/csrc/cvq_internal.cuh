@@ -233,6 +233,7 @@ __host__ __device__ __forceinline__ size_t gate_smem_bytes(const TypeDesc& t, in
 // Per-call list of gates for the unitary build kernel (passed by value).
 struct BuildArgs {
   int n;
+  int maxblk;            // most blocks of any gate of the call (grid y)
   int ustride;           // complex entries reserved per gate
   int type_of[MAX_GATES];
   double theta[MAX_GATES];
@@ -289,8 +290,8 @@ struct BRed {
   int inst, out, is_energy, slot0, count, stride;
 };
 
-cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, const int* ids, const double* theta,
-                               const int* active, cudaStream_t st);
+cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, int maxblk, const int* ids,
+                               const double* theta, const int* active, cudaStream_t st);
 cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const BInst* insts, const BSeg* segs,
                                const BItem* items, int nitems, int* counter, const int* ids, const double* theta,
                                const int* active, double* partial, cudaStream_t st);

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(128) k_batch_build(const BInst* __restrict__ i
   const TypeDesc& t = I.ops[op].t;
   if (t.diag) return;
   __shared__ double2 ph[BMAX];
-  build_gate_unitaries(t, theta[I.theta_off + ik.y], I.P, I.U + (size_t)ik.y * I.ustride, ph);
+  build_block_unitary(t, theta[I.theta_off + ik.y], I.P, I.U + (size_t)ik.y * I.ustride, blockIdx.y, ph);
 }
 
 // Shared state of one layer CTA.
@@ -199,10 +199,10 @@ __global__ void k_batch_reduce(const BRed* __restrict__ red, int n, const double
   else grad[d.out] = 2.0 * v;
 }
 
-cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, const int* ids, const double* theta,
-                               const int* active, cudaStream_t st) {
-  if (ngates <= 0) return cudaSuccess;
-  k_batch_build<<<ngates, 128, 0, st>>>(insts, gates, ngates, ids, theta, active);
+cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, int maxblk, const int* ids,
+                               const double* theta, const int* active, cudaStream_t st) {
+  if (ngates <= 0 || maxblk <= 0) return cudaSuccess;
+  k_batch_build<<<dim3(ngates, maxblk), 128, 0, st>>>(insts, gates, ngates, ids, theta, active);
   return cudaGetLastError();
 }
 

@@ -327,32 +327,33 @@ __device__ __forceinline__ void bh_gate_chunk(const SectorDev& S, const int32_t 
 // tridiagonal block, so exp(theta A) has purely real entries (real
 // generator) or real entries at even k - l and imaginary ones at odd k - l;
 // the other component is zero up to rounding and is set to zero.
-__device__ __forceinline__ void build_gate_unitaries(const TypeDesc& t, double th, const PoolDev& P, cdf* Ug,
-                                                     double2* ph) {
-  for (int bi = 0; bi < t.nblocks; ++bi) {
-    const BlockDesc bd = P.blk[t.blk_base + bi];
-    const int b = bd.size;
-    if (threadIdx.x < b) {
-      double s, c;
-      sincos(th * P.lam[t.lam_base + bd.ev_off + threadIdx.x], &s, &c);
-      ph[threadIdx.x] = make_double2(c, s);
+// One block bi of one gate (the calling CTA; blocks of one member are never
+// read by the gate kernels and are left out).
+__device__ __forceinline__ void build_block_unitary(const TypeDesc& t, double th, const PoolDev& P, cdf* Ug, int bi,
+                                                    double2* ph) {
+  if (bi >= t.nblocks) return;
+  const BlockDesc bd = P.blk[t.blk_base + bi];
+  const int b = bd.size;
+  if (b < 2) return;
+  if (threadIdx.x < b) {
+    double s, c;
+    sincos(th * P.lam[t.lam_base + bd.ev_off + threadIdx.x], &s, &c);
+    ph[threadIdx.x] = make_double2(c, s);
+  }
+  __syncthreads();
+  const double2* Vb = reinterpret_cast<const double2*>(P.V) + t.v_base + bd.u_off;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int k = e / b, l = e - k * b;
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < b; ++q) {
+      const double2 vk = Vb[k * b + q], vl = Vb[l * b + q], p = ph[q];
+      const double xr = vk.x * p.x - vk.y * p.y, xi = vk.x * p.y + vk.y * p.x;  // vk p
+      re += xr * vl.x + xi * vl.y;                                               // * conj(vl)
+      im += xi * vl.x - xr * vl.y;
     }
-    __syncthreads();
-    const double2* Vb = reinterpret_cast<const double2*>(P.V) + t.v_base + bd.u_off;
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-      const int k = e / b, l = e - k * b;
-      double re = 0.0, im = 0.0;
-      for (int q = 0; q < b; ++q) {
-        const double2 vk = Vb[k * b + q], vl = Vb[l * b + q], p = ph[q];
-        const double xr = vk.x * p.x - vk.y * p.y, xi = vk.x * p.y + vk.y * p.x;  // vk p
-        re += xr * vl.x + xi * vl.y;                                               // * conj(vl)
-        im += xi * vl.x - xr * vl.y;
-      }
-      if (t.realu || ((k - l) & 1) == 0) im = 0.0;
-      else re = 0.0;
-      Ug[bd.u_off + e] = make_cdf(df_from_double(re), df_from_double(im));
-    }
-    __syncthreads();
+    if (t.realu || ((k - l) & 1) == 0) im = 0.0;
+    else re = 0.0;
+    Ug[bd.u_off + e] = make_cdf(df_from_double(re), df_from_double(im));
   }
 }
 

@@ -44,7 +44,8 @@ cudaError_t launch_from_df(int64_t dim, const cdf* src, double2* dst, cudaStream
 
 // ------------------------------------------------------------ build
 
-// Block unitaries of every gate g of the call (one CTA per gate).
+// Block unitaries of every gate g of the call: one CTA per (gate, block), so
+// the FP64 work spreads over the GPU.
 __global__ void k_build(const __grid_constant__ BuildArgs a, const TypeDesc* __restrict__ types, PoolDev P,
                         cdf* __restrict__ U) {
   const int g = blockIdx.x;
@@ -52,12 +53,12 @@ __global__ void k_build(const __grid_constant__ BuildArgs a, const TypeDesc* __r
   const TypeDesc& t = types[a.type_of[g]];
   if (t.diag) return;  // diagonal gates are applied from per-run phase tables
   __shared__ double2 ph[BMAX];
-  build_gate_unitaries(t, a.theta[g], P, U + (size_t)g * a.ustride, ph);
+  build_block_unitary(t, a.theta[g], P, U + (size_t)g * a.ustride, blockIdx.y, ph);
 }
 
 cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_dev, PoolDev P, cdf* U, cudaStream_t st) {
-  if (a.n <= 0) return cudaSuccess;
-  k_build<<<a.n, 128, 0, st>>>(a, types_dev, P, U);
+  if (a.n <= 0 || a.maxblk <= 0) return cudaSuccess;
+  k_build<<<dim3(a.n, a.maxblk), 128, 0, st>>>(a, types_dev, P, U);
   return cudaGetLastError();
 }
 
