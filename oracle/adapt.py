@@ -31,10 +31,15 @@ def select(g):
 
 
 def run(sector, pool, psi_init, warm_ops=(), warm_theta=(), max_ops=160, grad_tol=1e-6, E0=None,
-        energy_tol=None, bfgs_max_iter=1000, warm_gtol=1e-9):
+        energy_tol=None, bfgs_max_iter=1000, warm_gtol=1e-9, hessian_recycling=False, fix_warm=False):
+    """hessian_recycling (App. D): each BFGS starts from the previous one's
+    final inverse Hessian, extended by an identity row and column for the new
+    parameter.  fix_warm (App. D): the warm-up layer keeps the parameters of
+    its initial optimisation; ADAPT then grows from the warm-up state."""
     ops = list(warm_ops)
     theta = np.array(warm_theta, dtype=np.float64)
     trace = []
+    H = None
 
     def fg(th):
         E, g = sector.energy_and_grad(ops, th, psi_init)
@@ -43,7 +48,11 @@ def run(sector, pool, psi_init, warm_ops=(), warm_theta=(), max_ops=160, grad_to
     if len(ops):
         res = bfgs.minimize(fg, theta, gtol=warm_gtol, max_iter=bfgs_max_iter)
         theta = res["x"]
+        H = res["H"]
         trace.append(dict(kind="warm", E=res["f"], nfev=res["nfev"], nit=res["nit"]))
+        if fix_warm:
+            psi_init = sector.apply_ansatz(ops, theta, psi_init)
+            ops, theta, H = [], np.zeros(0), None
     n_adapt = 0
     stop = "max_ops"
     while n_adapt < max_ops:
@@ -61,8 +70,13 @@ def run(sector, pool, psi_init, warm_ops=(), warm_theta=(), max_ops=160, grad_to
         theta = np.append(theta, 0.0)
         n_adapt += 1
         tol = min(1e-6, gmax * 1e-5)
-        res = bfgs.minimize(fg, theta, gtol=tol, max_iter=bfgs_max_iter)
+        H0 = None
+        if hessian_recycling and H is not None:
+            H0 = np.eye(theta.size)
+            H0[:-1, :-1] = H
+        res = bfgs.minimize(fg, theta, gtol=tol, max_iter=bfgs_max_iter, H0=H0)
         theta = res["x"]
+        H = res["H"]
         trace.append(dict(kind="adapt", op=k, gmax=gmax, E=res["f"], nfev=res["nfev"], nit=res["nit"]))
     E_final = fg(theta)[0] if len(ops) else sector.energy(psi_init)[0]
     return dict(ops=ops, theta=theta, trace=trace, E=E_final, stop=stop, n_adapt=n_adapt)

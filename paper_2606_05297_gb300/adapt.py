@@ -189,7 +189,8 @@ class Adapt:
     """One CV-ADAPT-VQE run on one Hamiltonian instance."""
 
     def __init__(self, model: Model, pool_ops: Sequence[Op], init_occ: Sequence[int], warm_ops: Sequence[Op] = (),
-                 warm_theta: Sequence[float] = (), n_max: int = 256, stream=None):
+                 warm_theta: Sequence[float] = (), n_max: int = 256, stream=None, hessian_recycling: bool = False,
+                 fix_warm: bool = False):
         import torch
         self.torch = torch
         self.model = model
@@ -205,6 +206,11 @@ class Adapt:
         self.theta = np.array(warm_theta, dtype=np.float64)
         self.trace = []
         self.Hinv = None
+        # App. D variants: BFGS starts from the previous iteration's inverse
+        # Hessian (extended by an identity row and column for the new
+        # parameter); the warm-up layer keeps its initial parameters
+        self.hessian_recycling = hessian_recycling
+        self.fix_warm = fix_warm
         self._out = torch.empty(n_max + 1, dtype=torch.float64, device="cuda")
         self._host = torch.empty(n_max + 1, dtype=torch.float64, pin_memory=True)
         self._g = torch.empty(self.K, dtype=torch.float64, device="cuda")
@@ -246,7 +252,11 @@ class Adapt:
             return None
         r = BFGS(self.fg).minimize(self.theta, gtol=gtol, max_iter=max_iter)
         self.theta = r.x
+        self.Hinv = r.Hinv
         self.trace.append(dict(kind="warm", E=r.f, nfev=r.nfev, nit=r.nit, status=r.status))
+        if self.fix_warm:  # the warm-up state becomes the reference of the adaptive ansatz
+            self.psi0 = self.state().clone()
+            self.ids, self.theta, self.Hinv = [], np.zeros(0), None
         return r
 
     def step(self, grad_tol=1e-6, max_iter=1000, g=None):
@@ -264,8 +274,13 @@ class Adapt:
             raise RuntimeError("ansatz length exceeds the workspace")
         self.ids.append(k)
         self.theta = np.append(self.theta, 0.0)
-        r = BFGS(self.fg).minimize(self.theta, gtol=min(1e-6, gmax * 1e-5), max_iter=max_iter)
+        H0 = None
+        if self.hessian_recycling and self.Hinv is not None:
+            H0 = np.eye(self.theta.size)
+            H0[:-1, :-1] = self.Hinv
+        r = BFGS(self.fg).minimize(self.theta, gtol=min(1e-6, gmax * 1e-5), max_iter=max_iter, Hinv0=H0)
         self.theta = r.x
+        self.Hinv = r.Hinv
         rec = dict(kind="adapt", op=k, gmax=gmax, E=r.f, nfev=r.nfev, nit=r.nit, status=r.status, n=len(self.ids),
                    seconds=time.perf_counter() - t0)
         self.trace.append(rec)
