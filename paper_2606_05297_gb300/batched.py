@@ -185,13 +185,34 @@ def c4_batch_inputs(seed: int = 0, count: int = 64, extra_ops: int = 8):
     return out
 
 
-def measure_c4(reps: int = 5, seed: int = 0, count: int = 64, extra_ops: int = 8, sequential: bool = True) -> dict:
+def shard(dims: Sequence[int], rank: int, world: int) -> List[int]:
+    """Instances of one rank when a sweep is split over `world` GPUs:
+    longest-first assignment to the least-loaded rank by sector dimension
+    (ties to the lower rank), so every rank computes the same split without
+    communicating.  Returns the sorted instance indices of `rank`."""
+    load = [0] * world
+    owner = [0] * len(dims)
+    for i in sorted(range(len(dims)), key=lambda k: (-dims[k], k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        owner[i] = r
+        load[r] += dims[i]
+    return [i for i in range(len(dims)) if owner[i] == rank]
+
+
+def measure_c4(reps: int = 5, seed: int = 0, count: int = 64, extra_ops: int = 8, sequential: bool = True,
+               rank: int = 0, world: int = 1) -> dict:
     """Throughput of energy-and-gradient evaluations over the 64-instance sweep:
     one batched graph launch per evaluation of every instance, against the
     same evaluations issued instance by instance through cvq_energy_and_grad.
-    Device-resident inputs; CUDA events on the launching stream."""
+    Device-resident inputs; CUDA events on the launching stream.  With
+    world > 1 this rank measures its own shard of the instances."""
     import torch
     data = c4_batch_inputs(seed, count, extra_ops)
+    if world > 1:
+        from math import comb
+        dims = [comb(m.N + m.L - 1, m.L - 1) for m, _, _, _ in data]
+        data = [data[i] for i in shard(dims, rank, world)]
+        count = len(data)
     sectors = [cvq.Sector(m) for m, _, _, _ in data]
     pools = [cvq.Pool(s, ops) for s, (_, ops, _, _) in zip(sectors, data)]
     psi0 = [s.basis_state(_mott(m)) for s, (m, _, _, _) in zip(sectors, data)]
