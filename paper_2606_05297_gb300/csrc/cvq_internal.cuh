@@ -217,22 +217,17 @@ struct GateArg {
 // Shared memory of a block-gate kernel: the gate tables (block unitaries,
 // block descriptors, members, generator factors) followed by each thread's
 // staging columns for bmax amplitudes and bmax sector indices.
-// Bose-Hubbard kernels read the block unitaries from global memory (every
-// warp works on one class, so each read is a broadcast served by L1) and keep
-// shared memory for the staging columns, which bounds their occupancy;
-// Kitaev-chain kernels stage the unitaries too.
-__host__ __device__ __forceinline__ size_t gate_tables_bytes(const TypeDesc& t, int kind) {
-  const size_t b = (kind == CVQ_BH ? 0 : (size_t)t.nu * sizeof(cdf)) + (size_t)t.nblocks * sizeof(BlockDesc) +
+__host__ __device__ __forceinline__ size_t gate_tables_bytes(const TypeDesc& t) {
+  const size_t b = (size_t)t.nu * sizeof(cdf) + (size_t)t.nblocks * sizeof(BlockDesc) +
                    (size_t)(DMAX * DMAX) * sizeof(int2) + (size_t)(DMAX * DMAX) * sizeof(float2);
   return (b + 15) & ~(size_t)15;
 }
 
 // Bose-Hubbard kernels also cache the members' sector indices (costly to
-// recompute; ranks fit in 32 bits for L, D <= 16); Kitaev-chain indices are
-// recomputed from the orbit base.
+// recompute); Kitaev-chain indices are recomputed from the orbit base.
 __host__ __device__ __forceinline__ size_t gate_smem_bytes(const TypeDesc& t, int kind) {
-  return gate_tables_bytes(t, kind) +
-         (size_t)NTHREADS * t.bmax * (sizeof(cdf) + (kind == CVQ_BH ? sizeof(int32_t) : 0));
+  return gate_tables_bytes(t) +
+         (size_t)NTHREADS * t.bmax * (sizeof(cdf) + (kind == CVQ_BH ? sizeof(int64_t) : 0));
 }
 
 // Per-call list of gates for the unitary build kernel (passed by value).

@@ -158,9 +158,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       copy_words(&sh.t, &I.ops[ids[I.ids_off + segs[it.seg].k0]].t, sizeof(TypeDesc));
       __syncthreads();
       const TypeDesc& t = sh.t;
-      const cdf* Ug = I.U + (size_t)sh.seg.k0 * I.ustride;
-      const GateSmem m = gate_smem(smem, t, KIND, Ug);
-      stage_gate<ADJ>(m, t, Ug, I.P, KIND);
+      const GateSmem m = gate_smem(smem, t);
+      stage_gate<ADJ>(m, t, I.U + (size_t)sh.seg.k0 * I.ustride, I.P);
       __syncthreads();
       dfacc gacc;
       acc_zero(gacc);

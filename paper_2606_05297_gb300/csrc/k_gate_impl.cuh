@@ -166,14 +166,14 @@ template <bool ADJ, bool REALU, bool CACHE, class IDX>
 __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__ Ub, const int2* __restrict__ mem,
                                             const float2* __restrict__ F, const float cpr, const float cpi,
                                             const IDX& idx, const cdf* src, cdf* dst, cdf* lam, cdf* stg,
-                                            int32_t* sx, dfacc& gacc) {
+                                            int64_t* sx, dfacc& gacc) {
   const int tid = threadIdx.x;
   // sector index of member l: cached in shared memory (CACHE) or recomputed
   auto X = [&](int l) -> int64_t { return CACHE ? sx[l * NTHREADS + tid] : idx(mem[l]); };
 #pragma unroll 4
   for (int l = 0; l < b; ++l) {
     const int64_t x = idx(mem[l]);
-    if (CACHE) sx[l * NTHREADS + tid] = (int32_t)x;
+    if (CACHE) sx[l * NTHREADS + tid] = x;
     stg[l * NTHREADS + tid] = src[x];
   }
   if (!ADJ) {
@@ -239,38 +239,29 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
 // members, generator factors (reverse only), then the per-thread staging
 // columns of amplitudes and sector indices.
 struct GateSmem {
-  const cdf* U;
+  cdf* U;
   BlockDesc* B;
   int2* M;
   float2* F;
   cdf* stg;
-  int32_t* sx;
+  int64_t* sx;
 };
 
-// Ug: the gate's unitaries in global memory, used in place by BH kernels.
-__device__ __forceinline__ GateSmem gate_smem(char* smem, const TypeDesc& t, int kind, const cdf* Ug) {
+__device__ __forceinline__ GateSmem gate_smem(char* smem, const TypeDesc& t) {
   GateSmem m;
-  char* q = smem;
-  if (kind == CVQ_BH) {
-    m.U = Ug;
-  } else {
-    m.U = reinterpret_cast<const cdf*>(q);
-    q += (size_t)t.nu * sizeof(cdf);
-  }
-  m.B = reinterpret_cast<BlockDesc*>(q);
+  m.U = reinterpret_cast<cdf*>(smem);
+  m.B = reinterpret_cast<BlockDesc*>(m.U + t.nu);
   m.M = reinterpret_cast<int2*>(m.B + t.nblocks);
   m.F = reinterpret_cast<float2*>(m.M + DMAX * DMAX);
-  m.stg = reinterpret_cast<cdf*>(smem + gate_tables_bytes(t, kind));
-  m.sx = reinterpret_cast<int32_t*>(m.stg + (size_t)t.bmax * NTHREADS);
+  m.stg = reinterpret_cast<cdf*>(smem + gate_tables_bytes(t));
+  m.sx = reinterpret_cast<int64_t*>(m.stg + (size_t)t.bmax * NTHREADS);
   return m;
 }
 
 // Copies one gate's tables into shared memory (the caller synchronises).
 template <bool ADJ>
-__device__ __forceinline__ void stage_gate(const GateSmem& m, const TypeDesc& t, const cdf* U, const PoolDev& P,
-                                           int kind) {
-  if (kind != CVQ_BH)
-    for (int e = threadIdx.x; e < t.nu; e += blockDim.x) const_cast<cdf*>(m.U)[e] = U[e];
+__device__ __forceinline__ void stage_gate(const GateSmem& m, const TypeDesc& t, const cdf* U, const PoolDev& P) {
+  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) m.U[e] = U[e];
   for (int e = threadIdx.x; e < t.nblocks; e += blockDim.x) m.B[e] = P.blk[t.blk_base + e];
   for (int e = threadIdx.x; e < t.nmem; e += blockDim.x) m.M[e] = P.mem[t.mem_base + e];
   if (ADJ)
@@ -369,15 +360,15 @@ __device__ __forceinline__ void build_block_unitary(const TypeDesc& t, double th
 // ------------------------------------------------------------ kernel
 
 template <int KIND, bool ADJ, bool REALU>
-__global__ void __launch_bounds__(NTHREADS, 3)
+__global__ void __launch_bounds__(NTHREADS, 2)
     k_gate_block(const __grid_constant__ SectorDev S, const __grid_constant__ GateArg g, PoolDev P, const cdf* src,
                  cdf* dst, cdf* lam, double* partial) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int32_t Gs[LMAX][DMAX + 1];  // BH ranks fit in 32 bits for L, D <= 16
   if (KIND == CVQ_BH) load_G(Gs, S);
   const TypeDesc& t = g.t;
-  const GateSmem m = gate_smem(smem, t, KIND, g.U);
-  stage_gate<ADJ>(m, t, g.U, P, KIND);
+  const GateSmem m = gate_smem(smem, t);
+  stage_gate<ADJ>(m, t, g.U, P);
   __syncthreads();
   const int j = t.single ? -1 : g.j;
   dfacc gacc;
