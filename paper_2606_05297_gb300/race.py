@@ -71,6 +71,7 @@ def main(argv=None):
     ap.add_argument("--top-k", type=int, default=8)
     ap.add_argument("--full-every", type=int, default=5)
     ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--hessian-recycling", action="store_true", help="both arms recycle the BFGS inverse Hessian (App. D)")
     a = ap.parse_args(argv)
 
     import torch
@@ -96,13 +97,15 @@ def main(argv=None):
     torch.cuda.empty_cache()
 
     plain, h_plain, r_plain, t_plain = run_arm(
-        lambda: adapt.Adapt(m, pool, occ, warm, wth, n_max=a.max_ops + len(warm) + 1), E0, a.max_ops)
+        lambda: adapt.Adapt(m, pool, occ, warm, wth, n_max=a.max_ops + len(warm) + 1,
+                            hessian_recycling=a.hessian_recycling), E0, a.max_ops)
     del plain
     torch.cuda.empty_cache()
     la, h_learn, r_learn, t_learn = run_arm(
         lambda: learned.LearnedAdapt(m, pool, occ, scorer, trainer=tr, top_k=a.top_k, full_every=a.full_every,
                                      train_steps=20, warm_ops=warm, warm_theta=wth,
-                                     n_max=a.max_ops + len(warm) + 1), E0, a.max_ops)
+                                     n_max=a.max_ops + len(warm) + 1, hessian_recycling=a.hessian_recycling),
+        E0, a.max_ops)
     st = la.stats
     out = dict(
         target=dict(model=f"kitaev_kerr open L={a.L} d={a.d} t=1 Delta=0.6 K=0.3", dim=int(la.sector.dim),
@@ -117,7 +120,7 @@ def main(argv=None):
                      reached=r_learn, exact_gradients=st.exact_gradients, full_screens=st.full_screens,
                      subset_screens=st.subset_screens, judged=st.judged, hits=st.hits,
                      mean_regret=float(np.mean(st.regret)) if st.regret else None, history=h_learn),
-        top_k=a.top_k, full_every=a.full_every)
+        top_k=a.top_k, full_every=a.full_every, hessian_recycling=a.hessian_recycling)
     print(json.dumps(out), flush=True)
     return out
 

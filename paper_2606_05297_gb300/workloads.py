@@ -154,6 +154,24 @@ def bkc_kerr_pool(L: int) -> List[Op]:
     return ops
 
 
+def bkc_table_pool(L: int, kerr: bool = False) -> List[Op]:
+    """Table I pool of the Kitaev chain as single-parameter generators: beam
+    splitter and two-mode squeezer on all pairs (phi in {0, pi/2}),
+    single-mode squeezer per site (both phases) and rotation per site, plus
+    Kerr per site and cross-Kerr per pair with a Kerr term."""
+    ops = []
+    for i in range(L):
+        for j in range(i + 1, L):
+            ops += [Op("hop", i, j, p) for p in (0, 1)] + [Op("sq2", i, j, p) for p in (0, 1)]
+            if kerr:
+                ops.append(Op("xkerr", i, j))
+    for r in range(L):
+        ops += [Op("sq1", r, -1, p) for p in (0, 1)] + [Op("rot", r)]
+        if kerr:
+            ops.append(Op("kerr", r))
+    return ops
+
+
 def paper_bkc_pool_two_param(L: int, kerr: bool = False) -> List[tuple]:
     """Table I pools with two-parameter gates counted once: BS and S2 on all
     pairs, S and R per site; BKC+K adds K per site and CK per pair."""
