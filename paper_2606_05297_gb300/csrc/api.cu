@@ -374,7 +374,10 @@ static std::complex<double> ipow(int p) {
 }
 
 // Build the block tables of one (type, phase) generator in sector S.
-static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, TypeDesc& t) {
+// dc > 0: projected gates (Sec. V.A): every block's chain is extended past the
+// cutoff up to occupations dc - 1 and the eigendecomposition is of that chain;
+// the members inside the cutoff are a contiguous segment of it.
+static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, TypeDesc& t, int dc = 0) {
   memset(&t, 0, sizeof t);
   t.type = type;
   t.phase = phase & 3;
@@ -408,14 +411,16 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
   t.lam_base = (int)pb.lam.size();
   const int D = S.D;
   t.nclass = (S.kind == CVQ_BH) ? S.N + 1 : 2;
-  auto allowed = [&](int cls, int a, int b) -> bool {
-    if (a < 0 || a >= D) return false;
+  auto allowed_c = [&](int cls, int a, int b, int cut) -> bool {
+    if (a < 0 || a >= cut) return false;
     if (t.single) return b == 0 && (a & 1) == cls;
-    if (b < 0 || b >= D) return false;
+    if (b < 0 || b >= cut) return false;
     if (S.kind == CVQ_BH) return a + b == cls;
     return ((a + b) & 1) == cls;
   };
-  int nu = 0, nmem = 0, nf = 0, nlam = 0;
+  auto allowed = [&](int cls, int a, int b) -> bool { return allowed_c(cls, a, b, D); };
+  const int cut_ext = dc > 0 ? dc : D;
+  int nu = 0, nmem = 0, nf = 0, nlam = 0, nv = 0;
   for (int cls = 0; cls < t.nclass; ++cls) {
     t.class_off[cls] = (int)pb.blk.size() - t.blk_base;
     for (int a = 0; a < D; ++a)
@@ -425,44 +430,60 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
         for (int x = a, y = b; allowed(cls, x, y); x += t.di, y += t.dj) ch.push_back({x, y});
         const int n = (int)ch.size();
         if (n > BMAX) return fail(CVQ_EINVAL, "block of size %d exceeds %d", n, BMAX);
+        // the chain the eigendecomposition is of: the block itself, or extended to the inner cutoff
+        std::vector<std::pair<int, int>> ex;
+        int x0 = a, y0 = b;
+        while (allowed_c(cls, x0 - t.di, y0 - t.dj, cut_ext)) {
+          x0 -= t.di;
+          y0 -= t.dj;
+        }
+        for (int x = x0, y = y0; allowed_c(cls, x, y, cut_ext); x += t.di, y += t.dj) ex.push_back({x, y});
+        const int ne = (int)ex.size();
+        int off = 0;
+        while (off < ne && ex[off] != ch[0]) ++off;
+        if (ne > MAX_BEXT || off + n > ne) return fail(CVQ_EINVAL, "extended chain of %d members exceeds %d", ne, MAX_BEXT);
         BlockDesc bd;
         memset(&bd, 0, sizeof bd);
         bd.size = n;
+        bd.bext = ne;
         bd.mem_off = nmem;
         bd.u_off = nu;
+        bd.v_off = nv;
         bd.f_off = nf;
         bd.ev_off = nlam;
-        std::vector<double> T((size_t)n * n, 0.0), Vr, w;
-        for (int k = 0; k + 1 < n; ++k) {
-          const int a0 = ch[k].first, b0 = ch[k].second, a1 = ch[k + 1].first, b1 = ch[k + 1].second;
-          double fk = (double)fact_ratio(std::min(a0, a1), std::max(a0, a1));
-          if (!t.single) fk *= (double)fact_ratio(std::min(b0, b1), std::max(b0, b1));
-          fk = std::sqrt(fk);
-          pb.F.push_back(split_df(fk));
-          T[(size_t)k * n + k + 1] = T[(size_t)(k + 1) * n + k] = acp * fk;
-        }
-        if (n > 1) {
-          jacobi_eigen(T, n, Vr, w);
+        auto factor = [&](const std::pair<int, int>& p0, const std::pair<int, int>& p1) {
+          double fk = (double)fact_ratio(std::min(p0.first, p1.first), std::max(p0.first, p1.first));
+          if (!t.single) fk *= (double)fact_ratio(std::min(p0.second, p1.second), std::max(p0.second, p1.second));
+          return std::sqrt(fk);
+        };
+        for (int k = 0; k + 1 < n; ++k) pb.F.push_back(split_df(factor(ch[k], ch[k + 1])));
+        std::vector<double> T((size_t)ne * ne, 0.0), Vr, w;
+        for (int k = 0; k + 1 < ne; ++k) T[(size_t)k * ne + k + 1] = T[(size_t)(k + 1) * ne + k] = acp * factor(ex[k], ex[k + 1]);
+        if (ne > 1) {
+          jacobi_eigen(T, ne, Vr, w);
         } else {
           Vr.assign(1, 1.0);
           w.assign(1, 0.0);
         }
+        // rows of the members (chain positions off .. off + n - 1) of W V, W = diag(om^k)
         std::complex<double> omk(1, 0);
-        for (int k = 0; k < n; ++k) {
-          for (int m = 0; m < n; ++m) {
-            const std::complex<double> v = omk * Vr[(size_t)k * n + m];
+        for (int k = 0; k < off; ++k) omk *= om;
+        for (int k = off; k < off + n; ++k) {
+          for (int m = 0; m < ne; ++m) {
+            const std::complex<double> v = omk * Vr[(size_t)k * ne + m];
             pb.V.push_back(v.real());
             pb.V.push_back(v.imag());
           }
           omk *= om;
         }
-        for (int m = 0; m < n; ++m) pb.lam.push_back(w[m]);
+        for (int m = 0; m < ne; ++m) pb.lam.push_back(w[m]);
         for (auto& pr : ch) pb.mem.push_back(make_int2(pr.first, pr.second));
         pb.blk.push_back(bd);
         nu += n * n;
+        nv += n * ne;
         nmem += n;
         nf += n - 1;
-        nlam += n;
+        nlam += ne;
         t.bmax = std::max(t.bmax, n);
       }
   }
@@ -490,7 +511,7 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
     t.chunk_base = (int)pb.chunks.size();
     for (int M = 0; M < t.nclass; ++M) {
       int bm = 0;
-      for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) bm = std::max(bm, pb.blk[t.blk_base + bi].size);
+      for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) bm = std::max(bm, pb.blk[t.blk_base + bi].bext);
       if (bm < 2) continue;  // only one-member blocks: the gate is the identity on this class
       const int64_t cnt = S.bh2_off[M + 1] - S.bh2_off[M];
       if (cnt > INT32_MAX) return fail(CVQ_EINVAL, "too many orbits in one class");
@@ -863,6 +884,7 @@ static int prepare_gates(const cvq_sector*, const cvq_pool* p, const int* op_ids
   BuildArgs a;
   a.n = n;
   a.maxblk = 0;
+  a.D = nullptr;
   a.ustride = p->ustride;
   for (int k = 0; k < n; ++k) {
     if (op_ids[k] < 0 || op_ids[k] >= p->K) return fail(CVQ_EINVAL, "op_ids[%d] = %d outside the pool", k, op_ids[k]);

@@ -19,6 +19,7 @@ namespace cvq {
 constexpr int LMAX = 16;
 constexpr int DMAX = 16;
 constexpr int BMAX = 16;          // largest block of a gate (<= D)
+constexpr int MAX_BEXT = 64;      // longest chain of a block's eigendecomposition (projected pools)
 constexpr int MAX_CLASSES = 17;   // BH: total pair occupation M = 0..N (N <= 15); BKC: 2 parities
 constexpr int MAX_GATES = 512;    // ansatz length per call and pool size
 constexpr int NTHREADS = 256;
@@ -180,8 +181,11 @@ struct BlockDesc {
   int mem_off;  // into members[]
   int u_off;    // complex offset of the size x size block within a gate's U
   int f_off;    // into F[] (size - 1 entries)
-  int ev_off;   // into lam[] (size entries); V shares u_off layout in V[]
-  int pad[3];
+  int ev_off;   // into lam[] (bext entries)
+  int bext;     // length of the chain the eigendecomposition is of: size, or the chain extended to the
+                // inner cutoff of a projected pool (the members are a contiguous segment of it)
+  int v_off;    // complex offset into V[] of the size x bext rows of the members
+  int pad;
 };
 
 struct TypeDesc {
@@ -234,6 +238,7 @@ __host__ __device__ __forceinline__ size_t gate_smem_bytes(const TypeDesc& t, in
 struct BuildArgs {
   int n;
   int maxblk;            // most blocks of any gate of the call (grid y)
+  cdf* D;                // projected pools: theta derivatives of the blocks (same layout as U), else null
   int ustride;           // complex entries reserved per gate
   int type_of[MAX_GATES];
   double theta[MAX_GATES];

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(128) k_batch_build(const BInst* __restrict__ i
   const int op = ids[I.ids_off + ik.y];
   const TypeDesc& t = I.ops[op].t;
   if (t.diag) return;
-  __shared__ double2 ph[BMAX];
+  __shared__ double2 ph[MAX_BEXT];
   build_block_unitary(t, theta[I.theta_off + ik.y], I.P, I.U + (size_t)ik.y * I.ustride, blockIdx.y, ph);
 }
 

@@ -284,7 +284,7 @@ __device__ __forceinline__ void bkc_gate_range(const SectorDev& S, int gi, int g
     bkc_orbit(S, gi, gj, it, items, idx.f0, cls);
     for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
       const BlockDesc bd = m.B[bi];
-      if (bd.size < 2) continue;  // zero generator: identity, no gradient term
+      if (bd.bext < 2) continue;  // zero generator: identity, no gradient term
       apply_block<ADJ, REALU, false>(bd.size, m.U + bd.u_off, m.M + bd.mem_off, m.F + bd.f_off, cpr, cpi, idx, src,
                                      dst, lam, m.stg, m.sx, gacc);
     }
@@ -312,7 +312,7 @@ __device__ __forceinline__ void bh_gate_chunk(const SectorDev& S, const int32_t 
     const BhIdxT<int32_t> idx = bh_idx_of<int32_t>(S, Gs, gi, gj, w0);
     for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
       const BlockDesc bd = m.B[bi];
-      if (bd.size < 2) continue;  // zero generator: identity, no gradient term
+      if (bd.bext < 2) continue;  // zero generator: identity, no gradient term
       apply_block<ADJ, REALU, true>(bd.size, m.U + bd.u_off, m.M + bd.mem_off, m.F + bd.f_off, cpr, cpi, idx, src,
                                     dst, lam, m.stg, m.sx, gacc);
     }
@@ -327,33 +327,46 @@ __device__ __forceinline__ void bh_gate_chunk(const SectorDev& S, const int32_t 
 // tridiagonal block, so exp(theta A) has purely real entries (real
 // generator) or real entries at even k - l and imaginary ones at odd k - l;
 // the other component is zero up to rounding and is set to zero.
-// One block bi of one gate (the calling CTA; blocks of one member are never
-// read by the gate kernels and are left out).
+// One block bi of one gate (the calling CTA): U = P (W V) e^{i theta Lambda}
+// (W V)^dag P over the block's members, and when Dg is given its theta
+// derivative D = P (W V) (i Lambda) e^{i theta Lambda} (W V)^dag P.  P keeps
+// the members of the (possibly extended) chain; blocks whose chain is a
+// single member are the identity and are never read.
 __device__ __forceinline__ void build_block_unitary(const TypeDesc& t, double th, const PoolDev& P, cdf* Ug, int bi,
-                                                    double2* ph) {
+                                                    double2* ph, cdf* Dg = nullptr) {
   if (bi >= t.nblocks) return;
   const BlockDesc bd = P.blk[t.blk_base + bi];
-  const int b = bd.size;
-  if (b < 2) return;
-  if (threadIdx.x < b) {
+  const int b = bd.size, be = bd.bext;
+  if (be < 2) return;
+  for (int q = threadIdx.x; q < be; q += blockDim.x) {
     double s, c;
-    sincos(th * P.lam[t.lam_base + bd.ev_off + threadIdx.x], &s, &c);
-    ph[threadIdx.x] = make_double2(c, s);
+    sincos(th * P.lam[t.lam_base + bd.ev_off + q], &s, &c);
+    ph[q] = make_double2(c, s);
   }
   __syncthreads();
-  const double2* Vb = reinterpret_cast<const double2*>(P.V) + t.v_base + bd.u_off;
+  const double2* Vb = reinterpret_cast<const double2*>(P.V) + t.v_base + bd.v_off;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int k = e / b, l = e - k * b;
-    double re = 0.0, im = 0.0;
-    for (int q = 0; q < b; ++q) {
-      const double2 vk = Vb[k * b + q], vl = Vb[l * b + q], p = ph[q];
+    double re = 0.0, im = 0.0, dre = 0.0, dim_ = 0.0;
+    for (int q = 0; q < be; ++q) {
+      const double2 vk = Vb[k * be + q], vl = Vb[l * be + q], p = ph[q];
       const double xr = vk.x * p.x - vk.y * p.y, xi = vk.x * p.y + vk.y * p.x;  // vk p
-      re += xr * vl.x + xi * vl.y;                                               // * conj(vl)
-      im += xi * vl.x - xr * vl.y;
+      const double ur = xr * vl.x + xi * vl.y, ui = xi * vl.x - xr * vl.y;       // * conj(vl)
+      re += ur;
+      im += ui;
+      if (Dg) {  // times i lambda_q
+        const double lq = P.lam[t.lam_base + bd.ev_off + q];
+        dre -= lq * ui;
+        dim_ += lq * ur;
+      }
     }
+    // Generators here have phases that are multiples of pi/2 on a bipartite
+    // chain, so U is real (real generator) or real at even k - l and
+    // imaginary at odd k - l; the other component is rounding and is zeroed.
     if (t.realu || ((k - l) & 1) == 0) im = 0.0;
     else re = 0.0;
     Ug[bd.u_off + e] = make_cdf(df_from_double(re), df_from_double(im));
+    if (Dg) Dg[bd.u_off + e] = make_cdf(df_from_double(dre), df_from_double(dim_));
   }
 }
 

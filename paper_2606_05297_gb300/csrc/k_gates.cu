@@ -52,8 +52,9 @@ __global__ void k_build(const __grid_constant__ BuildArgs a, const TypeDesc* __r
   if (g >= a.n) return;
   const TypeDesc& t = types[a.type_of[g]];
   if (t.diag) return;  // diagonal gates are applied from per-run phase tables
-  __shared__ double2 ph[BMAX];
-  build_block_unitary(t, a.theta[g], P, U + (size_t)g * a.ustride, blockIdx.y, ph);
+  __shared__ double2 ph[MAX_BEXT];
+  build_block_unitary(t, a.theta[g], P, U + (size_t)g * a.ustride, blockIdx.y, ph,
+                      a.D ? a.D + (size_t)g * a.ustride : nullptr);
 }
 
 cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_dev, PoolDev P, cdf* U, cudaStream_t st) {
