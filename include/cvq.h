@@ -168,6 +168,37 @@ int cvq_energy_and_grad_ckpt(const cvq_sector *s, const cvq_pool *p, const int *
                              const cvq_c128 *psi0, double *E_dev, double *grad_dev, int every, void *ckpt,
                              size_t ckpt_bytes, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Projected gates (Sec. V.A): each gate's matrix elements are those of the
+ * untruncated gate between states inside the cutoff, and the state is
+ * renormalised after every gate that the cutoff makes non-unitary (the block
+ * gates of a Kitaev-chain sector; diagonal gates stay unitary).  The
+ * untruncated elements are obtained from each block's chain extended to the
+ * inner cutoff: exact for beam splitters once inner_cutoff >= 2d - 1,
+ * converging with inner_cutoff for squeezers.
+ *   cvq_set_pool_projected: as cvq_set_pool, on a Kitaev-chain sector, with
+ *     d <= inner_cutoff <= 64 (EINVAL otherwise).  Such a pool works with
+ *     cvq_screen_pool (at theta = 0 the projected and truncated generators
+ *     agree) and with the calls below; cvq_apply_ansatz and
+ *     cvq_energy_and_grad reject it.
+ *   cvq_projected_states_bytes: size of the caller's state buffer for an
+ *     ansatz: one state per segment boundary (block gate or run of diagonal
+ *     gates) plus the theta derivatives of the block unitaries.
+ *   cvq_apply_ansatz_projected: the normalised psi_n.
+ *   cvq_energy_and_grad_projected: E = <psi_n|H|psi_n> and dE/dtheta through
+ *     the normalisations: with lambda = H psi_n, for each block gate
+ *     mu = (lambda - Re<psi_k|lambda> psi_k) / N_k, g_k = 2 Re<mu|D_k psi_{k-1}>,
+ *     lambda <- U_k^dag mu (every psi_k is kept in the state buffer).
+ * states: device, 256-byte aligned, >= cvq_projected_states_bytes; workspace as
+ * for cvq_energy_and_grad.  Errors: EINVAL, ENOMEM, ECUDA. */
+int cvq_set_pool_projected(const cvq_sector *s, const cvq_op *ops, int K, int inner_cutoff, cvq_pool **out);
+int cvq_projected_states_bytes(const cvq_sector *s, const cvq_pool *p, const int *op_ids, int n, size_t *bytes);
+int cvq_apply_ansatz_projected(const cvq_sector *s, const cvq_pool *p, const int *op_ids, const double *theta, int n,
+                               const cvq_c128 *psi0, cvq_c128 *psi_out, void *states, size_t states_bytes,
+                               void *workspace, size_t workspace_bytes, void *stream);
+int cvq_energy_and_grad_projected(const cvq_sector *s, const cvq_pool *p, const int *op_ids, const double *theta,
+                                  int n, const cvq_c128 *psi0, double *E_dev, double *grad_dev, void *states,
+                                  size_t states_bytes, void *workspace, size_t workspace_bytes, void *stream);
+
 /* One step of the Lanczos recurrence used for the exact ground energy E0
  * that defines Delta E = |E - E0| (Sec. IV.B stopping rule; exact
  * diagonalisation there).  Before the call the caller has w = H v and

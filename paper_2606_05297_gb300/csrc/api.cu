@@ -152,6 +152,7 @@ struct cvq_pool {
   PoolDev P{};
   int ustride = PHASE_TABLE;     // complex entries per gate in a call's U buffer
   std::vector<int> blk_size;     // host copy of every block's size (costs)
+  int dc = 0;                    // > 0: projected gates with this inner cutoff
 };
 
 static int64_t binom(int n, int k) {
@@ -524,7 +525,22 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
   return CVQ_OK;
 }
 
+static int set_pool(const cvq_sector* s, const cvq_op* ops, int K, int dc, cvq_pool** out);
+
 extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_pool** out) {
+  return set_pool(s, ops, K, 0, out);
+}
+
+extern "C" int cvq_set_pool_projected(const cvq_sector* s, const cvq_op* ops, int K, int inner_cutoff,
+                                      cvq_pool** out) {
+  if (!s) return fail(CVQ_EINVAL, "null argument");
+  if (s->S.kind != CVQ_BKC) return fail(CVQ_EINVAL, "projected gates apply to Kitaev-chain sectors (BH is not cut)");
+  if (inner_cutoff < s->S.D || inner_cutoff > MAX_BEXT)
+    return fail(CVQ_EINVAL, "inner cutoff %d outside [d = %d, %d]", inner_cutoff, s->S.D, MAX_BEXT);
+  return set_pool(s, ops, K, inner_cutoff, out);
+}
+
+static int set_pool(const cvq_sector* s, const cvq_op* ops, int K, int dc, cvq_pool** out) {
   if (!s || !out || (K > 0 && !ops)) return fail(CVQ_EINVAL, "null argument");
   *out = nullptr;
   if (K < 0 || K > MAX_GATES) return fail(CVQ_EINVAL, "pool size %d outside [0, %d]", K, MAX_GATES);
@@ -533,6 +549,7 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
   if (!p) return fail(CVQ_ENOMEM, "host allocation");
   p->sec = s;
   p->K = K;
+  p->dc = dc;
   PoolBuild pb;
   std::map<std::pair<int, int>, int> seen;
   for (int k = 0; k < K; ++k) {
@@ -548,7 +565,7 @@ extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_p
     int ti;
     if (it == seen.end()) {
       TypeDesc t;
-      const int rc = build_type(S, o.type, key.second, pb, t);
+      const int rc = build_type(S, o.type, key.second, pb, t, dc);
       if (rc) { delete p; return rc; }
       ti = (int)p->types.size();
       p->types.push_back(t);
@@ -878,13 +895,13 @@ extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq
 }
 
 static int prepare_gates(const cvq_sector*, const cvq_pool* p, const int* op_ids, const double* theta, int n, cdf* U,
-                         cudaStream_t st) {
+                         cudaStream_t st, cdf* D = nullptr) {
   if (n < 0 || n > MAX_GATES) return fail(CVQ_EINVAL, "ansatz length %d outside [0, %d]", n, MAX_GATES);
   if (n > 0 && (!op_ids || !theta)) return fail(CVQ_EINVAL, "null op_ids / theta");
   BuildArgs a;
   a.n = n;
   a.maxblk = 0;
-  a.D = nullptr;
+  a.D = D;
   a.ustride = p->ustride;
   for (int k = 0; k < n; ++k) {
     if (op_ids[k] < 0 || op_ids[k] >= p->K) return fail(CVQ_EINVAL, "op_ids[%d] = %d outside the pool", k, op_ids[k]);
@@ -1016,6 +1033,7 @@ static int forward_sweep(const cvq_sector* s, const cvq_pool* p, const int* ids,
 extern "C" int cvq_apply_ansatz(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
                                 const cvq_c128* psi0, cvq_c128* psi_out, void* ws, size_t wsb, void* stream) {
   if (!s || !p || !psi0 || !psi_out) return fail(CVQ_EINVAL, "null argument");
+  if (p->dc) return fail(CVQ_EINVAL, "a projected pool needs cvq_apply_ansatz_projected");
   if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
   Layout l;
   if (int rc = check_ws(s, p, n, ws, wsb, l)) return rc;
@@ -1063,6 +1081,7 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
                            const cvq_c128* psi0, double* E_dev, double* grad_dev, void* ws, size_t wsb,
                            void* stream, Ckpt* ck) {
   if (!s || !p || !psi0 || !E_dev || (n > 0 && !grad_dev)) return fail(CVQ_EINVAL, "null argument");
+  if (p->dc) return fail(CVQ_EINVAL, "a projected pool needs cvq_energy_and_grad_projected");
   if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
   Layout l;
   if (int rc = check_ws(s, p, n, ws, wsb, l)) return rc;
@@ -1120,6 +1139,163 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
     ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * n, (double)NBLK * n);
     CVQ_CUDA(launch_reduce(partial, n, NBLK, 2.0, grad_dev, st), "reduce grad");
   }
+  return CVQ_OK;
+}
+
+// ------------------------------------------------------------------ projected gates (Sec. V.A)
+
+// Caller buffer of the projected sweep: one df state per segment boundary
+// (nseg + 1), the theta derivatives of the block unitaries (n x ustride), and
+// per segment the squared norm before renormalising plus one scratch dot.
+struct ProjLayout {
+  size_t slots, D, n2, r, total;
+  int nseg;
+};
+
+static ProjLayout proj_layout(const cvq_sector* s, const cvq_pool* p, int nseg, int n) {
+  ProjLayout l;
+  l.nseg = nseg;
+  const size_t st = al256((size_t)s->S.dim * sizeof(cdf));
+  l.slots = 0;
+  l.D = (size_t)(nseg + 1) * st;
+  l.n2 = al256(l.D + (size_t)std::max(n, 1) * p->ustride * sizeof(cdf));
+  l.r = al256(l.n2 + (size_t)std::max(nseg, 1) * sizeof(double));
+  l.total = al256(l.r + sizeof(double));
+  return l;
+}
+
+extern "C" int cvq_projected_states_bytes(const cvq_sector* s, const cvq_pool* p, const int* op_ids, int n,
+                                          size_t* bytes) {
+  if (!s || !p || !bytes || (n > 0 && !op_ids)) return fail(CVQ_EINVAL, "null argument");
+  if (n < 0 || n > MAX_GATES) return fail(CVQ_EINVAL, "ansatz length %d outside [0, %d]", n, MAX_GATES);
+  for (int k = 0; k < n; ++k)
+    if (op_ids[k] < 0 || op_ids[k] >= p->K) return fail(CVQ_EINVAL, "op_ids[%d] = %d outside the pool", k, op_ids[k]);
+  *bytes = proj_layout(s, p, (int)segments(p, op_ids, n).size(), n).total;
+  return CVQ_OK;
+}
+
+// Forward projected sweep into the state slots; returns the segments.
+static int proj_forward(const cvq_sector* s, const cvq_pool* p, const int* ids, const double* theta, int n,
+                        const cvq_c128* psi0, char* sb, const ProjLayout& pl, const cdf* U, double* partial,
+                        std::vector<Seg>& segs, cudaStream_t st) {
+  const size_t stride = al256((size_t)s->S.dim * sizeof(cdf));
+  auto slot = [&](int k) { return (cdf*)(sb + pl.slots + (size_t)k * stride); };
+  double* n2 = (double*)(sb + pl.n2);
+  const double dim = (double)s->S.dim;
+  segs = segments(p, ids, n);
+  if (int rc = to_df(s, psi0, slot(0), st)) return rc;
+  for (size_t si = 0; si < segs.size(); ++si) {
+    const Seg& g = segs[si];
+    cdf* psi = slot((int)si + 1);
+    CVQ_CUDA(cudaMemcpyAsync(psi, slot((int)si), sizeof(cdf) * (size_t)s->S.dim, cudaMemcpyDeviceToDevice, st),
+             "copy state");
+    if (g.diag) {
+      DiagRunArg a;
+      diag_run_arg(s, p, ids, theta, g, a);
+      ProfScope ps(KK_GATE_DIAG, st, 32.0 * dim, dim * (8.0 * s->S.L + 8.0 * a.npair));
+      CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, nullptr, nullptr, false, st), "diagonal run");
+    } else {
+      const GateArg ga = gate_arg(p, ids[g.k0], U + (size_t)g.k0 * p->ustride);
+      {
+        const OpCost c = op_cost(s, p, ids[g.k0]);
+        ProfScope ps(KK_GATE, st, c.fb, c.ff);
+        CVQ_CUDA(launch_gate(s->S, ga, p->P, psi, psi, st), "projected gate");
+      }
+      CVQ_CUDA(launch_dot_re(s->S.dim, psi, psi, partial, st), "norm");
+      CVQ_CUDA(launch_reduce(partial, 1, NBLK, 1.0, n2 + si, st), "reduce norm");
+      CVQ_CUDA(launch_scale_inv_sqrt(s->S.dim, psi, n2 + si, st), "renormalise");
+    }
+  }
+  return CVQ_OK;
+}
+
+static int proj_prepare(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
+                        void* ws, size_t wsb, void* states, size_t states_bytes, Layout& l, ProjLayout& pl,
+                        cudaStream_t st) {
+  if (!p->dc) return fail(CVQ_EINVAL, "the pool was not built with cvq_set_pool_projected");
+  if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
+  if (int rc = check_ws(s, p, n, ws, wsb, l)) return rc;
+  size_t need = 0;
+  if (int rc = cvq_projected_states_bytes(s, p, op_ids, n, &need)) return rc;
+  if (!states || ((uintptr_t)states & 255)) return fail(CVQ_EINVAL, "state buffer NULL or not 256-byte aligned");
+  if (states_bytes < need) return fail(CVQ_EINVAL, "state buffer of %zu bytes, %zu needed", states_bytes, need);
+  pl = proj_layout(s, p, (int)segments(p, op_ids, n).size(), n);
+  cdf* U = (cdf*)((char*)ws + l.U);
+  return prepare_gates(s, p, op_ids, theta, n, U, st, (cdf*)((char*)states + pl.D));
+}
+
+extern "C" int cvq_apply_ansatz_projected(const cvq_sector* s, const cvq_pool* p, const int* op_ids,
+                                          const double* theta, int n, const cvq_c128* psi0, cvq_c128* psi_out,
+                                          void* states, size_t states_bytes, void* ws, size_t wsb, void* stream) {
+  if (!s || !p || !psi0 || !psi_out) return fail(CVQ_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Layout l;
+  ProjLayout pl;
+  if (int rc = proj_prepare(s, p, op_ids, theta, n, ws, wsb, states, states_bytes, l, pl, st)) return rc;
+  std::vector<Seg> segs;
+  if (int rc = proj_forward(s, p, op_ids, theta, n, psi0, (char*)states, pl, (cdf*)((char*)ws + l.U),
+                            (double*)((char*)ws + l.partial), segs, st))
+    return rc;
+  const size_t stride = al256((size_t)s->S.dim * sizeof(cdf));
+  return from_df(s, (const cdf*)((char*)states + (size_t)segs.size() * stride), psi_out, st);
+}
+
+extern "C" int cvq_energy_and_grad_projected(const cvq_sector* s, const cvq_pool* p, const int* op_ids,
+                                             const double* theta, int n, const cvq_c128* psi0, double* E_dev,
+                                             double* grad_dev, void* states, size_t states_bytes, void* ws,
+                                             size_t wsb, void* stream) {
+  if (!s || !p || !psi0 || !E_dev || (n > 0 && !grad_dev)) return fail(CVQ_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  Layout l;
+  ProjLayout pl;
+  if (int rc = proj_prepare(s, p, op_ids, theta, n, ws, wsb, states, states_bytes, l, pl, st)) return rc;
+  char* sb = (char*)states;
+  cdf* U = (cdf*)((char*)ws + l.U);
+  const cdf* D = (const cdf*)(sb + pl.D);
+  cdf* lam = (cdf*)((char*)ws + l.lam);
+  double* partial = (double*)((char*)ws + l.partial);
+  std::vector<Seg> segs;
+  if (int rc = proj_forward(s, p, op_ids, theta, n, psi0, sb, pl, U, partial, segs, st)) return rc;
+  const size_t stride = al256((size_t)s->S.dim * sizeof(cdf));
+  auto slot = [&](int k) { return (cdf*)(sb + pl.slots + (size_t)k * stride); };
+  double* n2 = (double*)(sb + pl.n2);
+  double* rdot = (double*)(sb + pl.r);
+  const int ns = (int)segs.size();
+  double* pE = partial + (size_t)n * NBLK;
+  if (int rc = run_apply_H(s, slot(ns), lam, pE, st)) return rc;
+  CVQ_CUDA(launch_reduce(pE, 1, NBLK, 1.0, E_dev, st), "reduce E");
+  const double dim = (double)s->S.dim;
+  for (int si = ns - 1; si >= 0; --si) {
+    const Seg& g = segs[si];
+    if (g.diag) {  // unitary: the plain reverse step on psi_k (slot si + 1, consumed)
+      DiagRunArg a;
+      diag_run_arg(s, p, op_ids, theta, g, a);
+      cdf* psi = slot(si + 1);
+      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_ACC) {
+        DiagGradArg ga;
+        memset(&ga, 0, sizeof ga);
+        ga.m = std::min(DIAG_ACC, g.m - q0);
+        for (int q = 0; q < ga.m; ++q) {
+          ga.diag[q] = a.diag[q0 + q];
+          ga.gi[q] = a.gi[q0 + q];
+          ga.gj[q] = a.gj[q0 + q];
+        }
+        CVQ_CUDA(launch_diag_grad(s->S, ga, psi, lam, partial + (size_t)(g.k0 + q0) * NBLK, st), "diagonal-run gradients");
+      }
+      ProfScope ps(KK_ADJ_DIAG, st, 64.0 * dim, dim * (8.0 * s->S.L + 8.0 * a.npair + 24.0));
+      CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, lam, partial + (size_t)g.k0 * NBLK, true, st), "adjoint diagonal run");
+    } else {
+      CVQ_CUDA(launch_dot_re(s->S.dim, slot(si + 1), lam, partial + (size_t)g.k0 * NBLK, st), "Re <psi_k|lambda>");
+      CVQ_CUDA(launch_reduce(partial + (size_t)g.k0 * NBLK, 1, NBLK, 1.0, rdot, st), "reduce dot");
+      const GateArg ga = gate_arg(p, op_ids[g.k0], U + (size_t)g.k0 * p->ustride);
+      const OpCost c = op_cost(s, p, op_ids[g.k0]);
+      ProfScope ps(KK_ADJ, st, c.ab + 16.0 * dim, c.af);
+      CVQ_CUDA(launch_gate_proj_adj(s->S, ga, D + (size_t)g.k0 * p->ustride, p->P, slot(si), slot(si + 1), lam, rdot,
+                                    n2 + si, partial + (size_t)g.k0 * NBLK, st),
+               "projected reverse step");
+    }
+  }
+  if (n > 0) CVQ_CUDA(launch_reduce(partial, n, NBLK, 2.0, grad_dev, st), "reduce grad");
   return CVQ_OK;
 }
 

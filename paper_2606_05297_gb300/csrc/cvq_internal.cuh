@@ -234,6 +234,12 @@ __host__ __device__ __forceinline__ size_t gate_smem_bytes(const TypeDesc& t, in
          (size_t)NTHREADS * t.bmax * (sizeof(cdf) + (kind == CVQ_BH ? sizeof(int64_t) : 0));
 }
 
+// Shared tables of the projected reverse step: unitaries, derivatives, blocks, members.
+__host__ __device__ __forceinline__ size_t proj_tables_bytes(const TypeDesc& t) {
+  const size_t b = 2 * (size_t)t.nu * sizeof(cdf) + (size_t)t.nblocks * sizeof(BlockDesc) + (size_t)t.nmem * sizeof(int2);
+  return (b + 15) & ~(size_t)15;
+}
+
 // Per-call list of gates for the unitary build kernel (passed by value).
 struct BuildArgs {
   int n;
@@ -348,6 +354,11 @@ cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf
                              cudaStream_t st);
 cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
                             double* partial, bool adjoint, cudaStream_t st);
+cudaError_t launch_dot_re(int64_t dim, const cdf* a, const cdf* b, double* partial, cudaStream_t st);
+cudaError_t launch_scale_inv_sqrt(int64_t dim, cdf* v, const double* n2, cudaStream_t st);
+cudaError_t launch_gate_proj_adj(const SectorDev& S, const GateArg& g, const cdf* D, PoolDev P, const cdf* prev,
+                                 const cdf* cur, cdf* lam, const double* rdot, const double* n2, double* partial,
+                                 cudaStream_t st);
 cudaError_t launch_screen(const SectorDev& S, const ScreenArg& a, const cdf* psi, const cdf* sigma, double* partial,
                           cudaStream_t st);
 cudaError_t launch_screen_epilogue(const ScreenMap& m, int nsh, const double* z, double* grad, cudaStream_t st);

@@ -473,3 +473,71 @@ def energy_and_grad_ckpt(sector: Sector, pool: Pool, op_ids, theta, psi0, every:
                                       _ptr(E), _ptr(grad), int(every), _ptr(ckpt), ckpt.numel(), _ptr(ws), wsb,
                                       _stream(stream)), "cvq_energy_and_grad_ckpt")
     return E, grad[:n]
+
+
+def _proj_sigs(L):
+    vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
+    L.cvq_set_pool_projected.argtypes = [vp, C.POINTER(_Op), C.c_int, C.c_int, C.POINTER(vp)]
+    L.cvq_projected_states_bytes.argtypes = [vp, vp, ip, C.c_int, C.POINTER(C.c_size_t)]
+    L.cvq_apply_ansatz_projected.argtypes = [vp, vp, ip, dp, C.c_int, vp, vp, vp, C.c_size_t, vp, C.c_size_t, vp]
+    L.cvq_energy_and_grad_projected.argtypes = [vp, vp, ip, dp, C.c_int, vp, vp, vp, vp, C.c_size_t, vp, C.c_size_t,
+                                                vp]
+    return L
+
+
+class ProjectedPool(Pool):
+    """A pool whose gates are the untruncated gates projected onto the cutoff (Sec. V.A)."""
+
+    def __init__(self, sector: Sector, ops: Sequence[Op], inner_cutoff: int):
+        L = _proj_sigs(lib())
+        self.sector = sector
+        self.ops = list(ops)
+        K = len(self.ops)
+        arr = (_Op * max(K, 1))(*[_Op(OP_CODES[o.type], o.i, o.j if o.j is not None else -1, o.phase)
+                                  for o in self.ops])
+        h = C.c_void_p()
+        _check(L.cvq_set_pool_projected(sector.h, arr, K, int(inner_cutoff), C.byref(h)), "cvq_set_pool_projected")
+        self.h = h
+        self.K = K
+        self.inner_cutoff = int(inner_cutoff)
+
+
+def _proj_states(sector, pool, ids, n, states, device):
+    import torch
+    b = C.c_size_t()
+    _check(lib().cvq_projected_states_bytes(sector.h, pool.h, ids, n, C.byref(b)), "cvq_projected_states_bytes")
+    if states is None or states.numel() < b.value:
+        states = torch.empty(int(b.value), dtype=torch.uint8, device=device)
+    return states
+
+
+def apply_ansatz_projected(sector: Sector, pool: ProjectedPool, op_ids, theta, psi0, out=None, ws=None, states=None,
+                           stream=None):
+    import torch
+    _proj_sigs(lib())
+    n, ids, th = _ids_theta(op_ids, theta)
+    if out is None:
+        out = torch.empty_like(psi0)
+    ws, wsb = _ws(sector, pool, n, ws)
+    states = _proj_states(sector, pool, ids, n, states, psi0.device)
+    _check(lib().cvq_apply_ansatz_projected(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                            _ptr(psi0), _ptr(out), _ptr(states), states.numel(), _ptr(ws), wsb,
+                                            _stream(stream)), "cvq_apply_ansatz_projected")
+    return out
+
+
+def energy_and_grad_projected(sector: Sector, pool: ProjectedPool, op_ids, theta, psi0, E=None, grad=None, ws=None,
+                              states=None, stream=None):
+    import torch
+    _proj_sigs(lib())
+    n, ids, th = _ids_theta(op_ids, theta)
+    if E is None:
+        E = torch.empty(1, dtype=torch.float64, device=psi0.device)
+    if grad is None:
+        grad = torch.empty(max(n, 1), dtype=torch.float64, device=psi0.device)
+    ws, wsb = _ws(sector, pool, n, ws)
+    states = _proj_states(sector, pool, ids, n, states, psi0.device)
+    _check(lib().cvq_energy_and_grad_projected(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                               _ptr(psi0), _ptr(E), _ptr(grad), _ptr(states), states.numel(),
+                                               _ptr(ws), wsb, _stream(stream)), "cvq_energy_and_grad_projected")
+    return E, grad[:n]
