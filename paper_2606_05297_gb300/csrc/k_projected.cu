@@ -104,7 +104,13 @@ __global__ void __launch_bounds__(NTHREADS)
     bkc_orbit(S, g.i, j, it, items, idx.f0, cls);
     for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
       const BlockDesc bd = sB[bi];
-      if (bd.bext < 2) continue;
+      if (bd.bext < 2) {  // identity and no gradient term, but lambda still becomes mu
+        const int64_t x = idx(sM[bd.mem_off]);
+        const cdf la = lam[x], ps = cur[x];
+        lam[x] = make_cdf(df_mul(df_add(re_of(la), df_neg(df_mul(r, re_of(ps)))), invN),
+                          df_mul(df_add(im_of(la), df_neg(df_mul(r, im_of(ps)))), invN));
+        continue;
+      }
       proj_block<REALU>(bd.size, sU + bd.u_off, sD + bd.u_off, sM + bd.mem_off, idx, prev, cur, lam, r, invN, stg,
                         gacc);
     }
