@@ -42,6 +42,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--warm", type=int, default=0, help="unprofiled repetitions before cudaProfilerStart")
     ap.add_argument("--kernels", action="store_true", help="print per-kernel event timings of the profiled range")
+    ap.add_argument("--projected", type=int, default=0,
+                    help="Kitaev workloads: projected gates with this inner cutoff (Sec. V.A) instead of truncated ones")
     a = ap.parse_args()
     import torch
     from paper_2606_05297_gb300 import build, cvq
@@ -49,12 +51,13 @@ def main():
     build.build()
     m, pool = make(a.workload)
     s = cvq.Sector(m)
-    p = cvq.Pool(s, pool)
+    p = cvq.ProjectedPool(s, pool, a.projected) if a.projected else cvq.Pool(s, pool)
+    eg = cvq.energy_and_grad_projected if a.projected else cvq.energy_and_grad
     ids, th = W.random_ansatz(len(pool), a.depth, a.seed, scale=0.2)
     psi0 = torch.from_numpy(W.random_state(s.dim, a.seed + 1)).cuda()
     ws = s.workspace(p, a.depth)
     for _ in range(a.warm):
-        cvq.energy_and_grad(s, p, ids, th, psi0, ws=ws)
+        eg(s, p, ids, th, psi0, ws=ws)
         cvq.screen_pool(s, p, psi0, ws=ws)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()  # profiled range, for profilers started with --profile-from-start off
@@ -62,7 +65,7 @@ def main():
         cvq.profile_start(1 << 16)
     t0 = time.perf_counter()
     for _ in range(a.reps):
-        E, g = cvq.energy_and_grad(s, p, ids, th, psi0, ws=ws)
+        E, g = eg(s, p, ids, th, psi0, ws=ws)
         cvq.screen_pool(s, p, psi0, ws=ws)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
