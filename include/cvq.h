@@ -344,6 +344,12 @@ typedef struct {
 } cvq_kernel_stat;
 
 int cvq_profile_start(int capacity);
+/* Time only one launch in `every` of each kernel kind (default 1: all).  The
+ * others are still counted (launches, bytes, flops), and a kind's device time
+ * is its timed launches' time scaled to all of its launches; fewer event
+ * records keep the host's launch path short.  Takes effect at the next
+ * cvq_profile_start. */
+int cvq_profile_sample(int every);
 int cvq_profile_stop(cvq_kernel_stat *out, int max_out, int *n_out);
 
 #ifdef __cplusplus

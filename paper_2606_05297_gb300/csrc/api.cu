@@ -63,6 +63,10 @@ static std::mutex g_prof_mu;
 static bool g_prof_on = false;
 static std::vector<ProfRec> g_prof;
 static size_t g_prof_n = 0;
+static int g_prof_every = 1;                 // time one launch in this many of each kind
+static int64_t g_prof_count[KK_COUNT];       // every launch while timing is on
+static int64_t g_prof_timed[KK_COUNT];       // of which timed with an event pair
+static double g_prof_bytes[KK_COUNT], g_prof_flops[KK_COUNT];
 
 // Brackets one launch with an event pair on its stream while timing is on.
 struct ProfScope {
@@ -71,7 +75,11 @@ struct ProfScope {
   ProfScope(int kind, cudaStream_t s, double bytes, double flops) : st(s) {
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on || g_prof_n >= g_prof.size()) return;
+    if (!g_prof_on) return;
+    g_prof_bytes[kind] += bytes;
+    g_prof_flops[kind] += flops;
+    if (g_prof_count[kind]++ % g_prof_every != 0 || g_prof_n >= g_prof.size()) return;
+    ++g_prof_timed[kind];
     idx = (int)g_prof_n++;
     g_prof[idx].kind = kind;
     g_prof[idx].bytes = bytes;
@@ -98,7 +106,18 @@ extern "C" int cvq_profile_start(int capacity) {
     }
   }
   g_prof_n = 0;
+  memset(g_prof_count, 0, sizeof g_prof_count);
+  memset(g_prof_timed, 0, sizeof g_prof_timed);
+  memset(g_prof_bytes, 0, sizeof g_prof_bytes);
+  memset(g_prof_flops, 0, sizeof g_prof_flops);
   g_prof_on = true;
+  return CVQ_OK;
+}
+
+extern "C" int cvq_profile_sample(int every) {
+  if (every < 1) return fail(CVQ_EINVAL, "every must be >= 1");
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_every = every;
   return CVQ_OK;
 }
 
@@ -112,10 +131,13 @@ extern "C" int cvq_profile_stop(cvq_kernel_stat* out, int max_out, int* n_out) {
     CVQ_CUDA(cudaEventSynchronize(r.b), "cudaEventSynchronize");
     float ms = 0.f;
     CVQ_CUDA(cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
-    acc[r.kind].launches += 1;
     acc[r.kind].ms += ms;
-    acc[r.kind].bytes += r.bytes;
-    acc[r.kind].flops += r.flops;
+  }
+  for (int k = 0; k < KK_COUNT; ++k) {  // every launch counts; the timed ones stand for their kind
+    acc[k].launches = g_prof_count[k];
+    if (g_prof_timed[k] > 0) acc[k].ms *= (double)g_prof_count[k] / (double)g_prof_timed[k];
+    acc[k].bytes = g_prof_bytes[k];
+    acc[k].flops = g_prof_flops[k];
   }
   g_prof_n = 0;
   int n = 0;
@@ -1364,7 +1386,11 @@ int internal_sector_device(const cvq_sector* s) { return s ? s->device : -1; }
 int internal_prof_mlp_begin(cudaStream_t st, double bytes, double flops) {
   if (!g_prof_on) return -1;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  if (!g_prof_on || g_prof_n >= g_prof.size()) return -1;
+  if (!g_prof_on) return -1;
+  g_prof_bytes[KK_MLP] += bytes;
+  g_prof_flops[KK_MLP] += flops;
+  if (g_prof_count[KK_MLP]++ % g_prof_every != 0 || g_prof_n >= g_prof.size()) return -1;
+  ++g_prof_timed[KK_MLP];
   const int idx = (int)g_prof_n++;
   g_prof[idx].kind = KK_MLP;
   g_prof[idx].bytes = bytes;

@@ -245,6 +245,12 @@ class _KStat(C.Structure):
                 ("flops", C.c_double)]
 
 
+def profile_sample(every: int):
+    L = lib()
+    L.cvq_profile_sample.argtypes = [C.c_int]
+    _check(L.cvq_profile_sample(int(every)), "cvq_profile_sample")
+
+
 def profile_start(capacity: int = 1 << 20):
     """Time every later launch of this library with CUDA events on its stream."""
     L = lib()
