@@ -149,10 +149,17 @@ def sum_over_ranks(x, ws):
     return _reduce(x, ws, dist.ReduceOp.SUM)
 
 
-def csrc_hash():
+# Sources each measured kernel is compiled from: a committed traffic figure
+# stands only while these are unchanged.
+KERNEL_SOURCES = {
+    "adjoint_block": ["k_gate_impl.cuh", "k_gate_bh_adj.cu", "k_gate_bkc_adj.cu", "cvq_internal.cuh", "df.cuh"],
+}
+
+
+def csrc_hash(files=None):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2606_05297_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files if files is not None else os.listdir(d)):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -160,15 +167,15 @@ def csrc_hash():
 
 def measured_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was captured on the current kernel sources."""
+    was captured on the kernel's current sources."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        if d.get("csrc_hash") != csrc_hash():
-            return None
         e = d["kernels"].get(kernel)
-        return None if e is None else float(e["dram_bytes_per_launch_full_size"])
+        if e is None or e.get("sources_hash") != csrc_hash(KERNEL_SOURCES.get(kernel)):
+            return None
+        return float(e["dram_bytes_per_launch_full_size"])
     except Exception:
         return None
 
