@@ -199,18 +199,6 @@ int cvq_energy_and_grad_projected(const cvq_sector *s, const cvq_pool *p, const 
                                   int n, const cvq_c128 *psi0, double *E_dev, double *grad_dev, void *states,
                                   size_t states_bytes, void *workspace, size_t workspace_bytes, void *stream);
 
-/* cvq_energy_and_grad with every segment's forward output kept (a segment is
- * a block gate or a run of diagonal gates): the reverse sweep then reads psi_k
- * instead of recomputing it with U^dag, so each block gate's reverse step
- * updates lambda only.  Same results as cvq_energy_and_grad to rounding.
- * states: device, 256-byte aligned, >= cvq_kept_states_bytes (one state per
- * segment, 16 B per amplitude).  Errors as cvq_energy_and_grad, plus EINVAL
- * for a short buffer and for projected pools. */
-int cvq_kept_states_bytes(const cvq_sector *s, const cvq_pool *p, const int *op_ids, int n, size_t *bytes);
-int cvq_energy_and_grad_kept(const cvq_sector *s, const cvq_pool *p, const int *op_ids, const double *theta, int n,
-                             const cvq_c128 *psi0, double *E_dev, double *grad_dev, void *states, size_t states_bytes,
-                             void *workspace, size_t workspace_bytes, void *stream);
-
 /* One step of the Lanczos recurrence used for the exact ground energy E0
  * that defines Delta E = |E - E0| (Sec. IV.B stopping rule; exact
  * diagonalisation there).  Before the call the caller has w = H v and

@@ -190,7 +190,7 @@ class Adapt:
 
     def __init__(self, model: Model, pool_ops: Sequence[Op], init_occ: Sequence[int], warm_ops: Sequence[Op] = (),
                  warm_theta: Sequence[float] = (), n_max: int = 256, stream=None, hessian_recycling: bool = False,
-                 fix_warm: bool = False, keep_states: Optional[bool] = None, keep_budget: float = 16e9):
+                 fix_warm: bool = False):
         import torch
         self.torch = torch
         self.model = model
@@ -211,11 +211,6 @@ class Adapt:
         # parameter); the warm-up layer keeps its initial parameters
         self.hessian_recycling = hessian_recycling
         self.fix_warm = fix_warm
-        # keep every segment's forward state when it fits the budget: the reverse
-        # sweep then updates lambda only (cvq_energy_and_grad_kept)
-        if keep_states is None:
-            keep_states = n_max * self.sector.dim * 16.0 <= keep_budget
-        self.states = cvq.kept_states(self.sector, self.pool, n_max) if keep_states else None
         self._out = torch.empty(n_max + 1, dtype=torch.float64, device="cuda")
         self._host = torch.empty(n_max + 1, dtype=torch.float64, pin_memory=True)
         self._g = torch.empty(self.K, dtype=torch.float64, device="cuda")
@@ -225,14 +220,8 @@ class Adapt:
     # energy and gradient of the current ansatz structure at theta (host vectors)
     def fg(self, theta):
         n = len(self.ids)
-        if self.states is not None:
-            E, g = cvq.energy_and_grad_kept(self.sector, self.pool, self.ids, theta, self.psi0, E=self._out[0:1],
-                                            grad=self._out[1:n + 1] if n else self._out[1:2], ws=self.ws,
-                                            states=self.states, stream=self.stream)
-        else:
-            E, g = cvq.energy_and_grad(self.sector, self.pool, self.ids, theta, self.psi0, E=self._out[0:1],
-                                       grad=self._out[1:n + 1] if n else self._out[1:2], ws=self.ws,
-                                       stream=self.stream)
+        E, g = cvq.energy_and_grad(self.sector, self.pool, self.ids, theta, self.psi0, E=self._out[0:1],
+                                   grad=self._out[1:n + 1] if n else self._out[1:2], ws=self.ws, stream=self.stream)
         h = self._host[: n + 1]
         h.copy_(self._out[: n + 1], non_blocking=True)
         (self.stream or self.torch.cuda.current_stream()).synchronize()

@@ -709,7 +709,6 @@ static int check_ws(const cvq_sector* s, const cvq_pool* p, int n, void* ws, siz
 // with lambda (3 b - 2).  Diagonal gates: 1 (forward) or 3 (reverse) per amplitude.
 struct OpCost {
   double fb, ff, ab, af;
-  double kf = 0.0;  // reverse step flops when psi_k is kept (lambda <- U^dag lambda and the gradient term)
 };
 
 static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
@@ -726,7 +725,7 @@ static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
   }
   // Blocks of one member have a zero generator: the gate is the identity there
   // and the kernels skip them, so they count neither bytes nor flops.
-  double ff = 0.0, af = 0.0, kf = 0.0, amps = 0.0;
+  double ff = 0.0, af = 0.0, amps = 0.0;
   for (int cls = 0; cls < t.nclass; ++cls) {
     double orbits;
     if (S.kind == CVQ_BH) {
@@ -737,24 +736,21 @@ static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
       for (int r = 0; r < S.L - nm; ++r) items *= S.D;
       orbits = (S.L == nm) ? (cls == S.parity ? 1.0 : 0.0) : items / 2.0;
     }
-    double bf = 0.0, baf = 0.0, bkf = 0.0;
+    double bf = 0.0, baf = 0.0;
     for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
       const int b = p->blk_size[t.blk_base + bi];
       if (b < 2) continue;
       bf += 8.0 * b * b;
       baf += 8.0 * (2.0 * b * b + 3.0 * b - 2.0);
-      bkf += 8.0 * (1.0 * b * b + 3.0 * b - 2.0);
       amps += orbits * b;
     }
     ff += orbits * bf;
     af += orbits * baf;
-    kf += orbits * bkf;
   }
   c.fb = 32.0 * amps;
   c.ab = 64.0 * amps;
   c.ff = ff;
   c.af = af;
-  c.kf = kf;
   return c;
 }
 
@@ -1162,104 +1158,6 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
     }
   }
   {
-    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * n, (double)NBLK * n);
-    CVQ_CUDA(launch_reduce(partial, n, NBLK, 2.0, grad_dev, st), "reduce grad");
-  }
-  return CVQ_OK;
-}
-
-// ------------------------------------------------------------------ kept forward states
-
-// One df state per segment: the output of that segment, written by the forward
-// sweep (block gates write only the members they change; the reverse step of
-// that gate reads only those).
-extern "C" int cvq_kept_states_bytes(const cvq_sector* s, const cvq_pool* p, const int* op_ids, int n, size_t* bytes) {
-  if (!s || !p || !bytes || (n > 0 && !op_ids)) return fail(CVQ_EINVAL, "null argument");
-  if (n < 0 || n > MAX_GATES) return fail(CVQ_EINVAL, "ansatz length %d outside [0, %d]", n, MAX_GATES);
-  for (int k = 0; k < n; ++k)
-    if (op_ids[k] < 0 || op_ids[k] >= p->K) return fail(CVQ_EINVAL, "op_ids[%d] = %d outside the pool", k, op_ids[k]);
-  *bytes = segments(p, op_ids, n).size() * al256((size_t)s->S.dim * sizeof(cdf));
-  return CVQ_OK;
-}
-
-extern "C" int cvq_energy_and_grad_kept(const cvq_sector* s, const cvq_pool* p, const int* op_ids,
-                                        const double* theta, int n, const cvq_c128* psi0, double* E_dev,
-                                        double* grad_dev, void* states, size_t states_bytes, void* ws, size_t wsb,
-                                        void* stream) {
-  if (!s || !p || !psi0 || !E_dev || (n > 0 && !grad_dev)) return fail(CVQ_EINVAL, "null argument");
-  if (p->dc) return fail(CVQ_EINVAL, "a projected pool needs cvq_energy_and_grad_projected");
-  if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
-  Layout l;
-  if (int rc = check_ws(s, p, n, ws, wsb, l)) return rc;
-  size_t need = 0;
-  if (int rc = cvq_kept_states_bytes(s, p, op_ids, n, &need)) return rc;
-  if (need > 0 && (!states || ((uintptr_t)states & 255))) return fail(CVQ_EINVAL, "state buffer NULL or not 256-byte aligned");
-  if (states_bytes < need) return fail(CVQ_EINVAL, "state buffer of %zu bytes, %zu needed", states_bytes, need);
-  cudaStream_t st = (cudaStream_t)stream;
-  cdf* psi = (cdf*)((char*)ws + l.psi);
-  cdf* lam = (cdf*)((char*)ws + l.lam);
-  cdf* U = (cdf*)((char*)ws + l.U);
-  double* partial = (double*)((char*)ws + l.partial);
-  const size_t stride = al256((size_t)s->S.dim * sizeof(cdf));
-  auto slot = [&](int k) { return (cdf*)((char*)states + (size_t)k * stride); };
-  if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
-  if (int rc = to_df(s, psi0, psi, st)) return rc;
-  const std::vector<Seg> segs = segments(p, op_ids, n);
-  const double dim = (double)s->S.dim;
-  for (size_t si = 0; si < segs.size(); ++si) {
-    const Seg& g = segs[si];
-    if (g.diag) {
-      DiagRunArg a;
-      diag_run_arg(s, p, op_ids, theta, g, a);
-      {
-        ProfScope ps(KK_GATE_DIAG, st, 32.0 * dim, dim * (8.0 * s->S.L + 8.0 * a.npair));
-        CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, nullptr, nullptr, false, st), "diagonal run");
-      }
-      CVQ_CUDA(cudaMemcpyAsync(slot((int)si), psi, sizeof(cdf) * (size_t)s->S.dim, cudaMemcpyDeviceToDevice, st),
-               "keep state");
-    } else {
-      const GateArg ga = gate_arg(p, op_ids[g.k0], U + (size_t)g.k0 * p->ustride);
-      const OpCost c = op_cost(s, p, op_ids[g.k0]);
-      ProfScope ps(KK_GATE, st, c.fb + 16.0 * (c.fb / 32.0), c.ff);
-      CVQ_CUDA(launch_gate_keep(s->S, ga, p->P, psi, slot((int)si), st), "gate");
-    }
-  }
-  double* pE = partial + (size_t)n * NBLK;
-  if (int rc = run_apply_H(s, psi, lam, pE, st)) return rc;
-  {
-    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK, NBLK);
-    CVQ_CUDA(launch_reduce(pE, 1, NBLK, 1.0, E_dev, st), "reduce E");
-  }
-  for (int si = (int)segs.size() - 1; si >= 0; --si) {
-    const Seg& g = segs[si];
-    if (g.diag) {  // the plain reverse step on the kept output (consumed)
-      DiagRunArg a;
-      diag_run_arg(s, p, op_ids, theta, g, a);
-      cdf* pk = slot(si);
-      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_ACC) {
-        DiagGradArg ga;
-        memset(&ga, 0, sizeof ga);
-        ga.m = std::min(DIAG_ACC, g.m - q0);
-        for (int q = 0; q < ga.m; ++q) {
-          ga.diag[q] = a.diag[q0 + q];
-          ga.gi[q] = a.gi[q0 + q];
-          ga.gj[q] = a.gj[q0 + q];
-        }
-        ProfScope ps(KK_ADJ_DIAG, st, 32.0 * dim, dim * (16.0 + 4.0 * ga.m));
-        CVQ_CUDA(launch_diag_grad(s->S, ga, pk, lam, partial + (size_t)(g.k0 + q0) * NBLK, st), "diagonal-run gradients");
-      }
-      ProfScope ps(KK_ADJ_DIAG, st, 64.0 * dim,
-                   dim * (8.0 * s->S.L + 8.0 * a.npair + 24.0 + 4.0 * std::min(g.m, DIAG_ACC)));
-      CVQ_CUDA(launch_diag_run(s->S, a, pk, pk, lam, partial + (size_t)g.k0 * NBLK, true, st), "adjoint diagonal run");
-    } else {
-      const GateArg ga = gate_arg(p, op_ids[g.k0], U + (size_t)g.k0 * p->ustride);
-      const OpCost c = op_cost(s, p, op_ids[g.k0]);
-      ProfScope ps(KK_ADJ, st, 0.75 * c.ab, c.kf);  // psi_k read; lambda read and written
-      CVQ_CUDA(launch_gate_adjoint_kept(s->S, ga, p->P, slot(si), lam, partial + (size_t)g.k0 * NBLK, st),
-               "adjoint gate");
-    }
-  }
-  if (n > 0) {
     ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * n, (double)NBLK * n);
     CVQ_CUDA(launch_reduce(partial, n, NBLK, 2.0, grad_dev, st), "reduce grad");
   }

@@ -343,11 +343,6 @@ cudaError_t launch_apply_H(const SectorDev& S, const cdf* psi, cdf* sigma, doubl
 cudaError_t launch_reduce(const double* partial, int nred, int nblk, double scale, double* out, cudaStream_t st);
 cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_dev, PoolDev P, cdf* U, cudaStream_t st);
 cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* src, cdf* dst, cudaStream_t st);
-// In place on psi, also writing the changed members to keep (its other members are left as they are).
-cudaError_t launch_gate_keep(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* keep, cudaStream_t st);
-// Reverse step from the kept output psi_k of the gate: gradient term and lambda <- U^dag lambda only.
-cudaError_t launch_gate_adjoint_kept(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* psi_k, cdf* lam,
-                                     double* partial, cudaStream_t st);
 cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial,
                                 cudaStream_t st);
 // Gradient-only pass over up to DIAG_ACC gates of a diagonal run (their f type and modes).

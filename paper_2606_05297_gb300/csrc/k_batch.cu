@@ -165,16 +165,16 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       acc_zero(gacc);
       if (KIND == CVQ_BKC) {
         if (t.realu)
-          bkc_gate_range<ADJ, true>(S, sh.gi, sh.gj, t, m, it.a + threadIdx.x, it.b, NTHREADS, I.psi, I.psi, ADJ ? I.lam : nullptr,
+          bkc_gate_range<ADJ, true>(S, sh.gi, sh.gj, t, m, it.a + threadIdx.x, it.b, NTHREADS, I.psi, I.psi, I.lam,
                                     gacc);
         else
-          bkc_gate_range<ADJ, false>(S, sh.gi, sh.gj, t, m, it.a + threadIdx.x, it.b, NTHREADS, I.psi, I.psi, ADJ ? I.lam : nullptr,
+          bkc_gate_range<ADJ, false>(S, sh.gi, sh.gj, t, m, it.a + threadIdx.x, it.b, NTHREADS, I.psi, I.psi, I.lam,
                                      gacc);
       } else {
         for (int64_t c = it.a; c < it.b; ++c) {
           const int4 ch = I.P.chunks[t.chunk_base + c];
-          if (t.realu) bh_gate_chunk<ADJ, true>(S, G32, sh.gi, sh.gj, t, m, ch, I.psi, I.psi, ADJ ? I.lam : nullptr, gacc);
-          else bh_gate_chunk<ADJ, false>(S, G32, sh.gi, sh.gj, t, m, ch, I.psi, I.psi, ADJ ? I.lam : nullptr, gacc);
+          if (t.realu) bh_gate_chunk<ADJ, true>(S, G32, sh.gi, sh.gj, t, m, ch, I.psi, I.psi, I.lam, gacc);
+          else bh_gate_chunk<ADJ, false>(S, G32, sh.gi, sh.gj, t, m, ch, I.psi, I.psi, I.lam, gacc);
         }
       }
       if (ADJ) {

@@ -182,9 +182,7 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
       acc_zero(ar);
       acc_zero(ai);
       for (int l = 0; l < b; ++l) cmac_cb<REALU, false>(ar, ai, Ub[k * b + l], stg[l * NTHREADS + tid], (k ^ l) & 1);
-      const cdf v = make_cdf(acc_get(ar), acc_get(ai));
-      dst[X(k)] = v;
-      if (lam) lam[X(k)] = v;  // forward: lam, when given, receives a copy of the changed members
+      dst[X(k)] = make_cdf(acc_get(ar), acc_get(ai));
     }
     return;
   }
@@ -217,7 +215,7 @@ __device__ __forceinline__ void apply_block(const int b, const cdf* __restrict__
       lk = lk1;
     }
   }
-  for (int k = 0; dst && k < b; ++k) {  // psi <- U^dag psi (skipped when psi_{k-1} is kept elsewhere)
+  for (int k = 0; k < b; ++k) {  // psi <- U^dag psi
     dfacc ar, ai;
     acc_zero(ar);
     acc_zero(ai);

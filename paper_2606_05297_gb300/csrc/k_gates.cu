@@ -98,15 +98,6 @@ cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const c
   return launch_gate_impl<false>(S, g, P, src, dst, nullptr, nullptr, st);
 }
 
-cudaError_t launch_gate_keep(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* keep, cudaStream_t st) {
-  return launch_gate_impl<false>(S, g, P, psi, psi, keep, nullptr, st);
-}
-
-cudaError_t launch_gate_adjoint_kept(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* psi_k, cdf* lam,
-                                     double* partial, cudaStream_t st) {
-  return launch_gate_impl<true>(S, g, P, psi_k, nullptr, lam, partial, st);
-}
-
 cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial,
                                 cudaStream_t st) {
   return launch_gate_impl<true>(S, g, P, psi, psi, lam, partial, st);

@@ -547,32 +547,3 @@ def energy_and_grad_projected(sector: Sector, pool: ProjectedPool, op_ids, theta
                                                _ptr(psi0), _ptr(E), _ptr(grad), _ptr(states), states.numel(),
                                                _ptr(ws), wsb, _stream(stream)), "cvq_energy_and_grad_projected")
     return E, grad[:n]
-
-
-def kept_states(sector: Sector, pool: Pool, n_max: int, device="cuda"):
-    """A state buffer for cvq_energy_and_grad_kept large enough for any ansatz of up to n_max gates."""
-    import torch
-    stride = (sector.dim * 16 + 255) // 256 * 256
-    return torch.empty(max(n_max, 1) * stride, dtype=torch.uint8, device=device)
-
-
-def energy_and_grad_kept(sector: Sector, pool: Pool, op_ids, theta, psi0, E=None, grad=None, ws=None, states=None,
-                         stream=None):
-    """cvq_energy_and_grad with the forward states kept (see the header)."""
-    import torch
-    L = lib()
-    L.cvq_energy_and_grad_kept.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double),
-                                           C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
-                                           C.c_void_p, C.c_size_t, C.c_void_p]
-    n, ids, th = _ids_theta(op_ids, theta)
-    if E is None:
-        E = torch.empty(1, dtype=torch.float64, device=psi0.device)
-    if grad is None:
-        grad = torch.empty(max(n, 1), dtype=torch.float64, device=psi0.device)
-    ws, wsb = _ws(sector, pool, n, ws)
-    if states is None:
-        states = kept_states(sector, pool, n, psi0.device)
-    _check(L.cvq_energy_and_grad_kept(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n, _ptr(psi0),
-                                      _ptr(E), _ptr(grad), _ptr(states), states.numel(), _ptr(ws), wsb,
-                                      _stream(stream)), "cvq_energy_and_grad_kept")
-    return E, grad[:n]
