@@ -1,13 +1,16 @@
 """Learned-proposal ADAPT against plain full-screen ADAPT on the same GPU.
 
     python -m paper_2606_05297_gb300.race [--L 10 --d 6] [--max-ops 40]
+    python -m paper_2606_05297_gb300.race --target bh --L 8 --U 3.4 --max-ops 150
 
 1. Trace collection: plain ADAPT runs on the Bose-Hubbard L=4 chain (Mott
    start), the L=12 periodic chain at U/J = 3.4 and the Kitaev chain with
    Kerr at L=8, d=8 (vacuum start) store one training list per iteration;
    the scorer is trained on them with the project's own kernels.
-2. E0 of the target instance (Kitaev chain with Kerr, t=1, Delta=0.6,
-   K=0.3, open chain) by Lanczos on the device.
+2. E0 of the target instance by Lanczos on the device: the Kitaev chain
+   with Kerr (t=1, Delta=0.6, K=0.3, open chain; default), or with
+   `--target bh` a periodic Bose-Hubbard chain at N = L and the given U/J
+   (a chain length the traces do not contain), all-pairs pool, Mott start.
 3. Both arms from the same warm start: plain full-screen ADAPT, and learned
    ADAPT (exact screen of the scorer's top k, full screen every
    `full_every` iterations, online training on every full screen).  Each
@@ -63,7 +66,9 @@ def run_arm(make, E0, max_ops, grad_tol=1e-6):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--target", choices=["kitaev", "bh"], default="kitaev")
     ap.add_argument("--L", type=int, default=10)
+    ap.add_argument("--U", type=float, default=3.4, help="U/J of the Bose-Hubbard target")
     ap.add_argument("--d", type=int, default=6)
     ap.add_argument("--max-ops", type=int, default=40)
     ap.add_argument("--trace-ops", type=int, default=20)
@@ -86,9 +91,16 @@ def main(argv=None):
     losses = tr.train(a.train_steps)
     t_train = time.perf_counter() - t0
 
-    m = W.kitaev_kerr(a.L, a.d, t=1.0, Delta=0.6, K=0.3, periodic=False)
-    pool = W.bkc_kerr_pool(a.L)
-    occ = W.vacuum_occupation(a.L)
+    if a.target == "bh":
+        m = W.bose_hubbard(a.L, a.L, J=1.0, U=a.U, periodic=True)
+        pool = W.bh_allpairs_pool(a.L)
+        occ = W.mott_occupation(a.L, a.L)
+        label = f"bose_hubbard periodic L={a.L} N={a.L} J=1 U={a.U}"
+    else:
+        m = W.kitaev_kerr(a.L, a.d, t=1.0, Delta=0.6, K=0.3, periodic=False)
+        pool = W.bkc_kerr_pool(a.L)
+        occ = W.vacuum_occupation(a.L)
+        label = f"kitaev_kerr open L={a.L} d={a.d} t=1 Delta=0.6 K=0.3"
     warm = W.hva_layer(m)
     wth = W.warm_start_thetas(len(warm), 0)
     sec = cvq.Sector(m)
@@ -108,7 +120,7 @@ def main(argv=None):
         E0, a.max_ops)
     st = la.stats
     out = dict(
-        target=dict(model=f"kitaev_kerr open L={a.L} d={a.d} t=1 Delta=0.6 K=0.3", dim=int(la.sector.dim),
+        target=dict(model=label, dim=int(la.sector.dim),
                     pool=len(pool), E0=E0, warm_start_gates=len(warm)),
         training=dict(lists=len(tr.X), rows=tr.rows(), loss_first=losses[0] if losses else None,
                       loss_last=losses[-1] if losses else None, seconds=t_train,
