@@ -216,23 +216,35 @@ static double string_on_ket(const orc_sector *s, const orc_string *st, int *n) {
 }
 
 /* out = O in, by applying every string to every basis ket (scatter form).
- * Returns 3 if some string maps a sector state out of the sector (the
- * operator does not respect the symmetry). */
+ * Strings are taken one after another; for one string the map |x> -> |y> is
+ * a fixed shift of the occupations, so distinct kets never meet in one y and
+ * the kets of a string can be spread over OpenMP threads without a race.
+ * Each out[y] thus sums its terms in string order.  Returns 3 if some string
+ * maps a sector state out of the sector (the operator does not respect the
+ * symmetry). */
+#define ORC_PAR_MIN 32768  /* smaller sectors run on one thread */
 int orc_apply(void *sh, void *oh, const cplx *in, cplx *out) {
     const orc_sector *s = (const orc_sector *)sh;
     const orc_op *o = (const orc_op *)oh;
-    int n[32];
+    int err = 0;
     memset(out, 0, (size_t)s->dim * sizeof(cplx));
-    for (int64_t x = 0; x < s->dim; ++x) {
-        if (in[x] == 0.0) continue;
-        for (int t = 0; t < o->ns; ++t) {
+    for (int t = 0; t < o->ns; ++t) {
+#pragma omp parallel for schedule(static) if (s->dim >= ORC_PAR_MIN)
+        for (int64_t x = 0; x < s->dim; ++x) {
+            int n[32];
+            if (in[x] == 0.0) continue;
             key_tuple(s, s->key[x], n);
             double f = string_on_ket(s, &o->s[t], n);
             if (f == 0.0) continue;
             int64_t y = sector_find(s, n);
-            if (y < 0) return 3;
+            if (y < 0) {
+#pragma omp atomic write
+                err = 3;
+                continue;
+            }
             out[y] += o->s[t].c * f * in[x];
         }
+        if (err) return err;
     }
     return 0;
 }
@@ -243,8 +255,10 @@ int orc_apply(void *sh, void *oh, const cplx *in, cplx *out) {
 int orc_apply_rows(void *sh, void *oh, const cplx *in, const int64_t *rows, int64_t nrows, cplx *out) {
     const orc_sector *s = (const orc_sector *)sh;
     const orc_op *o = (const orc_op *)oh;
-    int n[32];
+    int err = 0;
+#pragma omp parallel for schedule(static) if (nrows >= ORC_PAR_MIN)
     for (int64_t i = 0; i < nrows; ++i) {
+        int n[32];
         cplx acc = 0.0;
         for (int t = 0; t < o->ns; ++t) {
             const orc_string *st = &o->s[t];
@@ -259,12 +273,16 @@ int orc_apply_rows(void *sh, void *oh, const cplx *in, const int64_t *rows, int6
             double f = string_on_ket(s, &adj, n);
             if (f == 0.0) continue;
             int64_t x = sector_find(s, n);
-            if (x < 0) return 3;
+            if (x < 0) {
+#pragma omp atomic write
+                err = 3;
+                break;
+            }
             acc += st->c * f * in[x];
         }
         out[i] = acc;
     }
-    return 0;
+    return err;
 }
 
 /* Upper bound on ||O||_2 for anti-Hermitian or Hermitian O: the largest
@@ -273,9 +291,10 @@ int orc_apply_rows(void *sh, void *oh, const cplx *in, const int64_t *rows, int6
 double orc_norm_bound(void *sh, void *oh) {
     const orc_sector *s = (const orc_sector *)sh;
     const orc_op *o = (const orc_op *)oh;
-    int n[32];
     double best = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : best) if (s->dim >= ORC_PAR_MIN)
     for (int64_t x = 0; x < s->dim; ++x) {
+        int n[32];
         double col = 0.0;
         for (int t = 0; t < o->ns; ++t) {
             key_tuple(s, s->key[x], n);
@@ -322,6 +341,7 @@ int orc_expm_apply(void *sh, void *oh, double theta, const cplx *in, cplx *out) 
             int rc = orc_apply(sh, oh, term, tmp);
             if (rc) { free(v); free(term); free(tmp); return rc; }
             double tn = 0.0;
+#pragma omp parallel for schedule(static) if (dim >= ORC_PAR_MIN)
             for (int64_t x = 0; x < dim; ++x) {
                 term[x] = tmp[x] * (h / k);
                 v[x] += term[x];
