@@ -4,7 +4,7 @@ Follows Sec. IV.B: evaluate the Eq. (grad) gradient of every pool operator on
 the current state, append the operator with the largest |g| as
 exp(theta A) with theta = 0, re-minimise E over all parameters with BFGS.
 
-Readings where the paper is silent (see the design notes):
+Readings where the paper is silent:
   * warm start (Sec. IV.B, App. C/D): one HVA layer with angles U[-0.05, 0.05]
     is optimised first (L-inf gradient tolerance 1e-9, 1000 iterations) and is
     re-optimised together with every ADAPT parameter afterwards;
