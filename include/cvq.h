@@ -26,8 +26,10 @@
  *     Calls only enqueue work; results are valid after the stream is
  *     synchronised.  Only cvq_init_sector and cvq_set_pool synchronise.
  *   - Device-side failures are not possible by construction (every index is
- *     derived from a checked sector); a CUDA launch error is reported as
- *     CVQ_ECUDA.
+ *     derived from a checked sector, and no kernel waits on another); a CUDA
+ *     launch or runtime error is reported as CVQ_ECUDA, except an error that
+ *     leaves the CUDA context unusable, reported as CVQ_EDEVICE
+ *     (cvq_status_from_cuda gives the mapping).
  *   - cvq_sector and cvq_pool are opaque, library-owned, immutable after
  *     creation, and may be shared by concurrent calls on different streams.
  *
@@ -51,10 +53,19 @@ enum cvq_status {
     CVQ_OK = 0,
     CVQ_EINVAL = 1,    /* bad argument (sizes, limits, op outside the sector's symmetry) */
     CVQ_ENOMEM = 2,    /* host or device allocation failed */
-    CVQ_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
-    CVQ_ETIMEOUT = 4,  /* a bounded device wait ran out (batched engine) */
-    CVQ_EDEVICE = 5    /* a kernel reported an error through its status word */
+    CVQ_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed; the context is still usable */
+    /* 4 is not used: no call of this library waits on the device with a time limit */
+    CVQ_EDEVICE = 5    /* the CUDA context is unusable: some kernel of this process hit a device-side
+                          fault (an illegal address or instruction, a failed assertion, an
+                          uncorrectable ECC error); every later call fails the same way until the
+                          process resets the device */
 };
+
+/* The status this library returns for the CUDA runtime error code `cuda_error`
+ * (a cudaError_t value): CVQ_OK for cudaSuccess, CVQ_EDEVICE for the errors
+ * that leave the context unusable, CVQ_ENOMEM for cudaErrorMemoryAllocation,
+ * CVQ_ECUDA otherwise.  Host only; needs no device. */
+int cvq_status_from_cuda(int cuda_error);
 
 enum cvq_kind { CVQ_BH = 0, CVQ_BKC = 1 };
 
@@ -310,22 +321,27 @@ int cvq_batch_set_active(cvq_batch *b, const int *active, void *stream);
 int cvq_batch_info(const cvq_batch *b, int *kernels_per_eval, int *items, int *layers, int64_t *n_params);
 
 /* Pool screen for callers that cannot allocate device memory.  The paper has
- * no counterpart to this call: it exists for code that must not call
- * cudaMalloc when it screens -- code running while a stream is captured into a
- * CUDA graph, real-time loops that cannot afford the device-wide
- * synchronisation an allocation implies, and hosts whose own allocator owns
- * all device memory.  It computes the same values as cvq_screen_pool for the
- * n_subset pool indices in the host array subset (1 <= n_subset <= 64,
- * EINVAL otherwise) and writes them to grad_dev[0..n_subset), with no
- * workspace: psi is read as complex128, each row of H psi is formed on the
- * fly, and the per-block partial sums live in a fixed device array of 64 x 608
- * doubles (311,296 bytes) that every GPU which loads the library keeps until
- * the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress), so make it before any stream
- * capture.  All calls on a device share the array: calls that overlap on the
- * GPU (different streams without ordering) race and give wrong results.
- * Each call overwrites the array rows it reads, so no clearing is needed.
- * Errors: EINVAL, ECUDA. */
+ * no counterpart to this call.  It exists for code that must not call
+ * cudaMalloc when it screens: latency-critical loops that cannot pay for the
+ * device-wide synchronisation an allocation brings, host applications whose
+ * own caching allocator has reserved all of the device's memory (so an
+ * allocation by this library would fail), and plug-ins that their host hands
+ * fixed buffers and forbids allocating.  It computes the same values as
+ * cvq_screen_pool for the n_subset pool indices in the host array subset
+ * (1 <= n_subset <= 64, EINVAL otherwise) and writes them to
+ * grad_dev[0..n_subset), with no workspace: psi is read as complex128, and
+ * each row of H psi is formed on the fly, once per pass over the sector for
+ * every 8 screened elements (a call costs about ceil(n_subset / 8)
+ * matvecs, against one pass per 8 distinct ladder shifts for
+ * cvq_screen_pool).  The per-block partial sums live in a fixed device array
+ * of 64 x 608 doubles (311,296 bytes) that every GPU which loads the library
+ * keeps until the process exits.  The first call on a device (and the first
+ * after a device reset, which gives the array a new address) looks up that
+ * array's device address with cudaGetSymbolAddress; make that first call
+ * before any stream capture.  All calls on a device share the array: calls
+ * that overlap on the GPU (different streams without ordering) race and give
+ * wrong results.  Each call overwrites the array rows it reads, so no
+ * clearing is needed.  Errors: EINVAL, ECUDA. */
 int cvq_screen_subset_noalloc(const cvq_sector *s, const cvq_pool *p, const cvq_c128 *psi, const int *subset,
                               int n_subset, double *grad_dev, void *stream);
 

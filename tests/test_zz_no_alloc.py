@@ -1,8 +1,10 @@
-"""cvq_screen_subset_noalloc, the screen for callers that cannot allocate device
-memory when they screen (inside a stream capture, in real-time loops, or under
-a host allocator that owns all device memory).  It must give the same values
-as cvq_screen_pool, call after call, although it keeps its partial sums in a
-fixed device array shared by every call instead of a caller workspace.
+"""cvq_screen_subset_noalloc, the screen for callers that cannot allocate
+device memory when they screen: latency-critical loops that cannot pay for the
+synchronisation of a cudaMalloc, host applications whose own allocator has
+reserved all of the device's memory, and plug-ins handed fixed buffers.  It
+must give the Eq. (grad) gradients of the FP64 oracle and the same values as
+cvq_screen_pool, call after call, although it keeps its partial sums in one
+fixed device array that every call shares instead of a caller workspace.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test."""
@@ -17,9 +19,10 @@ G_ABS = 1e-9  # the gradient tolerance of the other parity tests
 
 
 @pytest.mark.parametrize("which", ["bh", "bkc"])
-def test_noalloc_screen_matches_workspace_screen_twice(which):
+def test_noalloc_screen_matches_oracle_and_workspace_screen_twice(which):
     import torch
     assert torch.cuda.is_available()
+    from oracle.core import Sector as OS
     from paper_2606_05297_gb300 import build, cvq
     build.build()
     if which == "bh":
@@ -30,14 +33,19 @@ def test_noalloc_screen_matches_workspace_screen_twice(which):
         pool = W.bkc_kerr_pool(m.L) + [W.Op("rot", 2), W.Op("xkerr", 0, 4)]
     s = cvq.Sector(m)
     p = cvq.Pool(s, pool)
+    os_ = OS(m)
     rng = np.random.default_rng(3)
     for call in range(2):  # two calls in a row: the shared array keeps the previous call's contents
-        psi = torch.from_numpy(W.random_state(s.dim, 20 + call)).cuda()
-        subset = [int(k) for k in rng.choice(len(pool), size=8 + 24 * call, replace=False)]
+        psi_h = W.random_state(s.dim, 20 + call)
+        psi = torch.from_numpy(psi_h).cuda()
+        # 8 elements, then 43 (a ragged last pass of 3), always including the pool's last element
+        subset = [int(k) for k in rng.choice(len(pool), size=8 + 35 * call, replace=False)]
         subset[-1] = len(pool) - 1
-        ref = cvq.screen_pool(s, p, psi, subset=subset).cpu().numpy()
         got = cvq.screen_subset_noalloc(s, p, psi, subset).cpu().numpy()
-        assert got.shape == ref.shape
+        ref = cvq.screen_pool(s, p, psi, subset=subset).cpu().numpy()
+        oracle = os_.screen([pool[k] for k in subset], psi_h)
+        assert got.shape == ref.shape == oracle.shape
+        assert np.max(np.abs(got - oracle)) < G_ABS, (call, np.max(np.abs(got - oracle)))
         assert np.max(np.abs(got - ref)) < G_ABS, (call, np.max(np.abs(got - ref)))
     with pytest.raises(cvq.CvqError, match="n_subset"):
         cvq.screen_subset_noalloc(s, p, psi, list(range(65)))
