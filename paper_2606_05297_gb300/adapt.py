@@ -6,7 +6,7 @@ theta = 0, then re-minimise E(theta) over every parameter with BFGS whose
 energy and gradient come from cvq_energy_and_grad.  Only scalars and vectors
 of length n or K cross the host/device boundary.
 
-Readings of the paper used here (also stated in the design notes):
+Readings of the paper used here, where it is silent:
   * warm start: one HVA layer with angles U[-0.05, 0.05] is optimised first
     (L-inf gradient tolerance 1e-9) and stays in the ansatz, re-optimised with
     every ADAPT parameter (Sec. IV.B, App. C, App. D);

@@ -31,8 +31,37 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// Errors after which the context is unusable (every later CUDA call of the
+// process fails): device-side faults and their relatives.
+static bool sticky_cuda_error(cudaError_t e) {
+  switch (e) {
+    case cudaErrorIllegalAddress:
+    case cudaErrorLaunchFailure:
+    case cudaErrorIllegalInstruction:
+    case cudaErrorMisalignedAddress:
+    case cudaErrorInvalidAddressSpace:
+    case cudaErrorInvalidPc:
+    case cudaErrorHardwareStackError:
+    case cudaErrorAssert:
+    case cudaErrorLaunchTimeout:
+    case cudaErrorECCUncorrectable:
+    case cudaErrorContextIsDestroyed:
+      return true;
+    default:
+      return false;
+  }
+}
+
+extern "C" int cvq_status_from_cuda(int cuda_error) {
+  const cudaError_t e = (cudaError_t)cuda_error;
+  if (e == cudaSuccess) return CVQ_OK;
+  if (e == cudaErrorMemoryAllocation) return CVQ_ENOMEM;
+  return sticky_cuda_error(e) ? CVQ_EDEVICE : CVQ_ECUDA;
+}
+
 static int cuda_fail(cudaError_t e, const char* what) {
-  return fail(CVQ_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  const int code = cvq_status_from_cuda((int)e);
+  return fail(code == CVQ_OK ? CVQ_ECUDA : code, "%s: %s", what, cudaGetErrorString(e));
 }
 
 #define CVQ_CUDA(call, what)                         \

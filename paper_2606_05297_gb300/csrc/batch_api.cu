@@ -42,7 +42,10 @@ int errf(int code, const char* fmt, ...) {
   return internal_fail(code, buf);
 }
 
-int cuda_err(cudaError_t e, const char* what) { return errf(CVQ_ECUDA, "%s: %s", what, cudaGetErrorString(e)); }
+int cuda_err(cudaError_t e, const char* what) {
+  const int code = cvq_status_from_cuda((int)e);
+  return errf(code == CVQ_OK ? CVQ_ECUDA : code, "%s: %s", what, cudaGetErrorString(e));
+}
 
 #define BCUDA(call, what)                             \
   do {                                                \

@@ -249,7 +249,8 @@ struct InitRng {
 int cuda_err(cudaError_t e, const char* what) {
   char buf[256];
   snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
-  return internal_fail(CVQ_ECUDA, buf);
+  const int code = cvq_status_from_cuda((int)e);
+  return internal_fail(code == CVQ_OK ? CVQ_ECUDA : code, buf);
 }
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }

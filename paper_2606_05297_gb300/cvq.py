@@ -94,6 +94,28 @@ def _ptr(t) -> C.c_void_p:
     return C.c_void_p(t.data_ptr())
 
 
+_DTYPE_NAMES = {"c128": "complex128", "f64": "float64", "f32": "float32", "i32": "int32", "u8": "uint8"}
+
+
+def _dev(t, kind: str, n: int, what: str) -> C.c_void_p:
+    """Device pointer of tensor t after checking that the kernels may use it:
+    a contiguous CUDA tensor of dtype `kind` holding at least n elements.
+    Anything else would let a kernel read or write past the buffer."""
+    import torch
+    want = getattr(torch, _DTYPE_NAMES[kind])
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{what}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != want:
+        raise ValueError(f"{what}: dtype {t.dtype}, expected {want}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: must be contiguous")
+    if t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, need at least {n}")
+    if not t.is_cuda:
+        raise ValueError(f"{what}: must be a CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
 class Sector:
     """cvq_sector: the symmetry sector of a lattice model on the current device."""
 
@@ -169,8 +191,10 @@ def apply_H(sector: Sector, psi, sigma=None, energy=None, ws=None, stream=None):
     if sigma is None:
         sigma = torch.empty_like(psi)
     ws, wsb = _ws(sector, None, 0, ws)
-    _check(lib().cvq_apply_H(sector.h, _ptr(psi), _ptr(sigma), _ptr(energy) if energy is not None else None,
-                             _ptr(ws), wsb, _stream(stream)), "cvq_apply_H")
+    d = sector.dim
+    _check(lib().cvq_apply_H(sector.h, _dev(psi, "c128", d, "psi"), _dev(sigma, "c128", d, "sigma"),
+                             _dev(energy, "f64", 1, "energy") if energy is not None else None,
+                             _dev(ws, "u8", 0, "workspace"), wsb, _stream(stream)), "cvq_apply_H")
     return sigma
 
 
@@ -186,7 +210,8 @@ def screen_pool(sector: Sector, pool: Pool, psi, subset=None, out=None, ws=None,
     else:
         sa = (C.c_int * max(n, 1))(*[int(k) for k in subset])
         sp, ns = sa, n
-    _check(lib().cvq_screen_pool(sector.h, pool.h, _ptr(psi), sp, ns, _ptr(out), _ptr(ws), wsb, _stream(stream)),
+    _check(lib().cvq_screen_pool(sector.h, pool.h, _dev(psi, "c128", sector.dim, "psi"), sp, ns,
+                                 _dev(out, "f64", n, "out"), _dev(ws, "u8", 0, "workspace"), wsb, _stream(stream)),
            "cvq_screen_pool")
     return out[:n]
 
@@ -207,8 +232,10 @@ def apply_ansatz(sector: Sector, pool: Pool, op_ids, theta, psi0, out=None, ws=N
     if out is None:
         out = torch.empty_like(psi0)
     ws, wsb = _ws(sector, pool, n, ws)
-    _check(lib().cvq_apply_ansatz(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n, _ptr(psi0),
-                                  _ptr(out), _ptr(ws), wsb, _stream(stream)), "cvq_apply_ansatz")
+    d = sector.dim
+    _check(lib().cvq_apply_ansatz(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                  _dev(psi0, "c128", d, "psi0"), _dev(out, "c128", d, "out"),
+                                  _dev(ws, "u8", 0, "workspace"), wsb, _stream(stream)), "cvq_apply_ansatz")
     return out
 
 
@@ -221,16 +248,22 @@ def energy_and_grad(sector: Sector, pool: Pool, op_ids, theta, psi0, E=None, gra
     if grad is None:
         grad = torch.empty(max(n, 1), dtype=torch.float64, device=psi0.device)
     ws, wsb = _ws(sector, pool, n, ws)
-    _check(lib().cvq_energy_and_grad(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n, _ptr(psi0),
-                                     _ptr(E), _ptr(grad), _ptr(ws), wsb, _stream(stream)), "cvq_energy_and_grad")
+    _check(lib().cvq_energy_and_grad(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                     _dev(psi0, "c128", sector.dim, "psi0"), _dev(E, "f64", 1, "E"),
+                                     _dev(grad, "f64", n, "grad"), _dev(ws, "u8", 0, "workspace"), wsb,
+                                     _stream(stream)), "cvq_energy_and_grad")
     return E, grad[:n]
 
 
 def lanczos_step(sector: Sector, v_prev, v, w, v_next, alpha, beta_prev, beta, ws=None, stream=None):
     """w <- w - alpha v - beta_prev v_prev; beta = ||w||; v_next = w / beta (all on the device)."""
     ws, wsb = _ws(sector, None, 0, ws)
-    _check(lib().cvq_lanczos_step(sector.h, _ptr(v_prev), _ptr(v), _ptr(w), _ptr(v_next), _ptr(alpha),
-                                  _ptr(beta_prev), _ptr(beta), _ptr(ws), wsb, _stream(stream)), "cvq_lanczos_step")
+    d = sector.dim
+    _check(lib().cvq_lanczos_step(sector.h, _dev(v_prev, "c128", d, "v_prev"), _dev(v, "c128", d, "v"),
+                                  _dev(w, "c128", d, "w"), _dev(v_next, "c128", d, "v_next"),
+                                  _dev(alpha, "f64", 1, "alpha"), _dev(beta_prev, "f64", 1, "beta_prev"),
+                                  _dev(beta, "f64", 1, "beta"), _dev(ws, "u8", 0, "workspace"), wsb,
+                                  _stream(stream)), "cvq_lanczos_step")
 
 
 def op_cost(sector: Sector, pool: Pool, op: int):
@@ -272,14 +305,16 @@ def profile_stop():
 def screen_subset_noalloc(sector: Sector, pool: Pool, psi, subset, out=None, stream=None):
     """Eq. (grad) gradients of at most 64 pool elements without any workspace
     or device allocation inside the call (cvq_screen_subset_noalloc): for
-    callers that cannot allocate at that point, e.g. inside a stream capture.
-    `out` must be preallocated by such callers; calls overlapping on the GPU race."""
+    callers that cannot allocate at that point (latency-critical loops, hosts
+    whose allocator owns all device memory).  Such callers pass a preallocated
+    `out`; calls that overlap on the GPU race on the library's shared array."""
     import torch
     n = len(subset)
     if out is None:
         out = torch.empty(max(n, 1), dtype=torch.float64, device=psi.device)
     sa = (C.c_int * max(n, 1))(*[int(k) for k in subset])
-    _check(lib().cvq_screen_subset_noalloc(sector.h, pool.h, _ptr(psi), sa, n, _ptr(out), _stream(stream)),
+    _check(lib().cvq_screen_subset_noalloc(sector.h, pool.h, _dev(psi, "c128", sector.dim, "psi"), sa, n,
+                                           _dev(out, "f64", n, "out"), _stream(stream)),
            "cvq_screen_subset_noalloc")
     return out[:n]
 
@@ -300,7 +335,8 @@ def features(sector: Sector, psi, pairs=(), out=None, stream=None):
         out = torch.empty(2 * L + 2 * npairs, dtype=torch.float64, device=psi.device)
     pi = (C.c_int * max(npairs, 1))(*[int(p[0]) for p in pairs])
     pj = (C.c_int * max(npairs, 1))(*[int(p[1]) for p in pairs])
-    _check(lib().cvq_features(sector.h, _ptr(psi), pi, pj, npairs, _ptr(out), _ptr(ws), C.c_size_t(ws.numel()),
+    _check(lib().cvq_features(sector.h, _dev(psi, "c128", sector.dim, "psi"), pi, pj, npairs,
+                              _dev(out, "f64", 2 * L + 2 * npairs, "out"), _ptr(ws), C.c_size_t(ws.numel()),
                               _stream(stream)), "cvq_features")
     return out
 
@@ -340,15 +376,21 @@ class Scorer:
 
     def forward(self, X, out=None, stream=None):
         import torch
-        assert X.dtype == torch.float32 and X.is_contiguous() and X.shape[-1] == MLP_IN
+        if X.dim() != 2 or X.shape[-1] != MLP_IN:
+            raise ValueError(f"X: expected shape (rows, {MLP_IN}), got {tuple(X.shape)}")
+        rows = int(X.shape[0])
         if out is None:
-            out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
-        _check(lib().cvq_mlp_forward(self.h, _ptr(X), int(X.shape[0]), _ptr(out), _stream(stream)), "cvq_mlp_forward")
+            out = torch.empty(rows, dtype=torch.float32, device=X.device)
+        _check(lib().cvq_mlp_forward(self.h, _dev(X, "f32", rows * MLP_IN, "X"), rows, _dev(out, "f32", rows, "out"),
+                                     _stream(stream)), "cvq_mlp_forward")
         return out
 
     def backward(self, X, dscores, stream=None):
-        _check(lib().cvq_mlp_backward(self.h, _ptr(X), int(X.shape[0]), _ptr(dscores), _stream(stream)),
-               "cvq_mlp_backward")
+        if X.dim() != 2 or X.shape[-1] != MLP_IN:
+            raise ValueError(f"X: expected shape (rows, {MLP_IN}), got {tuple(X.shape)}")
+        rows = int(X.shape[0])
+        _check(lib().cvq_mlp_backward(self.h, _dev(X, "f32", rows * MLP_IN, "X"), rows,
+                                      _dev(dscores, "f32", rows, "dscores"), _stream(stream)), "cvq_mlp_backward")
 
     def adam_step(self, lr: float, stream=None):
         self.t += 1
@@ -375,8 +417,10 @@ def listwise_loss(scores, targets, list_off, dscores=None, loss=None, stream=Non
         dscores = torch.empty_like(scores)
     if loss is None:
         loss = torch.empty(max(n, 0), dtype=torch.float32, device=scores.device)
-    _check(L.cvq_mlp_listwise_loss(_ptr(scores), _ptr(targets), _ptr(list_off), n, _ptr(dscores), _ptr(loss),
-                                   _stream(stream)), "cvq_mlp_listwise_loss")
+    rows = int(scores.numel())
+    _check(L.cvq_mlp_listwise_loss(_dev(scores, "f32", rows, "scores"), _dev(targets, "f32", rows, "targets"),
+                                   _dev(list_off, "i32", n + 1, "list_off"), n, _dev(dscores, "f32", rows, "dscores"),
+                                   _dev(loss, "f32", max(n, 0), "loss"), _stream(stream)), "cvq_mlp_listwise_loss")
     return loss, dscores
 
 
@@ -424,7 +468,8 @@ class Batch:
         flat = [int(k) for ids in op_ids if ids is not None for k in ids]
         na = (C.c_int * self.n)(*n_ops)
         ia = (C.c_int * max(1, len(flat)))(*flat)
-        pa = (C.c_void_p * self.n)(*[(p.data_ptr() if p is not None else 0) for p in psi0])
+        pa = (C.c_void_p * self.n)(*[(_dev(p, "c128", s.dim, f"psi0[{i}]").value if p is not None else 0)
+                                     for i, (p, s) in enumerate(zip(psi0, self._keep[0]))])
         self._psi0 = list(psi0)
         _check(lib().cvq_batch_set_ansatz(self.h, na, ia, pa), "cvq_batch_set_ansatz")
         self.n_ops = n_ops
@@ -445,8 +490,10 @@ class Batch:
         Returns the device tensors (E[n], grad[packed])."""
         if theta is not None:
             self.theta[: theta.numel()].copy_(theta)
-        _check(lib().cvq_batch_energy_and_grad(self.h, _ptr(self.theta), _ptr(self.E), _ptr(self.grad),
-                                               _stream(stream)), "cvq_batch_energy_and_grad")
+        _check(lib().cvq_batch_energy_and_grad(self.h, _dev(self.theta, "f64", self.offsets[-1], "theta"),
+                                               _dev(self.E, "f64", self.n, "E"),
+                                               _dev(self.grad, "f64", self.offsets[-1], "grad"), _stream(stream)),
+               "cvq_batch_energy_and_grad")
         return self.E, self.grad[: self.offsets[-1]]
 
     def info(self):
@@ -475,9 +522,11 @@ def energy_and_grad_ckpt(sector: Sector, pool: Pool, op_ids, theta, psi0, every:
     _check(L.cvq_checkpoint_bytes(sector.h, n, int(every), C.byref(need)), "cvq_checkpoint_bytes")
     if ckpt is None:
         ckpt = torch.empty(max(int(need.value), 1), dtype=torch.uint8, device=psi0.device)
-    _check(L.cvq_energy_and_grad_ckpt(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n, _ptr(psi0),
-                                      _ptr(E), _ptr(grad), int(every), _ptr(ckpt), ckpt.numel(), _ptr(ws), wsb,
-                                      _stream(stream)), "cvq_energy_and_grad_ckpt")
+    _check(L.cvq_energy_and_grad_ckpt(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                      _dev(psi0, "c128", sector.dim, "psi0"), _dev(E, "f64", 1, "E"),
+                                      _dev(grad, "f64", n, "grad"), int(every), _dev(ckpt, "u8", 0, "ckpt"),
+                                      ckpt.numel(), _dev(ws, "u8", 0, "workspace"), wsb, _stream(stream)),
+           "cvq_energy_and_grad_ckpt")
     return E, grad[:n]
 
 
@@ -526,9 +575,12 @@ def apply_ansatz_projected(sector: Sector, pool: ProjectedPool, op_ids, theta, p
         out = torch.empty_like(psi0)
     ws, wsb = _ws(sector, pool, n, ws)
     states = _proj_states(sector, pool, ids, n, states, psi0.device)
+    d = sector.dim
     _check(lib().cvq_apply_ansatz_projected(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n,
-                                            _ptr(psi0), _ptr(out), _ptr(states), states.numel(), _ptr(ws), wsb,
-                                            _stream(stream)), "cvq_apply_ansatz_projected")
+                                            _dev(psi0, "c128", d, "psi0"), _dev(out, "c128", d, "out"),
+                                            _dev(states, "u8", 0, "states"), states.numel(),
+                                            _dev(ws, "u8", 0, "workspace"), wsb, _stream(stream)),
+           "cvq_apply_ansatz_projected")
     return out
 
 
@@ -544,6 +596,8 @@ def energy_and_grad_projected(sector: Sector, pool: ProjectedPool, op_ids, theta
     ws, wsb = _ws(sector, pool, n, ws)
     states = _proj_states(sector, pool, ids, n, states, psi0.device)
     _check(lib().cvq_energy_and_grad_projected(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n,
-                                               _ptr(psi0), _ptr(E), _ptr(grad), _ptr(states), states.numel(),
-                                               _ptr(ws), wsb, _stream(stream)), "cvq_energy_and_grad_projected")
+                                               _dev(psi0, "c128", sector.dim, "psi0"), _dev(E, "f64", 1, "E"),
+                                               _dev(grad, "f64", n, "grad"), _dev(states, "u8", 0, "states"),
+                                               states.numel(), _dev(ws, "u8", 0, "workspace"), wsb,
+                                               _stream(stream)), "cvq_energy_and_grad_projected")
     return E, grad[:n]

@@ -50,3 +50,18 @@ def test_oracle_shares_no_code_with_cuda_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "from oracle" not in src and "import oracle" not in src, f
+
+
+def test_status_of_cuda_errors():
+    """CUDA errors that leave the context unusable map to CVQ_EDEVICE (5), an
+    allocation failure to CVQ_ENOMEM (2), everything else to CVQ_ECUDA (3);
+    host only, no device needed.  Values are cudaError_t codes of CUDA 13."""
+    from paper_2606_05297_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    f = lib.cvq_status_from_cuda
+    f.argtypes, f.restype = [ctypes.c_int], ctypes.c_int
+    assert f(0) == 0                      # cudaSuccess
+    assert f(1) == 3                      # cudaErrorInvalidValue
+    assert f(2) == 2                      # cudaErrorMemoryAllocation
+    for code in (700, 710, 715, 716, 719, 214):  # illegal address, assert, illegal instruction, misaligned, launch failure, ECC
+        assert f(code) == 5, code
