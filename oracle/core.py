@@ -39,8 +39,20 @@ def lib():
         L.orc_screen.argtypes = [vp, vp, C.c_int, C.POINTER(vp), vp, dp, dp]
         L.orc_apply_ansatz.argtypes = [vp, C.c_int, C.POINTER(vp), dp, vp, vp]
         L.orc_energy_and_grad.argtypes = [vp, vp, C.c_int, C.POINTER(vp), dp, vp, dp, dp]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = None
+        L.orc_max_threads.restype = C.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (OpenMP)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
 
 
 def _ptr(a: np.ndarray):

@@ -35,6 +35,9 @@
  * numpy complex128 memory.
  */
 #include <complex.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -443,4 +446,21 @@ void orc_dot(const cplx *a, const cplx *b, int64_t dim, double *re, double *im) 
     cplx z = vec_dot(a, b, dim);
     *re = creal(z);
     *im = cimag(z);
+}
+
+/* Threads used by the parallel loops (the CPU baseline times 1 and all). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
