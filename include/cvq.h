@@ -320,6 +320,28 @@ int cvq_batch_energy_and_grad(cvq_batch *b, const double *theta_dev, double *E_d
 int cvq_batch_set_active(cvq_batch *b, const int *active, void *stream);
 int cvq_batch_info(const cvq_batch *b, int *kernels_per_eval, int *items, int *layers, int64_t *n_params);
 
+/* Batched pool screen, Eq. (grad) (the selection step of Sec. IV.B for every
+ * instance of the batch at once): for every active instance i with an
+ * ansatz, psi_i = U_i(theta_i) psi0_i is formed from the instance's ansatz
+ * (cvq_batch_set_ansatz) at theta_dev (packed like the op ids), and
+ *   grad_dev[o_i + k] = <psi_i|[H_i, A_{s_i[k]}]|psi_i>
+ * for the pool indices s_i: every pool element 0..K_i-1 when subset_off is
+ * NULL, else subset[subset_off[i] .. subset_off[i+1]) (host arrays;
+ * subset_off has n_inst + 1 nondecreasing entries from 0).  The outputs are
+ * packed instance after instance: o_i is the number of outputs of the
+ * instances before i, instances without an ansatz (n_ops = -1) having none.
+ * Inactive instances (cvq_batch_set_active) are not written.  Per instance
+ * the screen shares one neighbour read among all elements with the same
+ * ladder shift, and every partial sum has its own slot, summed in a fixed
+ * order: results are deterministic.  The first call for an ansatz structure,
+ * schedule, subset list or pair of buffer pointers builds a plan (allocates,
+ * synchronises) and captures it in a CUDA graph; later calls launch the
+ * graph on `stream`.  Calls on one batch (screens and evaluations) must be
+ * ordered: they share the batch's state buffers.  Errors: EINVAL (sizes,
+ * indices outside a pool), ENOMEM, ECUDA. */
+int cvq_batch_screen(cvq_batch *b, const double *theta_dev, const int *subset_off, const int *subset, double *grad_dev,
+                     void *stream);
+
 /* Pool screen for callers that cannot allocate device memory.  The paper has
  * no counterpart to this call.  It exists for code that must not call
  * cudaMalloc when it screens: latency-critical loops that cannot pay for the

@@ -66,7 +66,7 @@ class BatchedAdapt:
 
     def __init__(self, models: Sequence[Model], pool_ops: Sequence[Sequence[Op]], init_occ: Sequence[Sequence[int]],
                  warm_ops: Sequence[Sequence[Op]] = None, warm_theta: Sequence[Sequence[float]] = None,
-                 n_max: int = 160, tune: bool = True):
+                 n_max: int = 160, tune: bool = True, hessian_recycling: bool = False):
         import torch
         self.torch = torch
         n = len(models)
@@ -81,7 +81,6 @@ class BatchedAdapt:
         self.theta = [np.array(t, dtype=np.float64) for t in warm_theta]
         self.n_max = n_max
         self.batch = cvq.Batch(self.sectors, self.pools, n_max)
-        self.ws = [s.workspace(p, n_max) for s, p in zip(self.sectors, self.pools)]
         self.done = [False] * n
         self.trace: List[list] = [[] for _ in range(n)]
         self.rounds = 0
@@ -89,11 +88,19 @@ class BatchedAdapt:
         self.tune = tune
         self.tuned = None
         self._host = torch.empty(n * n_max + n, dtype=torch.float64, pin_memory=True)
+        self.batch_ready = False
+        self.screens = 0
+        self._gout = None
+        # App. D: each BFGS starts from the instance's previous inverse Hessian,
+        # extended by an identity row and column for the new parameter
+        self.hessian_recycling = hessian_recycling
+        self.Hinv: List[Optional[np.ndarray]] = [None] * n
 
     # ---------------------------------------------------------------- evaluations
 
     def _structure(self):
         self.batch.set_ansatz([None if self.done[i] else self.ids[i] for i in range(len(self.ids))], self.psi0)
+        self.batch_ready = True
         if self.tune and self.tuned is None:
             self._load_theta({i: self.theta[i] for i in range(len(self.ids)) if not self.done[i]})
             self.tuned = autotune(self.batch, self.sectors)
@@ -137,36 +144,76 @@ class BatchedAdapt:
                 for i in range(len(self.ids)) if len(self.ids[i])}
         for i, r in self.lockstep(gens).items():
             self.theta[i] = r.x
+            self.Hinv[i] = r.Hinv
             self.trace[i].append(dict(kind="warm", E=r.f, nfev=r.nfev, nit=r.nit, status=r.status))
 
-    def step(self, grad_tol: float = 1e-6, max_iter: int = 1000):
-        """One ADAPT iteration on every instance that has not converged.
-        Returns the number of instances that grew."""
-        grown = {}
-        for i in range(len(self.ids)):
-            if self.done[i]:
-                continue
-            psi = cvq.apply_ansatz(self.sectors[i], self.pools[i], self.ids[i], self.theta[i], self.psi0[i],
-                                   ws=self.ws[i])
-            g = cvq.screen_pool(self.sectors[i], self.pools[i], psi, subset=list(range(self.K[i])),
-                                ws=self.ws[i])[: self.K[i]].cpu().numpy()
+    def screen_all(self, subsets=None):
+        """Eq. (grad) on the current state of every instance that has not
+        converged, all in one batched launch (cvq_batch_screen): the pool
+        operators of subsets[i] (default: the whole pool without the warm-start
+        gates).  Returns {instance: host gradient vector}."""
+        n = len(self.ids)
+        if not self.batch_ready:
+            self._structure()
+        live = [i for i in range(n) if not self.done[i]]
+        self.batch.set_active([not self.done[i] for i in range(n)])
+        self._load_theta({i: self.theta[i] for i in live})
+        subs = [(list(range(self.K[i])) if subsets is None else list(subsets[i])) if not self.done[i] else []
+                for i in range(n)]
+        need = sum(len(q) for q in subs)
+        if self._gout is None or self._gout.numel() < max(need, 1):
+            self._gout = self.torch.empty(max(sum(self.K), 1), dtype=self.torch.float64, device="cuda")
+        out, off = self.batch.screen(subs, out=self._gout)
+        h = out[: max(off[-1], 1)].cpu().numpy()
+        self.screens += 1
+        return {i: h[off[i]:off[i + 1]].copy() for i in live}
+
+    def choose(self, grad_tol: float):
+        """The operator each live instance appends: {instance: (pool index, |g|)}
+        (plain rule: largest exact gradient of a full screen).  Instances whose
+        largest |g| is below grad_tol are marked done."""
+        chosen = {}
+        gs = self.screen_all()
+        for i, g in gs.items():
             k, gmax = select(g)
             if gmax < grad_tol or len(self.ids[i]) + 1 > self.n_max:
                 self.done[i] = True
                 continue
+            chosen[i] = (k, gmax)
+        return chosen
+
+    def step(self, grad_tol: float = 1e-6, max_iter: int = 1000, stop=None):
+        """One ADAPT iteration on every instance that has not converged (nor
+        been stopped: stop[i] True leaves instance i out for good).
+        Returns the number of instances that grew."""
+        if stop is not None:
+            for i, st in enumerate(stop):
+                if st:
+                    self.done[i] = True
+        grown = self.choose(grad_tol)
+        for i, (k, _) in grown.items():
             self.ids[i].append(k)
             self.theta[i] = np.append(self.theta[i], 0.0)
-            grown[i] = (k, gmax)
         if not grown:
             return 0
         self._structure()
-        gens = {i: BFGS(None).steps(self.theta[i], gtol=min(1e-6, gm * 1e-5), max_iter=max_iter)
-                for i, (_, gm) in grown.items()}
+        gens = {}
+        for i, (_, gm) in grown.items():
+            H0 = None
+            if self.hessian_recycling and self.Hinv[i] is not None:
+                H0 = np.eye(self.theta[i].size)
+                H0[:-1, :-1] = self.Hinv[i]
+            gens[i] = BFGS(None).steps(self.theta[i], gtol=min(1e-6, gm * 1e-5), max_iter=max_iter, Hinv0=H0)
         for i, r in self.lockstep(gens).items():
             self.theta[i] = r.x
+            self.Hinv[i] = r.Hinv
             self.trace[i].append(dict(kind="adapt", op=grown[i][0], gmax=grown[i][1], E=r.f, nfev=r.nfev, nit=r.nit,
                                       status=r.status, n=len(self.ids[i])))
+        self.after_step(grown)
         return len(grown)
+
+    def after_step(self, grown):
+        """Hook for drivers that keep per-iteration state (the learned proposal)."""
 
 
 def c4_batch_inputs(seed: int = 0, count: int = 64, extra_ops: int = 8):

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libcvq.so")
 SOURCES = ["api.cu", "k_gates.cu", "k_hamiltonian.cu", "k_gate_bh_fwd.cu", "k_gate_bh_adj.cu", "k_gate_bkc_fwd.cu",
-           "k_gate_bkc_adj.cu", "k_noalloc.cu", "k_features.cu", "k_mlp.cu", "k_batch.cu", "batch_api.cu", "k_projected.cu"]
+           "k_gate_bkc_adj.cu", "k_noalloc.cu", "k_features.cu", "k_mlp.cu", "k_batch.cu", "batch_api.cu", "k_projected.cu",
+           "k_tile.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

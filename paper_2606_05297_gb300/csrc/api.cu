@@ -204,6 +204,8 @@ struct cvq_pool {
   int ustride = PHASE_TABLE;     // complex entries per gate in a call's U buffer
   std::vector<int> blk_size;     // host copy of every block's size (costs)
   int dc = 0;                    // > 0: projected gates with this inner cutoff
+  void* tile_blob = nullptr;     // index tables of the tiled gates (one per distinct gate structure)
+  std::vector<TileMap> op_tiles; // per pool element (empty map for diagonal generators)
 };
 
 static int64_t binom(int n, int k) {
@@ -272,6 +274,7 @@ extern "C" int cvq_init_sector(const cvq_model* m, cvq_sector** out) {
     }
   }
   if (!rc && S.dim > ((int64_t)1 << 40)) rc = fail(CVQ_EINVAL, "sector dimension above 2^40");
+  if (!rc) set_bkc_div(S);
   if (rc) {
     delete s;
     return rc;
@@ -578,6 +581,109 @@ static int build_type(const SectorDev& S, int type, int phase, PoolBuild& pb, Ty
 
 static int set_pool(const cvq_sector* s, const cvq_op* ops, int K, int dc, cvq_pool** out);
 
+// Index tables of the tiled gates (k_tile.cu): one per distinct gate
+// structure (modes, move) of the pool's block generators.  Each region is one
+// block class of two or more members; its blocks are the class's orbits, in
+// orbit order, packed TILE_T / b to a tile.  Synchronises.
+static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
+  const SectorDev& S = p->sec->S;
+  struct Plan {
+    int type, i, j;
+    std::vector<TileRegion> reg;
+    int64_t ntiles = 0, max_count = 0;
+    size_t idx_off = 0, reg_off = 0;
+  };
+  std::vector<Plan> plans;
+  std::map<std::array<int, 7>, int> where;
+  const int slots = (S.dim >= TILE_LARGE_DIM) ? TILE_S_LARGE : 1;
+  const int T = TILE_T * slots;
+  std::vector<int> plan_of(p->K, -1);
+  auto orbits = [&](const TypeDesc& t, int cls) -> int64_t {
+    if (S.kind == CVQ_BH) return S.bh2_off[cls + 1] - S.bh2_off[cls];
+    const int nm = t.single ? 1 : 2;
+    if (S.L == nm) return cls == S.parity ? 1 : 0;
+    int64_t items = 1;
+    for (int r = 0; r < S.L - nm; ++r) items *= S.D;
+    return items / 2;
+  };
+  for (int k = 0; k < p->K; ++k) {
+    const TypeDesc& t = p->types[p->op_type[k]];
+    if (t.diag) continue;
+    const std::array<int, 7> key = {p->op_i[k], p->op_j[k], t.di, t.dj, t.single, t.nblocks, t.nu};
+    auto it = where.find(key);
+    if (it != where.end()) {
+      plan_of[k] = it->second;
+      continue;
+    }
+    Plan pl;
+    pl.type = p->op_type[k];
+    pl.i = p->op_i[k];
+    pl.j = p->op_j[k];
+    for (int cls = 0; cls < t.nclass; ++cls)
+      for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
+        const BlockDesc& bd = pb.blk[t.blk_base + bi];
+        if (bd.size < 2) continue;  // zero generator: identity
+        const int64_t cnt = orbits(t, cls);
+        if (cnt <= 0) continue;
+        if (cnt > INT32_MAX) return fail(CVQ_EINVAL, "too many orbits in one class for the tiled gates");
+        TileRegion R;
+        memset(&R, 0, sizeof R);
+        R.b = bd.size;
+        R.nbt = T / bd.size;
+        R.count = (int)cnt;
+        R.u_off = bd.u_off;
+        R.f_off = bd.f_off;
+        R.bi = bi;
+        R.cls = cls;
+        R.tile0 = pl.ntiles;
+        pl.ntiles += (cnt + R.nbt - 1) / R.nbt;
+        pl.max_count = std::max(pl.max_count, cnt);
+        pl.reg.push_back(R);
+      }
+    where[key] = (int)plans.size();
+    plan_of[k] = (int)plans.size();
+    plans.push_back(std::move(pl));
+  }
+  p->op_tiles.assign(p->K, TileMap{nullptr, nullptr, 0, 0, 0});
+  auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t total = 0;
+  for (auto& pl : plans) {
+    pl.idx_off = total;
+    total = a256(total + (size_t)pl.ntiles * T * sizeof(int));
+    pl.reg_off = total;
+    total = a256(total + pl.reg.size() * sizeof(TileRegion));
+  }
+  if (total == 0) return CVQ_OK;
+  const size_t o_bad = total;  // count of member indices outside [0, dim) (must stay 0)
+  total += 256;
+  cudaError_t e = cudaMalloc(&p->tile_blob, total);
+  if (e != cudaSuccess) return fail(CVQ_ENOMEM, "cudaMalloc(%zu) for the gate tables: %s", total, cudaGetErrorString(e));
+  char* base = (char*)p->tile_blob;
+  int* bad = (int*)(base + o_bad);
+  if ((e = cudaMemset(bad, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "gate table build");
+  for (auto& pl : plans) {
+    int* idx = (int*)(base + pl.idx_off);
+    TileRegion* reg = (TileRegion*)(base + pl.reg_off);
+    if ((e = cudaMemset(idx, 0xFF, (size_t)pl.ntiles * T * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemcpy(reg, pl.reg.data(), pl.reg.size() * sizeof(TileRegion), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = launch_tile_build(S, pl.i, pl.j, p->types[pl.type], p->P, reg, (int)pl.reg.size(), pl.max_count, slots,
+                               idx, bad, 0)) != cudaSuccess)
+      return cuda_fail(e, "gate table build");
+  }
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "gate table build");
+  int nbad = 0;
+  if ((e = cudaMemcpy(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "gate table build");
+  if (nbad) return fail(CVQ_EINVAL, "gate table build produced %d indices outside the sector", nbad);
+  for (int k = 0; k < p->K; ++k) {
+    if (plan_of[k] < 0) continue;
+    const Plan& pl = plans[plan_of[k]];
+    p->op_tiles[k] = TileMap{(const int*)(base + pl.idx_off), (const TileRegion*)(base + pl.reg_off),
+                             (int)pl.reg.size(), slots, pl.ntiles};
+  }
+  return CVQ_OK;
+}
+
 extern "C" int cvq_set_pool(const cvq_sector* s, const cvq_op* ops, int K, cvq_pool** out) {
   return set_pool(s, ops, K, 0, out);
 }
@@ -677,6 +783,16 @@ static int set_pool(const cvq_sector* s, const cvq_op* ops, int K, int dc, cvq_p
     delete p;
     return cuda_fail(e, "pool upload");
   }
+  // Tiled gates need int32 sector indices; projected pools keep the orbit
+  // kernels.  The tables are built from the pool tables uploaded above.
+  if (dc == 0 && S.dim <= (int64_t)INT32_MAX) {
+    if (int rc = build_tiles(p, pb)) {
+      if (p->tile_blob) cudaFree(p->tile_blob);
+      cudaFree(p->blob);
+      delete p;
+      return rc;
+    }
+  }
   *out = p;
   return CVQ_OK;
 }
@@ -684,6 +800,7 @@ static int set_pool(const cvq_sector* s, const cvq_op* ops, int K, int dc, cvq_p
 extern "C" void cvq_destroy_pool(cvq_pool* p) {
   if (!p) return;
   if (p->blob) cudaFree(p->blob);
+  if (p->tile_blob) cudaFree(p->tile_blob);
   delete p;
 }
 
@@ -861,25 +978,10 @@ extern "C" int cvq_apply_H(const cvq_sector* s, const cvq_c128* psi, cvq_c128* s
   return CVQ_OK;
 }
 
-extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq_c128* psi, const int* subset,
-                               int n_subset, double* grad_dev, void* ws, size_t wsb, void* stream) {
-  if (!s || !p || !psi || !grad_dev) return fail(CVQ_EINVAL, "null argument");
-  if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
-  SubsetArg sub;
-  if (subset) {
-    if (n_subset < 0 || n_subset > p->K) return fail(CVQ_EINVAL, "n_subset %d outside [0, K=%d]", n_subset, p->K);
-    for (int k = 0; k < n_subset; ++k) {
-      if (subset[k] < 0 || subset[k] >= p->K) return fail(CVQ_EINVAL, "subset[%d] = %d outside the pool", k, subset[k]);
-      sub.idx[k] = subset[k];
-    }
-    sub.n = n_subset;
-  } else {
-    sub.n = p->K;
-    for (int k = 0; k < p->K; ++k) sub.idx[k] = k;
-  }
-  // distinct shifts (canonical: lower mode first) and diagonal functions
-  static thread_local ScreenArg sa;
-  static thread_local ScreenMap sm;
+// The screen of the pool indices in sub: its distinct ladder shifts
+// (canonical: lower mode first) and diagonal functions, and per screened
+// element the rows of Z it combines.
+static int screen_plan(const cvq_pool* p, const SubsetArg& sub, ScreenArg& sa, ScreenMap& sm) {
   sa.nsh = sa.ndg = 0;
   sm.n = sub.n;
   std::map<std::array<int, 4>, int> shift_id, diag_id;
@@ -919,6 +1021,34 @@ extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq
       sm.e[k] = make_int4(0, sp, sn, 0);
     }
   }
+  return CVQ_OK;
+}
+
+// Checked subset (NULL: the whole pool) into sub.
+static int screen_subset(const cvq_pool* p, const int* subset, int n_subset, SubsetArg& sub) {
+  if (subset) {
+    if (n_subset < 0 || n_subset > p->K) return fail(CVQ_EINVAL, "n_subset %d outside [0, K=%d]", n_subset, p->K);
+    for (int k = 0; k < n_subset; ++k) {
+      if (subset[k] < 0 || subset[k] >= p->K) return fail(CVQ_EINVAL, "subset[%d] = %d outside the pool", k, subset[k]);
+      sub.idx[k] = subset[k];
+    }
+    sub.n = n_subset;
+  } else {
+    sub.n = p->K;
+    for (int k = 0; k < p->K; ++k) sub.idx[k] = k;
+  }
+  return CVQ_OK;
+}
+
+extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq_c128* psi, const int* subset,
+                               int n_subset, double* grad_dev, void* ws, size_t wsb, void* stream) {
+  if (!s || !p || !psi || !grad_dev) return fail(CVQ_EINVAL, "null argument");
+  if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
+  SubsetArg sub;
+  if (int rc = screen_subset(p, subset, n_subset, sub)) return rc;
+  static thread_local ScreenArg sa;
+  static thread_local ScreenMap sm;
+  if (int rc = screen_plan(p, sub, sa, sm)) return rc;
   Layout l;
   if (int rc = check_ws(s, p, 0, ws, wsb, l)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -972,6 +1102,7 @@ static GateArg gate_arg(const cvq_pool* p, int op, const cdf* U) {
   g.j = p->op_j[op];
   g.t = p->types[p->op_type[op]];
   g.U = U;
+  g.tm = p->op_tiles.empty() ? TileMap{nullptr, nullptr, 0, 0, 0} : p->op_tiles[op];
   return g;
 }
 
@@ -1044,6 +1175,12 @@ static void diag_run_arg(const cvq_sector* s, const cvq_pool* p, const int* ids,
   }
   for (int r = 0; r < LMAX; ++r)
     for (int nn = 0; nn < DMAX; ++nn) a.T[r][nn] = cdf_of(std::cos(ang[r][nn]), std::sin(ang[r][nn]));
+  bool on[LMAX] = {};
+  for (int q = 0; q < g.m; ++q)
+    if (a.diag[q] != 4) on[a.gi[q]] = true;
+  a.nact = 0;
+  for (int r = 0; r < s->S.L; ++r)
+    if (on[r]) a.act[a.nact++] = r;
 }
 
 // Checkpointed forward states: before the first segment whose first gate index
@@ -1390,6 +1527,14 @@ const GateArg* internal_pool_ops(const cvq_pool* p, const cvq_sector** sec, int*
 }
 
 int internal_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
+// The screen plan of a pool subset (NULL: the whole pool), for the batched screen.
+int internal_screen_plan(const cvq_pool* p, const int* subset, int n_subset, ScreenArg* sa, ScreenMap* sm) {
+  if (!p || !sa || !sm) return fail(CVQ_EINVAL, "null argument");
+  SubsetArg sub;
+  if (int rc = screen_subset(p, subset, n_subset, sub)) return rc;
+  return screen_plan(p, sub, *sa, *sm);
+}
 
 // Host-side view of a pool for the batched engine.
 int internal_pool_host(const cvq_pool* p, const cvq_sector** sec, const TypeDesc** types, int* ntypes,

@@ -18,6 +18,7 @@ int internal_sector_device(const cvq_sector* s);
 int internal_pool_host(const cvq_pool* p, const cvq_sector** sec, const TypeDesc** types, int* ntypes,
                        const int** op_type, const int** op_i, const int** op_j, int* K, PoolDev* P, int* ustride,
                        const GateArg** ops_dev);
+int internal_screen_plan(const cvq_pool* p, const int* subset, int n_subset, ScreenArg* sa, ScreenMap* sm);
 }  // namespace cvq
 
 using namespace cvq;
@@ -91,6 +92,23 @@ struct cvq_batch {
   cudaGraphExec_t exec = nullptr;
   const double* g_theta = nullptr;
   double *g_E = nullptr, *g_grad = nullptr;
+  // batched screen: its own plan and graph (forward layers of the evaluation
+  // plan, then the screen layer, the reduction into z and the epilogue)
+  std::vector<const cvq_pool*> pools;
+  void* splan = nullptr;
+  cudaGraphExec_t sexec = nullptr;
+  bool s_valid = false;           // the screen plan matches the current ansatz structure and schedule
+  std::vector<int> s_key;         // the subsets it was built for
+  const double* s_theta = nullptr;
+  double* s_grad = nullptr;
+  int* s_counters = nullptr;
+  BScreen* s_screens = nullptr;
+  int4* s_desc = nullptr;
+  BItem* s_items = nullptr;
+  BRed* s_red = nullptr;
+  BScreenOut* s_outs = nullptr;
+  double *s_partial = nullptr, *s_z = nullptr;
+  int s_nitems = 0, s_nred = 0, s_nouts = 0;
 };
 
 namespace {
@@ -98,6 +116,14 @@ namespace {
 void drop_graph(cvq_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = nullptr;
+}
+
+void drop_screen(cvq_batch* b) {
+  if (b->sexec) cudaGraphExecDestroy(b->sexec);
+  b->sexec = nullptr;
+  if (b->splan) cudaFree(b->splan);
+  b->splan = nullptr;
+  b->s_valid = false;
 }
 
 // The segments of one instance: a block gate alone, or a run of consecutive
@@ -133,6 +159,11 @@ std::vector<BSeg> segments_of(const PoolView& p, int inst, const int* ids, int n
       s.gj[s.m] = p.op_j[op];
       ++s.m;
     }
+    bool on[LMAX] = {};
+    for (int q = 0; q < s.m; ++q)
+      if (s.diag[q] != 4) on[s.gi[q]] = true;
+    for (int r = 0; r < LMAX; ++r)
+      if (on[r]) s.act[s.nact++] = r;
     v.push_back(s);
     k += s.m;
   }
@@ -187,6 +218,7 @@ void items_of(const cvq_batch* b, int inst, int seg, const BSeg* sg, int kind, s
 
 int build_plan(cvq_batch* b) {
   drop_graph(b);
+  drop_screen(b);
   if (b->plan) cudaFree(b->plan);
   b->plan = nullptr;
   const int n = b->n;
@@ -330,7 +362,170 @@ int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
   return CVQ_OK;
 }
 
+// The plan of the batched screen for the given subsets (subset_off == NULL:
+// every instance's whole pool): per instance its distinct shifts and diagonal
+// functions, work items of about `tile` amplitudes, the reduction of their
+// partials into z rows and one epilogue entry per screened element.
+int build_screen_plan(cvq_batch* b, const int* subset_off, const int* subset) {
+  drop_screen(b);
+  const int n = b->n;
+  std::vector<BScreen> scr(n);
+  std::vector<int4> desc;
+  std::vector<BItem> items;
+  std::vector<BRed> red;
+  std::vector<BScreenOut> outs;
+  std::vector<ScreenArg> sa(1);
+  std::vector<ScreenMap> sm(1);
+  int slot = 0, zrows = 0;
+  for (int i = 0; i < n; ++i) {
+    memset(&scr[i], 0, sizeof(BScreen));
+    if (b->n_ops[i] < 0) continue;
+    const int* sub = subset_off ? subset + subset_off[i] : nullptr;
+    const int ns = subset_off ? subset_off[i + 1] - subset_off[i] : 0;
+    if (int rc = internal_screen_plan(b->pools[i], sub, ns, sa.data(), sm.data())) return rc;
+    const ScreenArg& A = sa[0];
+    const ScreenMap& M = sm[0];
+    scr[i].sh_off = (int)desc.size();
+    scr[i].nsh = A.nsh;
+    desc.insert(desc.end(), A.sh, A.sh + A.nsh);
+    scr[i].dg_off = (int)desc.size();
+    scr[i].ndg = A.ndg;
+    desc.insert(desc.end(), A.dg, A.dg + A.ndg);
+    const int rows = 2 * A.nsh + A.ndg;
+    if (rows > 0) {
+      const int s0 = slot;
+      int cnt = 0;
+      for (int64_t x = 0; x < b->S[i].dim; x += b->tile, ++cnt) {
+        BItem it;
+        it.kind = BI_APPLYH;  // unused by the screen kernel
+        it.inst = i;
+        it.seg = -1;
+        it.slot = slot;
+        it.a = x;
+        it.b = std::min<int64_t>(b->S[i].dim, x + b->tile);
+        items.push_back(it);
+        slot += rows;
+      }
+      for (int r = 0; r < rows; ++r) red.push_back({i, zrows + r, 1, s0 + r, cnt, rows});
+    }
+    for (int k = 0; k < M.n; ++k) {
+      BScreenOut o;
+      memset(&o, 0, sizeof o);
+      o.inst = i;
+      o.zrow = zrows;
+      o.out = (int)outs.size();
+      o.isdg = M.e[k].x;
+      o.sp = M.e[k].y;
+      o.sn = M.e[k].z;
+      o.d = 2 * A.nsh + M.e[k].y;  // diagonal sums follow the 2 nsh shift rows
+      o.cp = M.cp[k];
+      outs.push_back(o);
+    }
+    zrows += rows;
+  }
+  const int nl = (int)b->layer_n.size();
+  const size_t s_c = a256(sizeof(int) * (nl + 1));
+  const size_t s_s = a256(sizeof(BScreen) * n);
+  const size_t s_d = a256(sizeof(int4) * std::max<size_t>(1, desc.size()));
+  const size_t s_i = a256(sizeof(BItem) * std::max<size_t>(1, items.size()));
+  const size_t s_r = a256(sizeof(BRed) * std::max<size_t>(1, red.size()));
+  const size_t s_o = a256(sizeof(BScreenOut) * std::max<size_t>(1, outs.size()));
+  const size_t s_p = a256(sizeof(double) * std::max(1, slot));
+  const size_t s_z = a256(sizeof(double) * std::max(1, zrows));
+  BCUDA(cudaMalloc(&b->splan, s_c + s_s + s_d + s_i + s_r + s_o + s_p + s_z), "cudaMalloc of the screen plan");
+  char* q = (char*)b->splan;
+  b->s_counters = (int*)q;
+  q += s_c;
+  b->s_screens = (BScreen*)q;
+  q += s_s;
+  b->s_desc = (int4*)q;
+  q += s_d;
+  b->s_items = (BItem*)q;
+  q += s_i;
+  b->s_red = (BRed*)q;
+  q += s_r;
+  b->s_outs = (BScreenOut*)q;
+  q += s_o;
+  b->s_partial = (double*)q;
+  q += s_p;
+  b->s_z = (double*)q;
+  BCUDA(cudaMemcpy(b->s_screens, scr.data(), sizeof(BScreen) * n, cudaMemcpyHostToDevice), "copy screens");
+  if (!desc.empty()) BCUDA(cudaMemcpy(b->s_desc, desc.data(), sizeof(int4) * desc.size(), cudaMemcpyHostToDevice), "copy shifts");
+  if (!items.empty()) BCUDA(cudaMemcpy(b->s_items, items.data(), sizeof(BItem) * items.size(), cudaMemcpyHostToDevice), "copy items");
+  if (!red.empty()) BCUDA(cudaMemcpy(b->s_red, red.data(), sizeof(BRed) * red.size(), cudaMemcpyHostToDevice), "copy reductions");
+  if (!outs.empty()) BCUDA(cudaMemcpy(b->s_outs, outs.data(), sizeof(BScreenOut) * outs.size(), cudaMemcpyHostToDevice), "copy outputs");
+  b->s_nitems = (int)items.size();
+  b->s_nred = (int)red.size();
+  b->s_nouts = (int)outs.size();
+  b->s_valid = true;
+  return CVQ_OK;
+}
+
+int capture_screen(cvq_batch* b, const double* theta, double* grad) {
+  if (b->sexec) cudaGraphExecDestroy(b->sexec);
+  b->sexec = nullptr;
+  cudaStream_t st = b->cap;
+  const int nl = (int)b->layer_n.size();
+  const int nfwd = nl / 2 + 1;  // conversion, forward segments, matvec
+  BCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = cudaMemsetAsync(b->s_counters, 0, sizeof(int) * (nl + 1), st);
+  if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
+  const int grid = b->sms * b->ctas_per_sm;
+  for (int l = 0; l < nfwd && e == cudaSuccess; ++l)
+    e = launch_batch_layer(b->kind, false, grid, b->smem, b->inst_d, b->segs_d, b->items_d + b->layer_off[l],
+                           b->layer_n[l], b->s_counters + l, b->ids_d, theta, b->active_d, b->partial_d, st);
+  if (e == cudaSuccess)
+    e = launch_batch_screen(b->kind, grid, b->inst_d, b->s_items, b->s_nitems, b->s_counters + nl, b->active_d,
+                            b->s_screens, b->s_desc, b->s_partial, st);
+  if (e == cudaSuccess) e = launch_batch_reduce(b->s_red, b->s_nred, b->s_partial, b->active_d, b->s_z, nullptr, st);
+  if (e == cudaSuccess) e = launch_batch_screen_out(b->s_outs, b->s_nouts, b->s_z, b->active_d, grad, st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_err(e != cudaSuccess ? e : e2, "capture of the batched screen");
+  }
+  e = cudaGraphInstantiate(&b->sexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->sexec = nullptr;
+    return cuda_err(e, "graph instantiation");
+  }
+  b->s_theta = theta;
+  b->s_grad = grad;
+  return CVQ_OK;
+}
+
 }  // namespace
+
+extern "C" int cvq_batch_screen(cvq_batch* b, const double* theta_dev, const int* subset_off, const int* subset,
+                                double* grad_dev, void* stream) {
+  if (!b || !grad_dev) return errf(CVQ_EINVAL, "null argument");
+  if (!b->have) return errf(CVQ_EINVAL, "cvq_batch_set_ansatz has not been called");
+  if (b->n_theta > 0 && !theta_dev) return errf(CVQ_EINVAL, "null theta");
+  std::vector<int> key;
+  if (subset_off) {
+    if (subset_off[0] != 0) return errf(CVQ_EINVAL, "subset_off[0] must be 0");
+    for (int i = 0; i < b->n; ++i)
+      if (subset_off[i + 1] < subset_off[i]) return errf(CVQ_EINVAL, "subset_off decreases at instance %d", i);
+    if (subset_off[b->n] > 0 && !subset) return errf(CVQ_EINVAL, "null subset");
+    key.assign(subset_off, subset_off + b->n + 1);
+    key.insert(key.end(), subset, subset + subset_off[b->n]);
+  } else {
+    key.push_back(-1);
+  }
+  if (!b->s_valid || key != b->s_key) {
+    if (int rc = build_screen_plan(b, subset_off, subset)) {
+      drop_screen(b);
+      return rc;
+    }
+    b->s_key = key;
+  }
+  if (!b->sexec || b->s_theta != theta_dev || b->s_grad != grad_dev)
+    if (int rc = capture_screen(b, theta_dev, grad_dev)) return rc;
+  BCUDA(cudaGraphLaunch(b->sexec, (cudaStream_t)stream), "graph launch");
+  return CVQ_OK;
+}
 
 extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool* const* pools, int n_inst, int n_max,
                                 cvq_batch** out) {
@@ -342,6 +537,7 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
   if (!b) return errf(CVQ_ENOMEM, "host allocation");
   b->n = n_inst;
   b->n_max = n_max;
+  b->pools.assign(pools, pools + n_inst);
   b->pv.resize(n_inst);
   b->S.resize(n_inst);
   b->inst.resize(n_inst);
@@ -425,6 +621,7 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
 extern "C" void cvq_batch_destroy(cvq_batch* b) {
   if (!b) return;
   drop_graph(b);
+  drop_screen(b);
   if (b->plan) cudaFree(b->plan);
   if (b->state) cudaFree(b->state);
   if (b->inst_d) cudaFree(b->inst_d);

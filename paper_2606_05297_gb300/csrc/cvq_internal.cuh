@@ -40,6 +40,9 @@ struct SectorTabs {
 
 struct SectorDev {
   int kind, L, N, D, parity, periodic, nb, half;   // half = d / 2 (BKC)
+  int div32;                            // BKC with dim < 2^31: unrank by multiply-high divisions
+  uint32_t m_half, m_d;                 // their multipliers and shifts (set_bkc_div)
+  int s_half, s_d;
   int64_t dim;
   int64_t stride[LMAX];                 // BKC: d^(L-1-r)
   int64_t bh2_off[MAX_CLASSES + 1];     // BH two-mode gate work items of class M start at bh2_off[M]
@@ -150,19 +153,56 @@ __host__ __device__ __forceinline__ uint64_t spread2(uint64_t wo, int lo, int hi
   return w;
 }
 
+// n / q for 0 <= n < 2^31 and 1 <= q <= 2^31 with one 32 x 32 -> 64 bit
+// multiply: with l = ceil(log2 q) and m = ceil(2^(31+l) / q) < 2^32, the
+// quotient is (n m) >> (31 + l) (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", 1994: the error m q - 2^(31+l) is
+// below q <= 2^l, so n times it stays below 2^(31+l)).
+__host__ __device__ __forceinline__ uint32_t div_by_mul(uint32_t n, uint32_t m, int s) {
+  return (uint32_t)(((uint64_t)n * m) >> s);
+}
+
+__host__ __device__ __forceinline__ void div_magic(uint32_t q, uint32_t* m, int* s) {
+  int l = 0;
+  while ((1ull << l) < q) ++l;
+  *s = 31 + l;
+  *m = (uint32_t)(((1ull << (31 + l)) + q - 1) / q);
+}
+
+// The division constants of a Kitaev-chain sector (every caller that fills a
+// SectorDev by hand calls this after setting D, half and dim).
+__host__ __device__ __forceinline__ void set_bkc_div(SectorDev& S) {
+  S.div32 = (S.kind == CVQ_BKC && S.dim > 0 && S.dim <= 0x7fffffffll) ? 1 : 0;
+  if (!S.div32) return;
+  div_magic((uint32_t)S.half, &S.m_half, &S.s_half);
+  div_magic((uint32_t)S.D, &S.m_d, &S.s_d);
+}
+
 // Kitaev chain, even d: index = floor(f / 2), f = sum_r n_r d^(L-1-r).
 __host__ __device__ __forceinline__ uint64_t bkc_unrank(int64_t x, const SectorDev& S) {
   const int L = S.L, d = S.D;
-  int64_t hi = x / S.half;
-  const int lo = (int)(x - hi * S.half);
   uint64_t w = 0;
-  int par = 0;
-  for (int k = L - 2; k >= 0; --k) {
-    const int64_t q = hi / d;
-    const int n = (int)(hi - q * d);
-    hi = q;
-    w |= (uint64_t)n << (4 * k);
-    par += n;
+  int par = 0, lo;
+  if (S.div32) {  // every quantity below fits 31 bits
+    uint32_t hi = div_by_mul((uint32_t)x, S.m_half, S.s_half);
+    lo = (int)((uint32_t)x - hi * (uint32_t)S.half);
+    for (int k = L - 2; k >= 0; --k) {
+      const uint32_t q = div_by_mul(hi, S.m_d, S.s_d);
+      const int n = (int)(hi - q * (uint32_t)d);
+      hi = q;
+      w |= (uint64_t)n << (4 * k);
+      par += n;
+    }
+  } else {
+    int64_t hi = x / S.half;
+    lo = (int)(x - hi * S.half);
+    for (int k = L - 2; k >= 0; --k) {
+      const int64_t q = hi / d;
+      const int n = (int)(hi - q * d);
+      hi = q;
+      w |= (uint64_t)n << (4 * k);
+      par += n;
+    }
   }
   const int nl = 2 * lo + ((S.parity - par) & 1);
   w |= (uint64_t)nl << (4 * (L - 1));
@@ -211,11 +251,38 @@ struct PoolDev {
   const double* lam;
 };
 
+// Tiled block gates.  For one gate structure (modes, move) every block of
+// two or more members is listed once in a table of sector indices, grouped by
+// block class ("region": all blocks of one size, one unitary and one set of
+// generator factors).  A region is cut into tiles of T = TILE_T x S slots (S
+// slots per thread of a CTA) holding nbt = T / b whole blocks, member-major
+// within the tile: slot a * nbt + k is member a of the tile's block k, so
+// consecutive slots are the same member of neighbouring blocks.  Unused
+// slots hold -1.  Large sectors take S = TILE_S_LARGE, so that each thread
+// keeps several loads in flight from HBM; small ones S = 1, so that every
+// CTA gets work.
+constexpr int TILE_T = NTHREADS;
+constexpr int TILE_S_LARGE = 4;
+constexpr int64_t TILE_LARGE_DIM = 1 << 22;
+struct TileRegion {
+  int b, nbt, count;     // block size, blocks per tile, blocks in the region
+  int u_off, f_off;      // the class's unitary (within a gate's U) and generator factors (within the type's F)
+  int bi, cls, pad;      // block index within the type's list, orbit class (table build only)
+  int64_t tile0;         // first tile of the region
+};
+struct TileMap {
+  const int* idx;           // ntiles x (TILE_T x slots) sector indices; null: the gate has no table
+  const TileRegion* reg;    // nreg regions, in tile order
+  int nreg, slots;          // slots: S, the tile slots per thread
+  int64_t ntiles;
+};
+
 // Everything a gate kernel needs about one gate of an ansatz.
 struct GateArg {
   int i, j;              // modes
   TypeDesc t;            // structure of the generator
   const cdf* U;          // this gate's block unitaries (t.nu entries, df complex)
+  TileMap tm;            // tiled index table of the gate's structure (may be empty)
 };
 
 // Shared memory of a block-gate kernel: the gate tables (block unitaries,
@@ -261,6 +328,7 @@ struct DiagRunArg {
   int m, npair;
   int diag[MAX_RUN], gi[MAX_RUN], gj[MAX_RUN];   // per gate: f type (1..4) and modes
   int pi[MAX_RUN_PAIRS], pj[MAX_RUN_PAIRS];
+  int nact, act[LMAX];                            // modes with a single-mode gate (T[r] is not all ones)
   cdf T[LMAX][DMAX];
   cdf TP[MAX_RUN_PAIRS][DMAX * DMAX];
 };
@@ -286,6 +354,7 @@ struct BSeg {
   int inst, k0, m, isdiag, npair;
   int diag[BATCH_RUN], gi[BATCH_RUN], gj[BATCH_RUN];
   int pi[MAX_RUN_PAIRS], pj[MAX_RUN_PAIRS];
+  int nact, act[LMAX];  // modes with a single-mode gate of the run
 };
 
 // One work item: a range [a, b) of chunks (BH gate), orbits (BKC gate) or
@@ -301,6 +370,20 @@ struct BRed {
   int inst, out, is_energy, slot0, count, stride;
 };
 
+// Batched screen: one instance's distinct ladder shifts and diagonal
+// functions (ranges of the plan's descriptor array).  Its work items each
+// leave 2 nsh + ndg partial sums (Re and Im of Z per shift, then one per
+// diagonal function), reduced into rows zrow.. of the z buffer.
+struct BScreen {
+  int sh_off, nsh, dg_off, ndg;
+};
+// One screened element: g = 2 [Re(cp Z_sp) - Re(conj(cp) Z_sn)], or 2 D with D
+// in row d (the instance's diagonal rows follow its 2 nsh shift rows).
+struct BScreenOut {
+  int inst, zrow, out, isdg, sp, sn, d, pad;
+  double2 cp;
+};
+
 cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, int maxblk, const int* ids,
                                const double* theta, const int* active, cudaStream_t st);
 cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const BInst* insts, const BSeg* segs,
@@ -309,6 +392,11 @@ cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const 
 cudaError_t set_batch_smem_limit(int bytes);
 cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, const int* active, double* E,
                                 double* grad, cudaStream_t st);
+cudaError_t launch_batch_screen(int kind, int grid, const BInst* insts, const BItem* items, int nitems, int* counter,
+                                const int* active, const BScreen* screens, const int4* desc, double* partial,
+                                cudaStream_t st);
+cudaError_t launch_batch_screen_out(const BScreenOut* outs, int n, const double* z, const int* active, double* grad,
+                                    cudaStream_t st);
 
 // Pool indices screened by one launch (passed by value).
 struct SubsetArg {
@@ -343,6 +431,12 @@ cudaError_t launch_apply_H(const SectorDev& S, const cdf* psi, cdf* sigma, doubl
 cudaError_t launch_reduce(const double* partial, int nred, int nblk, double scale, double* out, cudaStream_t st);
 cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_dev, PoolDev P, cdf* U, cudaStream_t st);
 cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* src, cdf* dst, cudaStream_t st);
+// Tiled gates: the table of one gate structure, and the in-place forward gate
+// and reverse step that read it (k_tile.cu).
+cudaError_t launch_tile_build(const SectorDev& S, int i, int j, const TypeDesc& t, PoolDev P, const TileRegion* reg_dev,
+                              int nreg, int64_t max_count, int tile_slots, int* idx, int* bad, cudaStream_t st);
+cudaError_t launch_tile_gate(const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial, bool adjoint,
+                             cudaStream_t st);
 cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial,
                                 cudaStream_t st);
 // Gradient-only pass over up to DIAG_ACC gates of a diagonal run (their f type and modes).

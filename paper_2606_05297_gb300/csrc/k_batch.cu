@@ -199,6 +199,94 @@ __global__ void k_batch_reduce(const BRed* __restrict__ red, int n, const double
   else grad[d.out] = 2.0 * v;
 }
 
+// The screen layer of the batched screen: items [0, nitems) claimed in order
+// from *counter, each a range of one instance's sector, with that instance's
+// sigma = H psi in its lambda buffer.
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    k_batch_screen(const BInst* __restrict__ insts, const BItem* __restrict__ items, int nitems, int* counter,
+                   const int* __restrict__ active, const BScreen* __restrict__ screens, const int4* __restrict__ desc,
+                   double* __restrict__ partial) {
+  __shared__ SectorDev S;
+  __shared__ int item;
+  __shared__ int64_t G64[LMAX][DMAX + 1];
+  __shared__ float2 sq[DMAX][5];
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int k = item;
+    if (k >= nitems) break;
+    const BItem it = items[k];
+    if (!active[it.inst]) {
+      __syncthreads();
+      continue;
+    }
+    const BInst& I = insts[it.inst];
+    copy_words(&S, &I.S, sizeof(SectorDev));
+    __syncthreads();
+    if (KIND == CVQ_BH) load_G(G64, S);
+    for (int e = threadIdx.x; e < DMAX * 5; e += blockDim.x) (&sq[0][0])[e] = (&S.tab->sq[0][0])[e];
+    __syncthreads();
+    const BScreen sc = screens[it.inst];
+    const int nc_sh = (sc.nsh + SCREEN_CHUNK - 1) / SCREEN_CHUNK, nc_dg = (sc.ndg + SCREEN_CHUNK - 1) / SCREEN_CHUNK;
+    for (int c = 0; c < nc_sh + nc_dg; ++c) {
+      const bool isdg = c >= nc_sh;
+      const int base = (isdg ? c - nc_sh : c) * SCREEN_CHUNK;
+      const int cnt = min(SCREEN_CHUNK, (isdg ? sc.ndg : sc.nsh) - base);
+      dfacc zr[SCREEN_CHUNK], zi[SCREEN_CHUNK];
+      screen_chunk<KIND>(S, G64, sq, isdg, desc + (isdg ? sc.dg_off : sc.sh_off) + base, cnt, I.psi, I.lam,
+                         it.a + threadIdx.x, it.b, NTHREADS, zr, zi);
+#pragma unroll
+      for (int q = 0; q < SCREEN_CHUNK; ++q) {
+        if (q >= cnt) continue;
+        if (isdg) {
+          const double r = block_sum(acc_to_double(zr[q]));
+          if (threadIdx.x == 0) partial[(size_t)it.slot + 2 * sc.nsh + base + q] = r;
+        } else {
+          const double r = block_sum(acc_to_double(zr[q]));
+          const double im = block_sum(acc_to_double(zi[q]));
+          if (threadIdx.x == 0) {
+            partial[(size_t)it.slot + 2 * (base + q)] = r;
+            partial[(size_t)it.slot + 2 * (base + q) + 1] = im;
+          }
+        }
+      }
+    }
+    __syncthreads();  // S and the item number are reused by the next item
+  }
+}
+
+__global__ void k_batch_screen_out(const BScreenOut* __restrict__ outs, int n, const double* __restrict__ z,
+                                   const int* __restrict__ active, double* __restrict__ grad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const BScreenOut o = outs[k];
+  if (!active[o.inst]) return;
+  const double* zz = z + o.zrow;
+  if (o.isdg) {
+    grad[o.out] = 2.0 * zz[o.d];
+  } else {
+    const double pr = zz[2 * o.sp], pi = zz[2 * o.sp + 1], mr = zz[2 * o.sn], mi = zz[2 * o.sn + 1];
+    grad[o.out] = 2.0 * ((o.cp.x * pr - o.cp.y * pi) - (o.cp.x * mr + o.cp.y * mi));
+  }
+}
+
+cudaError_t launch_batch_screen(int kind, int grid, const BInst* insts, const BItem* items, int nitems, int* counter,
+                                const int* active, const BScreen* screens, const int4* desc, double* partial,
+                                cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  if (kind == CVQ_BH) k_batch_screen<CVQ_BH><<<grid, NTHREADS, 0, st>>>(insts, items, nitems, counter, active, screens, desc, partial);
+  else k_batch_screen<CVQ_BKC><<<grid, NTHREADS, 0, st>>>(insts, items, nitems, counter, active, screens, desc, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_screen_out(const BScreenOut* outs, int n, const double* z, const int* active, double* grad,
+                                    cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_batch_screen_out<<<(n + 127) / 128, 128, 0, st>>>(outs, n, z, active, grad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, int maxblk, const int* ids,
                                const double* theta, const int* active, cudaStream_t st) {
   if (ngates <= 0 || maxblk <= 0) return cudaSuccess;

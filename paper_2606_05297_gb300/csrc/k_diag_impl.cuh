@@ -24,10 +24,11 @@ __device__ __forceinline__ void cmac_conj_full(dfacc& ar, dfacc& ai, cdf u, cdf 
 }
 
 // psi[x] *= prod_r T[r][n_r] * prod_p TP[p][n_i D + n_j] for x = x0, x0 + step,
-// ... < x1 (modes with n_r = 0 contribute exactly 1).  A carries the run's
-// gate list (m, npair, diag, gi, gj, pi, pj).  ADJ: acc[k] += Re(conj(lam)
-// i f_k psi) at the run's output state, then psi and lam are multiplied by the
-// conjugate phase.
+// ... < x1, the first product over the modes a single-mode gate of the run
+// acts on (T is 1 on every other mode, and at n_r = 0).  A carries the run's
+// gate list (m, npair, diag, gi, gj, pi, pj) and its modes (nact, act).
+// ADJ: acc[k] += Re(conj(lam) i f_k psi) at the run's output state, then psi
+// and lam are multiplied by the conjugate phase.
 template <int KIND, bool ADJ, int NACC, class A>
 __device__ __forceinline__ void diag_run_range(const SectorDev& S, const int64_t (*Gs)[DMAX + 1],
                                                const cdf (*T)[DMAX], const cdf (*TP)[DMAX * DMAX], const A& a,
@@ -37,7 +38,8 @@ __device__ __forceinline__ void diag_run_range(const SectorDev& S, const int64_t
   for (int64_t x = x0; x < x1; x += step) {
     const uint64_t w = (KIND == CVQ_BKC) ? bkc_unrank(x, S) : bh_unrank(x, L, S.N, Gs);
     df pr = df_make(1.f, 0.f), pi = df_make(0.f, 0.f);
-    for (int r = 0; r < L; ++r) {
+    for (int q = 0; q < a.nact; ++q) {
+      const int r = a.act[q];
       const int n = occ_get(w, r);
       if (n == 0) continue;
       const cdf t = T[r][n];

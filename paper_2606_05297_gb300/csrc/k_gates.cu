@@ -75,6 +75,7 @@ void set_block_smem_limit(int bytes);
 template <bool ADJ>
 static cudaError_t launch_gate_impl(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* src, cdf* dst,
                                     cdf* lam, double* partial, cudaStream_t st) {
+  if (g.tm.idx && src == dst && !g.t.diag) return launch_tile_gate(g, P, dst, lam, partial, ADJ, st);
   // The largest gate table: a two-mode gate at cutoff 16 has at most
   // 2 * (1^2 + ... + 15^2) + 16^2 = 2736 block entries and at most 64 blocks.
   constexpr int kMaxNu = 2816, kMaxBlocks = 64;

@@ -112,4 +112,73 @@ __device__ __forceinline__ void apply_H_range(const SectorDev& S, const int64_t 
   }
 }
 
+// Pool screen, Eq. (grad): for a generator A = cp G - conj(cp) G^dag whose
+// ladder string G moves x by delta (and G^dag by -delta),
+//   Re <sigma|A psi> = Re(cp Z_delta) - Re(conj(cp) Z_{-delta}),
+//   Z_delta = sum_x F_delta(x) conj(sigma[x]) psi[x + delta],
+// with F_delta(x) the ladder factor of the move; for a diagonal generator
+// A = i f(n), Re <sigma|A psi> = sum_x f(x) Re(conj(sigma[x]) i psi[x]).
+// Every pool element that moves by the same delta (both phases of a beam
+// splitter or squeezer, for instance) shares one Z, so one neighbour read
+// per distinct shift serves them all.  This accumulates one chunk of at most
+// SCREEN_CHUNK shifts (desc[k] = (i, di, j, dj), j < 0 for a single-mode
+// move) or diagonal functions (desc[k] = (f type 1..4, i, j, 0)) over
+// x = x0, x0 + step, ... < x1: zr, zi hold Re and Im of Z per shift, zr the
+// diagonal sums.
+template <int KIND>
+__device__ __forceinline__ void screen_chunk(const SectorDev& S, const int64_t (*Gs)[DMAX + 1], const float2 (*sq)[5],
+                                             bool isdg, const int4* desc, int cnt, const cdf* __restrict__ psi,
+                                             const cdf* __restrict__ sigma, int64_t x0, int64_t x1, int64_t step,
+                                             dfacc* zr, dfacc* zi) {
+  const int L = S.L, Dm1 = S.D - 1;
+#pragma unroll
+  for (int k = 0; k < SCREEN_CHUNK; ++k) {
+    acc_zero(zr[k]);
+    acc_zero(zi[k]);
+  }
+  for (int64_t x = x0; x < x1; x += step) {
+    uint64_t wR = 0;
+    const uint64_t w = unrank<KIND>(x, S, Gs, &wR);
+    const cdf s = sigma[x];
+    if (isdg) {
+      const cdf p = psi[x];
+      dfacc cc;  // Re(conj(s) i p) = s.im p.re - s.re p.im
+      acc_zero(cc);
+      acc_mac(cc, im_of(s), re_of(p));
+      acc_mac(cc, df_neg(re_of(s)), im_of(p));
+      const df cv = acc_get(cc);
+#pragma unroll
+      for (int k = 0; k < SCREEN_CHUNK; ++k) {
+        if (k < cnt) {
+          const int4 d = desc[k];
+          const int ni = occ_get(w, d.y);
+          const int f = (d.x == 1) ? ni * ni : (d.x == 2) ? ni * (ni - 1) : (d.x == 3) ? ni : ni * occ_get(w, d.z);
+          if (f) acc_macf(zr[k], cv, (float)f);
+        }
+      }
+      continue;
+    }
+    const int64_t fx = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
+#pragma unroll
+    for (int k = 0; k < SCREEN_CHUNK; ++k) {
+      if (k >= cnt) continue;
+      const int4 h = desc[k];  // (i, di, j, dj), j < 0: single mode
+      const int ni = occ_get(w, h.x), nj = (h.z >= 0) ? occ_get(w, h.z) : 0;
+      if (ni + h.y < 0 || ni + h.y > Dm1 || (h.z >= 0 && (nj + h.w < 0 || nj + h.w > Dm1))) continue;
+      df F = df_make(sq[ni][h.y + 2].x, sq[ni][h.y + 2].y);
+      if (h.z >= 0) F = df_mul(F, df_make(sq[nj][h.w + 2].x, sq[nj][h.w + 2].y));
+      const cdf q = psi[moved_index<KIND>(x, w, wR, fx, h.x, h.y, h.z, h.w, S, Gs)];
+      dfacc tr, ti;  // conj(s) q
+      acc_zero(tr);
+      acc_zero(ti);
+      acc_mac(tr, re_of(s), re_of(q));
+      acc_mac(tr, im_of(s), im_of(q));
+      acc_mac(ti, re_of(s), im_of(q));
+      acc_mac(ti, df_neg(im_of(s)), re_of(q));
+      acc_mac(zr[k], F, acc_get(tr));
+      acc_mac(zi[k], F, acc_get(ti));
+    }
+  }
+}
+
 }  // namespace cvq

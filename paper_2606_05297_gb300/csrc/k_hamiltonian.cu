@@ -60,61 +60,14 @@ __global__ void __launch_bounds__(NTHREADS) k_screen(const __grid_constant__ Sec
   if (KIND == CVQ_BH) load_G(Gs, S);
   for (int e = threadIdx.x; e < DMAX * 5; e += blockDim.x) (&sq[0][0])[e] = (&S.tab->sq[0][0])[e];
   __syncthreads();
-  const int L = S.L, Dm1 = S.D - 1;
   const int nc_sh = (a.nsh + SCREEN_CHUNK - 1) / SCREEN_CHUNK, nc_dg = (a.ndg + SCREEN_CHUNK - 1) / SCREEN_CHUNK;
   for (int c = 0; c < nc_sh + nc_dg; ++c) {
     const bool isdg = c >= nc_sh;
     const int base = (isdg ? c - nc_sh : c) * SCREEN_CHUNK;
     const int cnt = min(SCREEN_CHUNK, (isdg ? a.ndg : a.nsh) - base);
     dfacc zr[SCREEN_CHUNK], zi[SCREEN_CHUNK];
-#pragma unroll
-    for (int k = 0; k < SCREEN_CHUNK; ++k) {
-      acc_zero(zr[k]);
-      acc_zero(zi[k]);
-    }
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x) {
-      uint64_t wR = 0;
-      const uint64_t w = unrank<KIND>(x, S, Gs, &wR);
-      const cdf s = sigma[x];
-      if (isdg) {
-        const cdf p = psi[x];
-        dfacc cc;  // Re(conj(s) i p) = s.im p.re - s.re p.im
-        acc_zero(cc);
-        acc_mac(cc, im_of(s), re_of(p));
-        acc_mac(cc, df_neg(re_of(s)), im_of(p));
-        const df cv = acc_get(cc);
-#pragma unroll
-        for (int k = 0; k < SCREEN_CHUNK; ++k) {
-          if (k < cnt) {
-            const int4 d = a.dg[base + k];
-            const int ni = occ_get(w, d.y);
-            const int f = (d.x == 1) ? ni * ni : (d.x == 2) ? ni * (ni - 1) : (d.x == 3) ? ni : ni * occ_get(w, d.z);
-            if (f) acc_macf(zr[k], cv, (float)f);
-          }
-        }
-        continue;
-      }
-      const int64_t fx = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
-#pragma unroll
-      for (int k = 0; k < SCREEN_CHUNK; ++k) {
-        if (k >= cnt) continue;
-        const int4 h = a.sh[base + k];  // (i, di, j, dj), j < 0: single mode
-        const int ni = occ_get(w, h.x), nj = (h.z >= 0) ? occ_get(w, h.z) : 0;
-        if (ni + h.y < 0 || ni + h.y > Dm1 || (h.z >= 0 && (nj + h.w < 0 || nj + h.w > Dm1))) continue;
-        df F = df_make(sq[ni][h.y + 2].x, sq[ni][h.y + 2].y);
-        if (h.z >= 0) F = df_mul(F, df_make(sq[nj][h.w + 2].x, sq[nj][h.w + 2].y));
-        const cdf q = psi[moved_index<KIND>(x, w, wR, fx, h.x, h.y, h.z, h.w, S, Gs)];
-        dfacc tr, ti;  // conj(s) q
-        acc_zero(tr);
-        acc_zero(ti);
-        acc_mac(tr, re_of(s), re_of(q));
-        acc_mac(tr, im_of(s), im_of(q));
-        acc_mac(ti, re_of(s), im_of(q));
-        acc_mac(ti, df_neg(im_of(s)), re_of(q));
-        acc_mac(zr[k], F, acc_get(tr));
-        acc_mac(zi[k], F, acc_get(ti));
-      }
-    }
+    screen_chunk<KIND>(S, Gs, sq, isdg, (isdg ? a.dg : a.sh) + base, cnt, psi, sigma,
+                       (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim, (int64_t)gridDim.x * blockDim.x, zr, zi);
 #pragma unroll
     for (int k = 0; k < SCREEN_CHUNK; ++k) {
       if (k >= cnt) continue;

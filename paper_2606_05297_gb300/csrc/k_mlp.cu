@@ -2,12 +2,13 @@
 // with bf16 weights and fp32 accumulation, its backward pass, a listwise
 // softmax cross-entropy, and Adam.
 //
-// One forward over a pool of ~200 operators is ~15 MFLOP, so these kernels
-// are bound by launch latency and the weight reads from L2, not by
-// arithmetic; they use CUDA cores with weight copies laid out so that
-// consecutive threads read consecutive bf16 values.  Every reduction (over
-// hidden units or over rows) runs in a fixed order, so results are
-// deterministic.
+// One forward over a pool of ~200 operators is ~15 MFLOP.  The two 256 x 256
+// contractions (hidden layer forward, its transpose and its weight gradient
+// backward) run on the tensor cores (mma.sync, bf16 operands, fp32 sums); the
+// 32-wide input layer, the biases and the output layer stay on the CUDA
+// cores, with weight copies laid out so that consecutive threads read
+// consecutive bf16 values.  Every reduction (over hidden units or over rows)
+// runs in a fixed order, so results are deterministic.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -24,7 +25,7 @@ int internal_fail(int code, const char* msg);
 int internal_prof_mlp_begin(cudaStream_t st, double bytes, double flops);
 void internal_prof_end(int idx, cudaStream_t st);
 
-constexpr int MF = 32, MH = 256, MRT = 8;  // input width, hidden width, rows per CTA
+constexpr int MF = 32, MH = 256;  // input width, hidden width
 constexpr int O_W1 = 0, O_B1 = O_W1 + MH * MF, O_W2 = O_B1 + MH, O_B2 = O_W2 + MH * MH, O_W3 = O_B2 + MH,
               O_B3 = O_W3 + MH, NPARAM = O_B3 + 1;
 
@@ -38,89 +39,238 @@ struct MlpDev {
 
 __device__ __forceinline__ float bf(bf16 v) { return __bfloat162float(v); }
 
-// Rows r0..r0+MRT-1: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), s = w3 . h2 + b3.
-__global__ void __launch_bounds__(MH) k_mlp_fwd(MlpDev m, const float* __restrict__ X, int rows,
-                                                float* __restrict__ out) {
-  __shared__ float xs[MRT][MF];
-  __shared__ float h1[MRT][MH];
-  __shared__ float red[MRT][MH / 32];
-  const int r0 = blockIdx.x * MRT, u = threadIdx.x;
-  for (int e = u; e < MRT * MF; e += MH) {
+// ------------------------------------------------------------ tensor-core layers
+//
+// The two 256 x 256 products (the hidden layer forward, and its transpose and
+// weight gradient backward) run on the tensor cores with
+// mma.sync.m16n8k16 (bf16 operands, fp32 accumulation).  The weights are
+// bf16 already; an fp32 activation a is split into two bf16 numbers
+// a_hi = bf16(a), a_lo = bf16(a - a_hi), whose sum is within 2^-18 |a| of a,
+// and both halves are multiplied (the weight gradient, whose two operands
+// are activations, takes hi*hi + hi*lo + lo*hi).  Each output still sums
+// its terms in a fixed order, so results are deterministic.
+
+constexpr int TC_ROWS = 16;            // rows of one forward / backward CTA (the MMA's M)
+constexpr int TC_PAD = 8;              // bf16 padding per shared row: conflict-free fragment loads
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void split_bf16(float x, bf16& hi, bf16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ uint32_t ld_pair(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// A fragment (16 x 16, row major) of rows 0..15, columns k0..k0+15 of a
+// shared [16][MH + TC_PAD] bf16 array.
+__device__ __forceinline__ void frag_a(uint32_t (&a)[4], const bf16 (*A)[MH + TC_PAD], int k0) {
+  const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+  a[0] = ld_pair(&A[g][k0 + 2 * t]);
+  a[1] = ld_pair(&A[g + 8][k0 + 2 * t]);
+  a[2] = ld_pair(&A[g][k0 + 2 * t + 8]);
+  a[3] = ld_pair(&A[g + 8][k0 + 2 * t + 8]);
+}
+
+// out[r][n] = sum_k A[r][k] B[n][k] for the 16 rows of A (hi and lo halves)
+// and this warp's 32 columns n0..n0+31; Bt is row n, column k (k contiguous).
+__device__ __forceinline__ void mma_rows_x_256(float (&c)[4][4], const bf16 (*Ah)[MH + TC_PAD],
+                                               const bf16 (*Al)[MH + TC_PAD], const bf16* __restrict__ Bt, int n0) {
+  const int g = (threadIdx.x & 31) >> 2, t = threadIdx.x & 3;
+#pragma unroll 4
+  for (int k0 = 0; k0 < MH; k0 += 16) {
+    uint32_t ah[4], al[4];
+    frag_a(ah, Ah, k0);
+    frag_a(al, Al, k0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bf16* bp = Bt + (size_t)(n0 + 8 * j + g) * MH + k0 + 2 * t;
+      const uint32_t b0 = ld_pair(bp), b1 = ld_pair(bp + 8);
+      mma_bf16(c[j], ah, b0, b1);
+      mma_bf16(c[j], al, b0, b1);
+    }
+  }
+}
+
+// Rows r0..r0+15: h1 = relu(W1 x + b1) on the CUDA cores (K = 32), then
+// h2 = relu(W2 h1 + b2) on the tensor cores, s = w3 . h2 + b3.
+__global__ void __launch_bounds__(MH) k_mlp_fwd_tc(MlpDev m, const float* __restrict__ X, int rows,
+                                                   float* __restrict__ out) {
+  __shared__ float xs[TC_ROWS][MF];
+  __shared__ __align__(16) bf16 Ah[TC_ROWS][MH + TC_PAD], Al[TC_ROWS][MH + TC_PAD];
+  __shared__ float red[TC_ROWS][MH / 32];
+  const int r0 = blockIdx.x * TC_ROWS, u = threadIdx.x;
+  for (int e = u; e < TC_ROWS * MF; e += MH) {
     const int r = e / MF, f = e % MF;
     xs[r][f] = (r0 + r < rows) ? X[(size_t)(r0 + r) * MF + f] : 0.f;
   }
   __syncthreads();
-  float acc[MRT];
+  float acc[TC_ROWS];
   const float b1 = bf(__float2bfloat16_rn(m.P[O_B1 + u]));
 #pragma unroll
-  for (int r = 0; r < MRT; ++r) acc[r] = b1;
+  for (int r = 0; r < TC_ROWS; ++r) acc[r] = b1;
   for (int f = 0; f < MF; ++f) {
     const float w = bf(m.W1T[f * MH + u]);
 #pragma unroll
-    for (int r = 0; r < MRT; ++r) acc[r] = fmaf(xs[r][f], w, acc[r]);
+    for (int r = 0; r < TC_ROWS; ++r) acc[r] = fmaf(xs[r][f], w, acc[r]);
   }
 #pragma unroll
-  for (int r = 0; r < MRT; ++r) {
-    const float h = fmaxf(acc[r], 0.f);
-    h1[r][u] = h;
+  for (int r = 0; r < TC_ROWS; ++r) {
+    const float h = (r0 + r < rows) ? fmaxf(acc[r], 0.f) : 0.f;
     if (r0 + r < rows) m.H1[(size_t)(r0 + r) * MH + u] = h;
+    split_bf16(h, Ah[r][u], Al[r][u]);
   }
   __syncthreads();
-  const int v = u;
-  const float b2 = bf(__float2bfloat16_rn(m.P[O_B2 + v]));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int n0 = 32 * warp;
+  float c[4][4];
 #pragma unroll
-  for (int r = 0; r < MRT; ++r) acc[r] = b2;
-  for (int k = 0; k < MH; ++k) {
-    const float w = bf(m.W2T[k * MH + v]);
-#pragma unroll
-    for (int r = 0; r < MRT; ++r) acc[r] = fmaf(h1[r][k], w, acc[r]);
+  for (int j = 0; j < 4; ++j) {
+    const int n = n0 + 8 * j + 2 * t;
+    const float b20 = bf(__float2bfloat16_rn(m.P[O_B2 + n])), b21 = bf(__float2bfloat16_rn(m.P[O_B2 + n + 1]));
+    c[j][0] = b20;
+    c[j][1] = b21;
+    c[j][2] = b20;
+    c[j][3] = b21;
   }
-  const float w3 = bf(m.W3[v]);
-  const int lane = v & 31, warp = v >> 5;
+  mma_rows_x_256(c, Ah, Al, m.W2, n0);
+  float s0 = 0.f, s1 = 0.f;  // score terms of rows g and g + 8
 #pragma unroll
-  for (int r = 0; r < MRT; ++r) {
-    const float h = fmaxf(acc[r], 0.f);
-    if (r0 + r < rows) m.H2[(size_t)(r0 + r) * MH + v] = h;
-    float c = h * w3;
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    if (lane == 0) red[r][warp] = c;
+  for (int j = 0; j < 4; ++j) {
+    const int n = n0 + 8 * j + 2 * t;
+    const float w30 = bf(m.W3[n]), w31 = bf(m.W3[n + 1]);
+    const float h00 = fmaxf(c[j][0], 0.f), h01 = fmaxf(c[j][1], 0.f);
+    const float h10 = fmaxf(c[j][2], 0.f), h11 = fmaxf(c[j][3], 0.f);
+    if (r0 + g < rows) {
+      m.H2[(size_t)(r0 + g) * MH + n] = h00;
+      m.H2[(size_t)(r0 + g) * MH + n + 1] = h01;
+    }
+    if (r0 + g + 8 < rows) {
+      m.H2[(size_t)(r0 + g + 8) * MH + n] = h10;
+      m.H2[(size_t)(r0 + g + 8) * MH + n + 1] = h11;
+    }
+    s0 = fmaf(h01, w31, fmaf(h00, w30, s0));
+    s1 = fmaf(h11, w31, fmaf(h10, w30, s1));
+  }
+  // the four lanes of a row group hold the row's terms of this warp's 32 columns
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+  s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+  s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+  if (t == 0) {
+    red[g][warp] = s0;
+    red[g + 8][warp] = s1;
   }
   __syncthreads();
-  if (v < MRT && r0 + v < rows) {
-    float s = bf(__float2bfloat16_rn(m.P[O_B3]));
-    for (int w = 0; w < MH / 32; ++w) s += red[v][w];
-    out[r0 + v] = s;
+  if (u < TC_ROWS && r0 + u < rows) {
+    float sc = bf(__float2bfloat16_rn(m.P[O_B3]));
+    for (int w = 0; w < MH / 32; ++w) sc += red[u][w];
+    out[r0 + u] = sc;
   }
 }
 
-// Per row: dH2 = ds w3 [h2 > 0], dH1 = (W2^T dH2) [h1 > 0].
-__global__ void __launch_bounds__(MH) k_mlp_bwd_rows(MlpDev m, int rows, const float* __restrict__ ds) {
-  __shared__ float d2[MRT][MH];
-  const int r0 = blockIdx.x * MRT, v = threadIdx.x;
+// Rows r0..r0+15: dH2 = ds w3 [h2 > 0] on the CUDA cores, then
+// dH1 = (W2^T dH2) [h1 > 0] on the tensor cores.
+__global__ void __launch_bounds__(MH) k_mlp_bwd_rows_tc(MlpDev m, int rows, const float* __restrict__ ds) {
+  __shared__ __align__(16) bf16 Ah[TC_ROWS][MH + TC_PAD], Al[TC_ROWS][MH + TC_PAD];
+  const int r0 = blockIdx.x * TC_ROWS, v = threadIdx.x;
   const float w3 = bf(m.W3[v]);
 #pragma unroll
-  for (int r = 0; r < MRT; ++r) {
-    float g = 0.f;
-    if (r0 + r < rows) g = (m.H2[(size_t)(r0 + r) * MH + v] > 0.f) ? ds[r0 + r] * w3 : 0.f;
-    d2[r][v] = g;
-    if (r0 + r < rows) m.dH2[(size_t)(r0 + r) * MH + v] = g;
+  for (int r = 0; r < TC_ROWS; ++r) {
+    float gv = 0.f;
+    if (r0 + r < rows) {
+      gv = (m.H2[(size_t)(r0 + r) * MH + v] > 0.f) ? ds[r0 + r] * w3 : 0.f;
+      m.dH2[(size_t)(r0 + r) * MH + v] = gv;
+    }
+    split_bf16(gv, Ah[r][v], Al[r][v]);
   }
   __syncthreads();
-  const int u = v;
-  float acc[MRT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int n0 = 32 * warp;
+  float c[4][4];
 #pragma unroll
-  for (int r = 0; r < MRT; ++r) acc[r] = 0.f;
-  for (int k = 0; k < MH; ++k) {
-    const float w = bf(m.W2[k * MH + u]);  // W2[k][u]
+  for (int j = 0; j < 4; ++j)
 #pragma unroll
-    for (int r = 0; r < MRT; ++r) acc[r] = fmaf(d2[r][k], w, acc[r]);
+    for (int q = 0; q < 4; ++q) c[j][q] = 0.f;
+  mma_rows_x_256(c, Ah, Al, m.W2T, n0);  // B[k = v][n = u] = W2[v][u], stored n-major as W2T[u][v]
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int n = n0 + 8 * j + 2 * t;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = r0 + g + 8 * h;
+      if (r >= rows) continue;
+      const float* H1 = m.H1 + (size_t)r * MH;
+      m.dH1[(size_t)r * MH + n] = (H1[n] > 0.f) ? c[j][2 * h] : 0.f;
+      m.dH1[(size_t)r * MH + n + 1] = (H1[n + 1] > 0.f) ? c[j][2 * h + 1] : 0.f;
+    }
   }
-#pragma unroll
-  for (int r = 0; r < MRT; ++r)
-    if (r0 + r < rows) m.dH1[(size_t)(r0 + r) * MH + u] = (m.H1[(size_t)(r0 + r) * MH + u] > 0.f) ? acc[r] : 0.f;
 }
 
-// Weight gradients as sums over rows in row order: one thread per parameter.
+// dW2[v][u] = sum_r dH2[r][v] H1[r][u] on the tensor cores: each CTA one
+// 64 x 64 output tile, rows taken 16 at a time in order.
+constexpr int DW_T = 64;
+__global__ void __launch_bounds__(MH) k_mlp_dw2_tc(MlpDev m, int rows) {
+  __shared__ __align__(16) bf16 Ah[DW_T][16 + TC_PAD], Al[DW_T][16 + TC_PAD];  // [v][r]
+  __shared__ __align__(16) bf16 Bh[DW_T][16 + TC_PAD], Bl[DW_T][16 + TC_PAD];  // [u][r]
+  const int v0 = (blockIdx.x / (MH / DW_T)) * DW_T, u0 = (blockIdx.x % (MH / DW_T)) * DW_T;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int wm = (warp >> 1) * 16, wn = (warp & 1) * 32;  // warp tile: 16 v x 32 u
+  float c[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[j][q] = 0.f;
+  for (int rb = 0; rb < rows; rb += 16) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * DW_T; e += blockDim.x) {
+      const int r = e / DW_T, x = e % DW_T;
+      const bool ok = rb + r < rows;
+      const float a = ok ? m.dH2[(size_t)(rb + r) * MH + v0 + x] : 0.f;
+      const float b = ok ? m.H1[(size_t)(rb + r) * MH + u0 + x] : 0.f;
+      split_bf16(a, Ah[x][r], Al[x][r]);
+      split_bf16(b, Bh[x][r], Bl[x][r]);
+    }
+    __syncthreads();
+    uint32_t ah[4], al[4];
+    ah[0] = ld_pair(&Ah[wm + g][2 * t]);
+    ah[1] = ld_pair(&Ah[wm + g + 8][2 * t]);
+    ah[2] = ld_pair(&Ah[wm + g][2 * t + 8]);
+    ah[3] = ld_pair(&Ah[wm + g + 8][2 * t + 8]);
+    al[0] = ld_pair(&Al[wm + g][2 * t]);
+    al[1] = ld_pair(&Al[wm + g + 8][2 * t]);
+    al[2] = ld_pair(&Al[wm + g][2 * t + 8]);
+    al[3] = ld_pair(&Al[wm + g + 8][2 * t + 8]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = wn + 8 * j + g;
+      const uint32_t bh0 = ld_pair(&Bh[n][2 * t]), bh1 = ld_pair(&Bh[n][2 * t + 8]);
+      const uint32_t bl0 = ld_pair(&Bl[n][2 * t]), bl1 = ld_pair(&Bl[n][2 * t + 8]);
+      mma_bf16(c[j], ah, bh0, bh1);
+      mma_bf16(c[j], ah, bl0, bl1);
+      mma_bf16(c[j], al, bh0, bh1);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int u = u0 + wn + 8 * j + 2 * t;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int v = v0 + wm + g + 8 * h;
+      m.G[O_W2 + v * MH + u] = c[j][2 * h];
+      m.G[O_W2 + v * MH + u + 1] = c[j][2 * h + 1];
+    }
+  }
+}
+
+// Weight gradients as sums over rows in row order: one thread per parameter
+// (W2 comes from k_mlp_dw2_tc).
 __global__ void __launch_bounds__(MH) k_mlp_bwd_weights(MlpDev m, const float* __restrict__ X, int rows,
                                                         const float* __restrict__ ds) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -132,9 +282,8 @@ __global__ void __launch_bounds__(MH) k_mlp_bwd_weights(MlpDev m, const float* _
   } else if (p < O_W2) {
     const int u = p - O_B1;
     for (int r = 0; r < rows; ++r) g += m.dH1[(size_t)r * MH + u];
-  } else if (p < O_B2) {  // W2[v][u] = sum_r dH2[r][v] h1[r][u]
-    const int q = p - O_W2, v = q / MH, u = q % MH;
-    for (int r = 0; r < rows; ++r) g = fmaf(m.dH2[(size_t)r * MH + v], m.H1[(size_t)r * MH + u], g);
+  } else if (p < O_B2) {  // W2: written by the tensor-core kernel
+    return;
   } else if (p < O_W3) {
     const int v = p - O_B2;
     for (int r = 0; r < rows; ++r) g += m.dH2[(size_t)r * MH + v];
@@ -351,7 +500,7 @@ extern "C" int cvq_mlp_forward(cvq_mlp* m, const float* X_dev, int rows, float* 
   const double fl = 2.0 * rows * (MF * MH + MH * MH + MH);
   const double by = 2.0 * (MF * MH + MH * MH + MH) + 4.0 * rows * (MF + 1 + 2 * MH);
   const int pi = internal_prof_mlp_begin(st, by, fl);
-  k_mlp_fwd<<<(rows + MRT - 1) / MRT, MH, 0, st>>>(m->d, X_dev, rows, scores_dev);
+  k_mlp_fwd_tc<<<(rows + TC_ROWS - 1) / TC_ROWS, MH, 0, st>>>(m->d, X_dev, rows, scores_dev);
   internal_prof_end(pi, st);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CVQ_OK : cuda_err(e, "mlp forward");
@@ -363,11 +512,16 @@ extern "C" int cvq_mlp_backward(cvq_mlp* m, const float* X_dev, int rows, const 
   cudaStream_t st = (cudaStream_t)stream;
   if (rows > 0) {
     const int pi = internal_prof_mlp_begin(st, 2.0 * MH * MH + 4.0 * rows * (1 + 4 * MH), 2.0 * rows * MH * MH);
-    k_mlp_bwd_rows<<<(rows + MRT - 1) / MRT, MH, 0, st>>>(m->d, rows, dscores_dev);
+    k_mlp_bwd_rows_tc<<<(rows + TC_ROWS - 1) / TC_ROWS, MH, 0, st>>>(m->d, rows, dscores_dev);
     internal_prof_end(pi, st);
   }
-  const int pi = internal_prof_mlp_begin(st, 4.0 * NPARAM + 4.0 * rows * (MF + 1 + 4 * MH),
-                                         2.0 * rows * (MF * MH + MH * MH + MH));
+  {
+    const int pi = internal_prof_mlp_begin(st, 8.0 * rows * 2 * MH + 4.0 * MH * MH, 2.0 * rows * MH * MH);
+    k_mlp_dw2_tc<<<(MH / DW_T) * (MH / DW_T), MH, 0, st>>>(m->d, rows);
+    internal_prof_end(pi, st);
+  }
+  const int pi = internal_prof_mlp_begin(st, 4.0 * NPARAM + 4.0 * rows * (MF + 1 + 2 * MH),
+                                         2.0 * rows * (MF * MH + MH));
   k_mlp_bwd_weights<<<(NPARAM + MH - 1) / MH, MH, 0, st>>>(m->d, X_dev, rows, dscores_dev);
   internal_prof_end(pi, st);
   const cudaError_t e = cudaGetLastError();

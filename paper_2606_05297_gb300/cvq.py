@@ -434,6 +434,7 @@ def _batch_sigs(L):
     L.cvq_batch_energy_and_grad.argtypes = [vp, vp, vp, vp, vp]
     L.cvq_batch_info.argtypes = [vp, ip, ip, ip, C.POINTER(C.c_int64)]
     L.cvq_batch_set_active.argtypes = [vp, ip, vp]
+    L.cvq_batch_screen.argtypes = [vp, vp, ip, ip, vp, vp]
     return L
 
 
@@ -495,6 +496,29 @@ class Batch:
                                                _dev(self.grad, "f64", self.offsets[-1], "grad"), _stream(stream)),
                "cvq_batch_energy_and_grad")
         return self.E, self.grad[: self.offsets[-1]]
+
+    def screen(self, subsets=None, out=None, stream=None):
+        """Eq. (grad) on the current state U(theta) psi0 of every active instance
+        (theta as last loaded into self.theta), for every pool element
+        (subsets None) or for subsets[i] (a list of pool indices per instance).
+        Returns the packed device tensor and the per-instance output offsets."""
+        import torch
+        K = [p.K for p in self._keep[1]]
+        counts = [0 if self.n_ops[i] < 0 else (K[i] if subsets is None else len(subsets[i])) for i in range(self.n)]
+        off = [0]
+        for c in counts:
+            off.append(off[-1] + c)
+        if out is None:
+            out = torch.empty(max(off[-1], 1), dtype=torch.float64, device="cuda")
+        if subsets is None:
+            so, sa = None, None
+        else:
+            so = (C.c_int * (self.n + 1))(*[0] + [sum(len(subsets[q]) for q in range(i + 1)) for i in range(self.n)])
+            flat = [int(k) for sub in subsets for k in sub]
+            sa = (C.c_int * max(1, len(flat)))(*flat)
+        _check(lib().cvq_batch_screen(self.h, _dev(self.theta, "f64", self.offsets[-1], "theta"), so, sa,
+                                      _dev(out, "f64", off[-1], "out"), _stream(stream)), "cvq_batch_screen")
+        return out, off
 
     def info(self):
         k, it, ly = C.c_int(), C.c_int(), C.c_int()

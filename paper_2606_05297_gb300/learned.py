@@ -25,6 +25,7 @@ import numpy as np
 
 from . import cvq
 from .adapt import Adapt, BFGS, TIE_REL, select
+from .batched import BatchedAdapt
 from .workloads import OP_TYPES, Model, Op
 
 NFEAT = 32
@@ -318,3 +319,117 @@ def hit_rate(scorer: "cvq.Scorer", Xs: Sequence[np.ndarray], gs: Sequence[np.nda
         top = np.lexsort((np.arange(len(s)), -s))[:top_k]
         hits += int(select(g)[0] in set(int(t) for t in top))
     return hits / max(len(Xs), 1)
+
+
+class LearnedBatchedAdapt(BatchedAdapt):
+    """Learned proposal on the batched engine: lockstep ADAPT over many
+    instances (a U/J sweep) in which every iteration makes one scorer forward
+    over the pool rows of every live instance, one batched exact screen of
+    each instance's top_k (its whole pool every full_every-th iteration of
+    that instance, and whenever its top_k gradients all fall below the
+    threshold), and one lockstep BFGS whose evaluations share batched graph
+    launches.  The scorer keeps training on every full screen."""
+
+    def __init__(self, models: Sequence[Model], pool_ops: Sequence[Sequence[Op]], init_occ, scorer: "cvq.Scorer",
+                 trainer: Optional[Trainer] = None, top_k: int = 8, full_every: int = 5, train_steps: int = 20,
+                 max_ops_hint: int = 160, **kw):
+        import torch
+        super().__init__(models, pool_ops, init_occ, **kw)
+        self.scorer = scorer
+        self.trainer = trainer
+        self.top_k = top_k
+        self.full_every = full_every
+        self.train_steps = train_steps
+        self.max_ops_hint = max_ops_hint
+        self.fbs = [FeatureBuilder(m, p) for m, p in zip(models, pool_ops)]
+        self.hists = [History(K) for K in self.K]
+        self.n_adapt = [0] * len(models)
+        self.stats = ProposalStats()
+        self.state_ws = [s.workspace(p, self.n_max) for s, p in zip(self.sectors, self.pools)]
+        self._Xd = torch.empty((max(sum(self.K), 1), NFEAT), dtype=torch.float32, device="cuda")
+
+    def _rows(self, live):
+        rows = {}
+        for i in live:
+            psi = cvq.apply_ansatz(self.sectors[i], self.pools[i], self.ids[i], self.theta[i], self.psi0[i],
+                                   ws=self.state_ws[i])
+            f = cvq.features(self.sectors[i], psi, self.fbs[i].pairs).cpu().numpy()
+            rows[i] = self.fbs[i].rows(f, self.hists[i], self.n_adapt[i] / self.max_ops_hint)
+        return rows
+
+    def _full_screen(self, i, X, g, top):
+        self.stats.full_screens += 1
+        self.stats.exact_gradients += self.K[i]
+        self.hists[i].record(np.arange(self.K[i]), g)
+        k, gmax = select(g)
+        if top is not None and gmax > 0.0:
+            self.stats.judged += 1
+            self.stats.hits += int(k in set(int(t) for t in top))
+            self.stats.regret.append(1.0 - float(np.abs(g[top]).max()) / gmax)
+        if self.trainer is not None:
+            self.trainer.add(X, g)
+        return k, gmax
+
+    def choose(self, grad_tol: float):
+        torch = self.torch
+        n = len(self.ids)
+        live = [i for i in range(n) if not self.done[i]]
+        if not live:
+            return {}
+        rows = self._rows(live)
+        Xcat = np.concatenate([rows[i] for i in live]).astype(np.float32)
+        self._Xd[: Xcat.shape[0]].copy_(torch.from_numpy(Xcat))
+        s_all = self.scorer.forward(self._Xd[: Xcat.shape[0]]).cpu().numpy()
+        top, o = {}, 0
+        for i in live:
+            s = s_all[o:o + self.K[i]]
+            o += self.K[i]
+            top[i] = np.lexsort((np.arange(self.K[i]), -s))[: self.top_k]
+        full = {i: self.n_adapt[i] % self.full_every == 0 for i in live}
+        subs = [[] for _ in range(n)]
+        for i in live:
+            subs[i] = list(range(self.K[i])) if full[i] else [int(t) for t in top[i]]
+        gs = self.screen_all(subs)
+        chosen, confirm, trained = {}, [], False
+        for i in live:
+            g = gs[i]
+            if full[i]:
+                chosen[i] = self._full_screen(i, rows[i], g, top[i])
+                trained = True
+                continue
+            sub = subs[i]
+            self.stats.subset_screens += 1
+            self.stats.exact_gradients += len(sub)
+            self.hists[i].record(sub, g)
+            a = np.abs(g)
+            m = float(a.max())
+            if m < grad_tol:  # the proposal sees nothing left: confirm with the whole pool
+                confirm.append(i)
+                continue
+            chosen[i] = (min(sub[j] for j in np.nonzero(a >= m * (1.0 - TIE_REL))[0]), m)
+        if confirm:
+            subs2 = [list(range(self.K[i])) if i in confirm else [] for i in range(n)]
+            gs2 = self.screen_all(subs2)
+            for i in confirm:
+                chosen[i] = self._full_screen(i, rows[i], gs2[i], None)
+                trained = True
+        if trained and self.trainer is not None:
+            self.trainer.train(self.train_steps)
+        for i in live:
+            self.hists[i].tick()
+        for i in list(chosen):
+            if chosen[i][1] < grad_tol or len(self.ids[i]) + 1 > self.n_max:
+                self.done[i] = True
+                del chosen[i]
+        return chosen
+
+    def after_step(self, grown):
+        for i, (k, gmax) in grown.items():
+            tr = [r for r in self.trace[i]]
+            E_before = tr[-2]["E"] if len(tr) >= 2 else None
+            h = self.hists[i]
+            h.selected[k] += 1
+            h.last_op = k
+            h.last_gmax = gmax
+            h.last_dE = abs(tr[-1]["E"] - E_before) if E_before is not None else 0.0
+            self.n_adapt[i] += 1

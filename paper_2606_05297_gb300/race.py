@@ -64,9 +64,112 @@ def run_arm(make, E0, max_ops, grad_tol=1e-6):
     return a, hist, reached, time.perf_counter() - t0
 
 
+def sweep_instances(count: int, seed: int, Ls=(4, 5), U_range=(1.0, 4.0)):
+    """A U/J sweep of small open Bose-Hubbard chains (N = L, Eq. BoseHubbard in
+    its literal sign), all-pairs pool, Mott start plus the HVA warm start:
+    instances on which ADAPT reaches |E - E0| < 1e-6 within the paper's budget
+    of about 160 operators."""
+    from . import workloads as W
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        L = int(Ls[q % len(Ls)])
+        U = float(np.exp(rng.uniform(np.log(U_range[0]), np.log(U_range[1]))))
+        m = W.bose_hubbard(L, L, J=1.0, U=U, periodic=False, name=f"bh_open_L{L}_U{U:.3f}")
+        warm = W.hva_layer(m)
+        out.append((m, W.bh_allpairs_pool(L), W.mott_occupation(L, L), warm, W.warm_start_thetas(len(warm), seed + q)))
+    return out
+
+
+def _reach(reached, dE, t, it):
+    for th in THRESHOLDS:
+        if dE < th and str(th) not in reached:
+            reached[str(th)] = dict(seconds=t, iterations=it)
+
+
+def _summary(per, t_total, n):
+    """Time at which every instance had reached each threshold (None if some never did)."""
+    out = {}
+    for th in THRESHOLDS:
+        ts = [p["reached"].get(str(th), {}).get("seconds") for p in per]
+        out[str(th)] = None if any(t is None for t in ts) else max(ts)
+    return dict(seconds=t_total, all_reached=out, instances_reaching_tol=sum(str(THRESHOLDS[-1]) in p["reached"] for p in per),
+                instances=n, dE_final=[p["dE"] for p in per], iterations=[p["iterations"] for p in per])
+
+
+def race_sweep(insts, E0s, scorer, trainer, max_ops=160, hessian_recycling=True, top_k=8, full_every=5,
+               tol=1e-6):
+    """Wall time to |E - E0| < tol on every instance of a sweep: plain
+    full-screen ADAPT run instance after instance, the same method on the
+    batched engine (lockstep BFGS, batched screens), and the learned proposal
+    on the batched engine."""
+    from . import adapt, batched, learned
+    n = len(insts)
+    arms = {}
+    # plain, one instance after another
+    t0 = time.perf_counter()
+    per = []
+    for (m, pool, occ, warm, wth), E0 in zip(insts, E0s):
+        A = adapt.Adapt(m, pool, occ, warm, wth, n_max=max_ops + len(warm) + 1, hessian_recycling=hessian_recycling)
+        A.optimise_warm_start()
+        reached, dE, it = {}, abs(A.trace[-1]["E"] - E0), 0
+        _reach(reached, dE, time.perf_counter() - t0, 0)
+        while it < max_ops and dE >= tol:
+            rec = A.step()
+            if rec is None:
+                break
+            it += 1
+            dE = abs(rec["E"] - E0)
+            _reach(reached, dE, time.perf_counter() - t0, it)
+        per.append(dict(dE=dE, iterations=it, reached=reached))
+    arms["plain_sequential"] = _summary(per, time.perf_counter() - t0, n)
+
+    def run_batched(make):
+        t0 = time.perf_counter()
+        B = make()
+        B.optimise_warm_start()
+        reached = [dict() for _ in range(n)]
+        dE = [abs(B.trace[i][-1]["E"] - E0s[i]) for i in range(n)]
+        its = [0] * n
+        for i in range(n):
+            _reach(reached[i], dE[i], time.perf_counter() - t0, 0)
+        for _ in range(max_ops):
+            stop = [d < tol for d in dE]
+            if all(stop):
+                break
+            last = [len(B.trace[i]) for i in range(n)]
+            if B.step(stop=stop) == 0:
+                break
+            t = time.perf_counter() - t0
+            for i in range(n):
+                if len(B.trace[i]) > last[i]:
+                    its[i] += 1
+                    dE[i] = abs(B.trace[i][-1]["E"] - E0s[i])
+                    _reach(reached[i], dE[i], t, its[i])
+        per = [dict(dE=dE[i], iterations=its[i], reached=reached[i]) for i in range(n)]
+        return B, _summary(per, time.perf_counter() - t0, n)
+
+    models = [x[0] for x in insts]
+    pools = [x[1] for x in insts]
+    occs = [x[2] for x in insts]
+    warms = [x[3] for x in insts]
+    wths = [x[4] for x in insts]
+    nm = max_ops + max(len(w) for w in warms) + 1
+    _, arms["plain_batched"] = run_batched(lambda: batched.BatchedAdapt(
+        models, pools, occs, warms, wths, n_max=nm, hessian_recycling=hessian_recycling))
+    B, arms["learned_batched"] = run_batched(lambda: learned.LearnedBatchedAdapt(
+        models, pools, occs, scorer, trainer=trainer, top_k=top_k, full_every=full_every, warm_ops=warms,
+        warm_theta=wths, n_max=nm, hessian_recycling=hessian_recycling))
+    st = B.stats
+    arms["learned_batched"].update(exact_gradients=st.exact_gradients, full_screens=st.full_screens,
+                                   subset_screens=st.subset_screens, judged=st.judged, hits=st.hits)
+    return arms
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--target", choices=["kitaev", "bh"], default="kitaev")
+    ap.add_argument("--target", choices=["kitaev", "bh", "sweep"], default="kitaev")
+    ap.add_argument("--count", type=int, default=8, help="instances of the sweep target")
     ap.add_argument("--L", type=int, default=10)
     ap.add_argument("--U", type=float, default=3.4, help="U/J of the Bose-Hubbard target")
     ap.add_argument("--d", type=int, default=6)
@@ -91,6 +194,21 @@ def main(argv=None):
     losses = tr.train(a.train_steps)
     t_train = time.perf_counter() - t0
 
+    if a.target == "sweep":
+        insts = sweep_instances(a.count, 100)
+        E0s = []
+        for (m, *_rest) in insts:
+            E0s.append(adapt.ground_energy(cvq.Sector(m)))
+        arms = race_sweep(insts, E0s, scorer, tr, max_ops=a.max_ops, hessian_recycling=a.hessian_recycling,
+                          top_k=a.top_k, full_every=a.full_every)
+        out = dict(target=dict(model="open Bose-Hubbard chains L in {4, 5}, N = L, U/J log-uniform [1, 4]",
+                               instances=[x[0].name for x in insts], E0=E0s, pool="all pairs",
+                               tolerance=1e-6),
+                   training=dict(lists=len(tr.X), rows=tr.rows(), seconds=t_train,
+                                 loss_first=losses[0] if losses else None, loss_last=losses[-1] if losses else None),
+                   arms=arms, top_k=a.top_k, full_every=a.full_every, hessian_recycling=a.hessian_recycling)
+        print(json.dumps(out), flush=True)
+        return out
     if a.target == "bh":
         m = W.bose_hubbard(a.L, a.L, J=1.0, U=a.U, periodic=True)
         pool = W.bh_allpairs_pool(a.L)

@@ -159,6 +159,26 @@ static void check_bh(int L, int N) {
     }
 }
 
+// n / q by multiply-high against plain division: every divisor of a sector
+// (1..16), the ends of the range, and a pseudo-random sweep of [0, 2^31).
+static void check_div() {
+  for (uint32_t q = 1; q <= 16; ++q) {
+    uint32_t m;
+    int sh;
+    div_magic(q, &m, &sh);
+    const uint32_t edge[] = {0u, 1u, q - 1, q, q + 1, 0x7fffffffu, 0x7ffffffeu, 0x40000000u, 0x3fffffffu};
+    for (uint32_t n : edge) CHECK(div_by_mul(n, m, sh) == n / q, "div q=%u n=%u", q, n);
+    uint64_t z = 0x9E3779B97F4A7C15ull * q;
+    for (int k = 0; k < 200000; ++k) {
+      z ^= z << 13;
+      z ^= z >> 7;
+      z ^= z << 17;
+      const uint32_t n = (uint32_t)(z & 0x7fffffffu);
+      CHECK(div_by_mul(n, m, sh) == n / q, "div q=%u n=%u", q, n);
+    }
+  }
+}
+
 static void check_bkc(int L, int d, int parity) {
   SectorDev S;
   memset(&S, 0, sizeof S);
@@ -177,7 +197,12 @@ static void check_bkc(int L, int d, int parity) {
   std::vector<int> cur(L);
   enum_tuples(L, d, tup, cur, 0, keep_par, parity);
   CHECK((int64_t)tup.size() == S.dim, "BKC dim");
+  // the 64-bit division path, then the multiply-high path the kernels take
   for (int64_t x = 0; x < S.dim; ++x) CHECK(bkc_unrank(x, S) == pack(tup[x]), "bkc unrank L=%d d=%d", L, d);
+  set_bkc_div(S);
+  CHECK(S.div32 == 1, "BKC small sector takes the 32-bit division");
+  for (int64_t x = 0; x < S.dim; ++x)
+    CHECK(bkc_unrank(x, S) == pack(tup[x]), "bkc unrank (multiply-high) L=%d d=%d", L, d);
   // gate orbits (two-mode and single-mode): every index covered once
   for (int i = 0; i < L; ++i)
     for (int j = -1; j < L; ++j) {
@@ -211,6 +236,7 @@ int main() {
   for (auto& c : bh) check_bh(c[0], c[1]);
   const int bkc[][3] = {{1, 4, 0}, {1, 6, 1}, {2, 2, 0}, {2, 4, 1}, {3, 4, 0}, {3, 6, 1}, {4, 4, 0}, {4, 2, 1}};
   for (auto& c : bkc) check_bkc(c[0], c[1], c[2]);
+  check_div();
   printf("%s (%d failures)\n", failures ? "FAILED" : "OK", failures);
   return failures ? 1 : 0;
 }

@@ -156,3 +156,56 @@ def test_batch_c4_instances_sampled():
         o = b.offsets[i]
         assert abs(E[i] - Er) <= E_REL * max(1.0, abs(Er))
         assert np.max(np.abs(g[o:o + len(ids)] - gr)) <= G_ABS
+
+
+def _screen_check(b, ans, pools, psi0, oss, subsets, out, off, skip=()):
+    out = out.cpu().numpy()
+    for i, (ids, th) in enumerate(ans):
+        if ids is None or i in skip:
+            continue
+        sub = list(range(len(pools[i]))) if subsets is None else subsets[i]
+        assert off[i + 1] - off[i] == len(sub)
+        if not sub:
+            continue
+        psi = oss[i].apply_ansatz([pools[i][k] for k in ids], th, psi0[i].cpu().numpy())
+        gref = oss[i].screen([pools[i][k] for k in sub], psi)
+        got = out[off[i]:off[i + 1]]
+        assert np.max(np.abs(got - gref)) < G_ABS, (i, np.max(np.abs(got - gref)))
+
+
+@pytest.mark.parametrize("kind", ["bh", "bkc"])
+def test_batch_screen_matches_oracle(kind):
+    """cvq_batch_screen: Eq. (grad) of every instance's whole pool, then of
+    per-instance subsets (one of them empty), on U(theta) psi0 of each
+    instance's ansatz, against the oracle's screen of the oracle's forward
+    state; an instance left out has no outputs, and a paused instance's
+    outputs are not written.  Repeated calls are bit-identical."""
+    import torch
+    if kind == "bh":
+        models = [W.c1_model(), W.bose_hubbard(5, 5, J=1.0, U=3.0, periodic=True),
+                  W.bose_hubbard(3, 7, J=0.7, U=-1.5, periodic=True), W.bose_hubbard(4, 2, J=1.0, U=1.0, periodic=False)]
+        pools = [_bh_pool(m.L) for m in models]
+        depths = [12, 20, 0, None]
+    else:
+        models = [W.kitaev_kerr(4, 4, t=1.0, Delta=0.6, K=0.3), W.kitaev_kerr(3, 6, t=1.0, Delta=0.2, K=0.5),
+                  W.kitaev_paper(3, 4, J=1.0, Delta=0.5, mu=-2.7, U=-1.0, periodic=True, parity=1)]
+        pools = [_bkc_pool(m.L) for m in models]
+        depths = [16, 9, 5]
+    b, secs, pls, psi0, ans, oss = _setup(models, pools, depths, 400)
+    th = _theta_vec(ans)
+    b.theta[: th.numel()].copy_(th)
+    out, off = b.screen()
+    _screen_check(b, ans, pools, psi0, oss, None, out, off)
+    out2, _ = b.screen()
+    assert np.array_equal(out.cpu().numpy(), out2.cpu().numpy())
+    rng = np.random.default_rng(1)
+    subsets = [sorted({int(k) for k in rng.integers(0, len(p), 6)} | {len(p) - 1}) for p in pools]
+    subsets[1] = []
+    out, off = b.screen(subsets)
+    _screen_check(b, ans, pools, psi0, oss, subsets, out, off)
+    # pause instance 0: its outputs keep what the buffer held
+    b.set_active([i != 0 and ans[i][0] is not None for i in range(len(ans))])
+    out.fill_(float("nan"))
+    out, off = b.screen(subsets, out=out)
+    assert np.all(np.isnan(out.cpu().numpy()[off[0]:off[1]]))
+    _screen_check(b, ans, pools, psi0, oss, subsets, out, off, skip=(0,))
