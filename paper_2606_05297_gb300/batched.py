@@ -13,6 +13,8 @@ The work-item size and CTAs per SM of the batched launches are chosen by
 """
 from __future__ import annotations
 
+import json
+import os
 from typing import Dict, List, Optional, Sequence
 
 import numpy as np
@@ -24,6 +26,37 @@ from .workloads import Model, Op
 TILES = (4096, 16384, 65536, 262144)
 CTAS = (1, 2)
 _TUNED: Dict[tuple, tuple] = {}
+# Schedules found by autotune, kept across processes: one JSON object per
+# GPU model and set of sector sizes (the build folder is never committed).
+TUNE_CACHE = os.environ.get("CVQ_TUNE_CACHE",
+                            os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "batch_tune.json"))
+
+
+def _tune_key(sectors) -> str:
+    import torch
+    return torch.cuda.get_device_name() + "|" + ",".join(str(d) for d in sorted(s.dim for s in sectors))
+
+
+def _load_tuned() -> Dict[str, list]:
+    try:
+        with open(TUNE_CACHE) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_tuned(key: str, tile: int, ctas: int) -> None:
+    d = _load_tuned()
+    d[key] = [int(tile), int(ctas)]
+    try:
+        os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
+        tmp = f"{TUNE_CACHE}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(d, f)
+        os.replace(tmp, TUNE_CACHE)
+    except OSError:
+        pass  # an unwritable cache only costs a re-tune in the next process
 
 
 def time_eval(batch: "cvq.Batch", reps: int = 3) -> float:
@@ -42,8 +75,13 @@ def time_eval(batch: "cvq.Batch", reps: int = 3) -> float:
 
 def autotune(batch: "cvq.Batch", sectors, tiles=TILES, ctas=CTAS, reps: int = 3, cache: bool = True) -> dict:
     """Time every (tile, CTAs per SM) schedule on the batch's current ansatz
-    and keep the fastest.  Results are cached per set of sector sizes."""
-    key = (tuple(sorted(s.dim for s in sectors)),)
+    and keep the fastest.  Results are cached per GPU model and set of sector
+    sizes, in memory and in TUNE_CACHE."""
+    key = _tune_key(sectors)
+    if cache and key not in _TUNED:
+        hit = _load_tuned().get(key)
+        if hit and len(hit) == 2:
+            _TUNED[key] = (int(hit[0]), int(hit[1]))
     if cache and key in _TUNED:
         tile, c = _TUNED[key]
         batch.set_schedule(tile, c)
@@ -58,6 +96,8 @@ def autotune(batch: "cvq.Batch", sectors, tiles=TILES, ctas=CTAS, reps: int = 3,
                 best = (tile, c, ms)
     batch.set_schedule(best[0], best[1])
     _TUNED[key] = (best[0], best[1])
+    if cache:
+        _store_tuned(key, best[0], best[1])
     return dict(tile=best[0], ctas_per_sm=best[1], ms=best[2], table=table, cached=False)
 
 

@@ -78,3 +78,18 @@ def test_oracle_hessian_recycling_reduces_evaluations():
     nfev = lambda r: sum(t["nfev"] for t in r["trace"] if t["kind"] == "adapt")
     assert ops(plain)[:4] == ops(hr)[:4]
     assert nfev(hr) < (2 / 3) * nfev(plain)
+
+
+def test_autotune_cache_round_trip(tmp_path, monkeypatch):
+    """The batched engine's schedule cache survives a new process: entries
+    written by one store are read back, merged with later ones, and a
+    corrupt file reads as empty."""
+    from paper_2606_05297_gb300 import batched
+    path = tmp_path / "tune.json"
+    monkeypatch.setattr(batched, "TUNE_CACHE", str(path))
+    assert batched._load_tuned() == {}
+    batched._store_tuned("GB300|6435,24310", 16384, 2)
+    batched._store_tuned("GB300|35", 4096, 1)
+    assert batched._load_tuned() == {"GB300|6435,24310": [16384, 2], "GB300|35": [4096, 1]}
+    path.write_text("{not json")
+    assert batched._load_tuned() == {}
