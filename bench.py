@@ -24,6 +24,9 @@ Beside the headline the JSON line carries
     algorithmic GB/s and fraction of the measured HBM bandwidth;
   * c4_batched: the batched engine on the 64-instance Bose-Hubbard sweep;
   * mlp: forward and backward latency of the proposal scorer on a 210-row pool;
+  * race: wall time to |E - E0| < 1e-6 on every instance of a U/J sweep of
+    small chains, plain full-screen ADAPT against the batched engine with and
+    without the learned proposal;
   * cpu_baseline: the FP64 oracle on the host cores, 1 thread and all threads,
     on a bounded sample scaled to the same iteration.
 
@@ -70,6 +73,7 @@ def parse():
     ap.add_argument("--no-c4", action="store_true", help="skip the batched 64-instance sweep measurement")
     ap.add_argument("--no-c5", action="store_true", help="skip the L=10 Kitaev-chain kernel measurement")
     ap.add_argument("--no-mlp", action="store_true", help="skip the scorer latency measurement")
+    ap.add_argument("--no-race", action="store_true", help="skip the learned-vs-plain wall-time race")
     ap.add_argument("--instances", type=int, default=len(U_VALUES),
                     help="use the first n of the U/J instances (profiling runs)")
     a = ap.parse_args()
@@ -389,6 +393,37 @@ def mlp_leg(rows=210, reps=200):
             "note": "back-to-back launches on one stream, CUDA events"}
 
 
+def race_leg(count=6, max_ops=100):
+    """Wall time to |E - E0| < 1e-6 on every instance of a U/J sweep of small
+    open Bose-Hubbard chains (L = N = 4, all-pairs pool, Mott start + warm
+    start, Hessian recycling in every arm): plain full-screen ADAPT instance
+    after instance, the same method on the batched engine, and the learned
+    proposal (scorer trained on plain-ADAPT traces of other systems) on the
+    batched engine."""
+    from paper_2606_05297_gb300 import adapt, cvq, learned, race
+    t0 = time.perf_counter()
+    scorer = cvq.Scorer(65536, seed=1)
+    tr = learned.Trainer(scorer, lr=1e-3)
+    for (m, pool, occ, wops, wth) in race.trace_sources(True):
+        learned.collect_traces(m, pool, occ, tr, warm_ops=wops, warm_theta=wth, max_ops=20, top_k=8)
+    losses = tr.train(300)
+    t_train = time.perf_counter() - t0
+    insts = race.sweep_instances(count, 100)
+    E0s = [adapt.ground_energy(cvq.Sector(x[0])) for x in insts]
+    arms = race.race_sweep(insts, E0s, scorer, tr, max_ops=max_ops, hessian_recycling=True)
+    out = {"workload": f"{count} open Bose-Hubbard chains L = N = 4, U/J log-uniform [1, 4] (seed 100), all-pairs "
+                       "pool of 22, Mott start + HVA warm start, Hessian recycling; tolerance 1e-6 against Lanczos E0",
+           "training_seconds": t_train, "training_lists": len(tr.X), "loss_first": losses[0], "loss_last": losses[-1]}
+    for k, v in arms.items():
+        out[k] = {"seconds_to_1e-6_all": v["all_reached"]["1e-06"], "seconds": v["seconds"],
+                  "instances_reaching_1e-6": v["instances_reaching_tol"], "all_reached": v["all_reached"],
+                  "iterations": v["iterations"]}
+        for extra in ("exact_gradients", "full_screens", "subset_screens", "judged", "hits"):
+            if extra in v:
+                out[k][extra] = v[extra]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -495,6 +530,7 @@ def run_ours(args):
     fixed = fixed_ansatz_leg()
     c5 = None if args.no_c5 else c5_kernel_leg(hbm)
     mlp = None if args.no_mlp else mlp_leg()
+    race_out = None if (args.no_race or rank != 0) else race_leg()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -542,7 +578,7 @@ def run_ours(args):
                        "l2": "256 MB buffer written between steps",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "fixed_ansatz": fixed, "c5_kernels": c5, "c4_batched": c4, "mlp": mlp,
+            "fixed_ansatz": fixed, "c5_kernels": c5, "c4_batched": c4, "mlp": mlp, "race": race_out,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in stats.items()},
         }
         if FIXED_NFEV is not None:

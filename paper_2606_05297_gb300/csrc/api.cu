@@ -583,15 +583,16 @@ static int set_pool(const cvq_sector* s, const cvq_op* ops, int K, int dc, cvq_p
 
 // Index tables of the tiled gates (k_tile.cu): one per distinct gate
 // structure (modes, move) of the pool's block generators.  Each region is one
-// block class of two or more members; its blocks are the class's orbits, in
-// orbit order, packed TILE_T / b to a tile.  Synchronises.
+// orbit class; its tiles hold G whole orbits each (every block of two or more
+// members of those orbits), G = T / (members per orbit).  Synchronises.
 static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
   const SectorDev& S = p->sec->S;
   struct Plan {
     int type, i, j;
     std::vector<TileRegion> reg;
+    std::vector<TileSub> sub;
     int64_t ntiles = 0, max_count = 0;
-    size_t idx_off = 0, reg_off = 0;
+    size_t idx_off = 0, reg_off = 0, sub_off = 0;
   };
   std::vector<Plan> plans;
   std::map<std::array<int, 7>, int> where;
@@ -619,32 +620,49 @@ static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
     pl.type = p->op_type[k];
     pl.i = p->op_i[k];
     pl.j = p->op_j[k];
-    for (int cls = 0; cls < t.nclass; ++cls)
+    for (int cls = 0; cls < t.nclass; ++cls) {
+      const int64_t cnt = orbits(t, cls);
+      if (cnt <= 0) continue;
+      if (cnt > INT32_MAX) return fail(CVQ_EINVAL, "too many orbits in one class for the tiled gates");
+      TileRegion R;
+      memset(&R, 0, sizeof R);
+      R.sub0 = (int)pl.sub.size();
+      int per_orbit = 0;
       for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
         const BlockDesc& bd = pb.blk[t.blk_base + bi];
         if (bd.size < 2) continue;  // zero generator: identity
-        const int64_t cnt = orbits(t, cls);
-        if (cnt <= 0) continue;
-        if (cnt > INT32_MAX) return fail(CVQ_EINVAL, "too many orbits in one class for the tiled gates");
-        TileRegion R;
-        memset(&R, 0, sizeof R);
-        R.b = bd.size;
-        R.nbt = T / bd.size;
-        R.count = (int)cnt;
-        R.u_off = bd.u_off;
-        R.f_off = bd.f_off;
-        R.bi = bi;
-        R.cls = cls;
-        R.tile0 = pl.ntiles;
-        pl.ntiles += (cnt + R.nbt - 1) / R.nbt;
-        pl.max_count = std::max(pl.max_count, cnt);
-        pl.reg.push_back(R);
+        TileSub u;
+        memset(&u, 0, sizeof u);
+        u.b = bd.size;
+        u.u_off = bd.u_off;
+        u.f_off = bd.f_off;
+        u.bi = bi;
+        pl.sub.push_back(u);
+        per_orbit += bd.size;
       }
+      R.nsub = (int)pl.sub.size() - R.sub0;
+      if (R.nsub == 0) continue;
+      if (R.nsub > TILE_MAX_SUB || per_orbit > T)
+        return fail(CVQ_EINVAL, "an orbit of %d members in %d blocks does not fit a tile", per_orbit, R.nsub);
+      R.G = T / per_orbit;
+      int off = 0;
+      for (int c = R.sub0; c < R.sub0 + R.nsub; ++c) {
+        pl.sub[c].off = off;
+        off += pl.sub[c].b * R.G;
+      }
+      R.count = (int)cnt;
+      R.cls = cls;
+      R.tile0 = pl.ntiles;
+      pl.ntiles += (cnt + R.G - 1) / R.G;
+      pl.max_count = std::max(pl.max_count, cnt);
+      pl.reg.push_back(R);
+    }
+    if (pl.sub.size() > 64) return fail(CVQ_EINVAL, "%zu block classes exceed the tiled gates' 64", pl.sub.size());
     where[key] = (int)plans.size();
     plan_of[k] = (int)plans.size();
     plans.push_back(std::move(pl));
   }
-  p->op_tiles.assign(p->K, TileMap{nullptr, nullptr, 0, 0, 0});
+  p->op_tiles.assign(p->K, TileMap{nullptr, nullptr, nullptr, 0, 0, 0, 0});
   auto a256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t total = 0;
   for (auto& pl : plans) {
@@ -652,6 +670,8 @@ static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
     total = a256(total + (size_t)pl.ntiles * T * sizeof(int));
     pl.reg_off = total;
     total = a256(total + pl.reg.size() * sizeof(TileRegion));
+    pl.sub_off = total;
+    total = a256(total + pl.sub.size() * sizeof(TileSub));
   }
   if (total == 0) return CVQ_OK;
   const size_t o_bad = total;  // count of member indices outside [0, dim) (must stay 0)
@@ -664,10 +684,12 @@ static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
   for (auto& pl : plans) {
     int* idx = (int*)(base + pl.idx_off);
     TileRegion* reg = (TileRegion*)(base + pl.reg_off);
+    TileSub* sub = (TileSub*)(base + pl.sub_off);
     if ((e = cudaMemset(idx, 0xFF, (size_t)pl.ntiles * T * sizeof(int))) != cudaSuccess ||
         (e = cudaMemcpy(reg, pl.reg.data(), pl.reg.size() * sizeof(TileRegion), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = launch_tile_build(S, pl.i, pl.j, p->types[pl.type], p->P, reg, (int)pl.reg.size(), pl.max_count, slots,
-                               idx, bad, 0)) != cudaSuccess)
+        (e = cudaMemcpy(sub, pl.sub.data(), pl.sub.size() * sizeof(TileSub), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = launch_tile_build(S, pl.i, pl.j, p->types[pl.type], p->P, reg, sub, (int)pl.reg.size(), pl.max_count,
+                               slots, idx, bad, 0)) != cudaSuccess)
       return cuda_fail(e, "gate table build");
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "gate table build");
@@ -679,7 +701,8 @@ static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
     if (plan_of[k] < 0) continue;
     const Plan& pl = plans[plan_of[k]];
     p->op_tiles[k] = TileMap{(const int*)(base + pl.idx_off), (const TileRegion*)(base + pl.reg_off),
-                             (int)pl.reg.size(), slots, pl.ntiles};
+                             (const TileSub*)(base + pl.sub_off), (int)pl.reg.size(), (int)pl.sub.size(), slots,
+                             pl.ntiles};
   }
   return CVQ_OK;
 }
@@ -1102,7 +1125,7 @@ static GateArg gate_arg(const cvq_pool* p, int op, const cdf* U) {
   g.j = p->op_j[op];
   g.t = p->types[p->op_type[op]];
   g.U = U;
-  g.tm = p->op_tiles.empty() ? TileMap{nullptr, nullptr, 0, 0, 0} : p->op_tiles[op];
+  g.tm = p->op_tiles.empty() ? TileMap{nullptr, nullptr, nullptr, 0, 0, 0, 0} : p->op_tiles[op];
   return g;
 }
 

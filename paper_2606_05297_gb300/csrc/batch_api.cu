@@ -56,6 +56,9 @@ int cuda_err(cudaError_t e, const char* what) {
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Shared memory one CTA of the small-instance kernel may use (tables + psi + lambda).
+constexpr int kSmallSmem = 160 * 1024;
+
 }  // namespace
 
 struct cvq_batch {
@@ -87,6 +90,10 @@ struct cvq_batch {
   int n_red = 0, n_gates = 0, n_items = 0, n_theta = 0;
   size_t smem = 0;
   int maxblk = 0;  // most blocks of any block-gate type of the batch's pools
+  // every sector fits one CTA's shared memory: one CTA per instance runs the
+  // whole evaluation (k_batch_small) instead of one launch per layer
+  bool small = false;
+  size_t small_smem = 0;
   // graph
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -237,11 +244,14 @@ int build_plan(cvq_batch* b) {
   b->n_theta = off;
   std::vector<BSeg> seg_all;
   std::vector<std::vector<int>> seg_id(n);
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
+    b->inst[i].seg0 = (int)seg_all.size();
+    b->inst[i].nseg = (b->n_ops[i] < 0) ? -1 : (int)segs[i].size();
     for (auto& s : segs[i]) {
       seg_id[i].push_back((int)seg_all.size());
       seg_all.push_back(s);
     }
+  }
   // layers: conversion, smax forward, matvec, smax reverse
   std::vector<std::vector<BItem>> layers(2 * smax + 2);
   std::vector<char> adj(2 * smax + 2, 0);
@@ -332,18 +342,7 @@ int build_plan(cvq_batch* b) {
   return CVQ_OK;
 }
 
-int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
-  drop_graph(b);
-  cudaStream_t st = b->cap;
-  BCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
-  cudaError_t e = cudaMemsetAsync(b->counters_d, 0, sizeof(int) * b->layer_n.size(), st);
-  if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
-  const int grid = b->sms * b->ctas_per_sm;
-  for (size_t l = 0; l < b->layer_n.size() && e == cudaSuccess; ++l)
-    e = launch_batch_layer(b->kind, b->layer_adj[l] != 0, grid, b->smem, b->inst_d, b->segs_d,
-                           b->items_d + b->layer_off[l], b->layer_n[l], b->counters_d + l, b->ids_d, theta,
-                           b->active_d, b->partial_d, st);
-  if (e == cudaSuccess) e = launch_batch_reduce(b->red_d, b->n_red, b->partial_d, b->active_d, E, grad, st);
+int finish_capture(cvq_batch* b, cudaStream_t st, cudaError_t e, const double* theta, double* E, double* grad) {
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(st, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -360,6 +359,30 @@ int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
   b->g_E = E;
   b->g_grad = grad;
   return CVQ_OK;
+}
+
+int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
+  drop_graph(b);
+  cudaStream_t st = b->cap;
+  BCUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = cudaSuccess;
+  if (b->small) {
+    e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
+    if (e == cudaSuccess)
+      e = launch_batch_small(b->kind, 0, b->n, b->smem, std::max(b->n_max, 1), b->small_smem, b->inst_d, b->segs_d,
+                             b->ids_d, theta, b->active_d, E, grad, st);
+    return finish_capture(b, st, e, theta, E, grad);
+  }
+  e = cudaMemsetAsync(b->counters_d, 0, sizeof(int) * b->layer_n.size(), st);
+  if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
+  // a layer needs no more CTAs than it has items (small instances leave most of the grid idle)
+  const int grid_max = b->sms * b->ctas_per_sm;
+  for (size_t l = 0; l < b->layer_n.size() && e == cudaSuccess; ++l)
+    e = launch_batch_layer(b->kind, b->layer_adj[l] != 0, std::min(grid_max, b->layer_n[l]), b->smem, b->inst_d, b->segs_d,
+                           b->items_d + b->layer_off[l], b->layer_n[l], b->counters_d + l, b->ids_d, theta,
+                           b->active_d, b->partial_d, st);
+  if (e == cudaSuccess) e = launch_batch_reduce(b->red_d, b->n_red, b->partial_d, b->active_d, E, grad, st);
+  return finish_capture(b, st, e, theta, E, grad);
 }
 
 // The plan of the batched screen for the given subsets (subset_off == NULL:
@@ -471,11 +494,16 @@ int capture_screen(cvq_batch* b, const double* theta, double* grad) {
   cudaError_t e = cudaMemsetAsync(b->s_counters, 0, sizeof(int) * (nl + 1), st);
   if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
   const int grid = b->sms * b->ctas_per_sm;
-  for (int l = 0; l < nfwd && e == cudaSuccess; ++l)
-    e = launch_batch_layer(b->kind, false, grid, b->smem, b->inst_d, b->segs_d, b->items_d + b->layer_off[l],
-                           b->layer_n[l], b->s_counters + l, b->ids_d, theta, b->active_d, b->partial_d, st);
+  if (b->small && e == cudaSuccess)  // forward sweep and H psi of every instance, one CTA each
+    e = launch_batch_small(b->kind, 1, b->n, b->smem, std::max(b->n_max, 1), b->small_smem, b->inst_d, b->segs_d,
+                           b->ids_d, theta, b->active_d, nullptr, nullptr, st);
+  for (int l = 0; l < nfwd && e == cudaSuccess && !b->small; ++l)
+    e = launch_batch_layer(b->kind, false, std::min(grid, b->layer_n[l]), b->smem, b->inst_d, b->segs_d,
+                           b->items_d + b->layer_off[l], b->layer_n[l], b->s_counters + l, b->ids_d, theta,
+                           b->active_d, b->partial_d, st);
   if (e == cudaSuccess)
-    e = launch_batch_screen(b->kind, grid, b->inst_d, b->s_items, b->s_nitems, b->s_counters + nl, b->active_d,
+    e = launch_batch_screen(b->kind, std::min(grid, b->s_nitems), b->inst_d, b->s_items, b->s_nitems,
+                            b->s_counters + nl, b->active_d,
                             b->s_screens, b->s_desc, b->s_partial, st);
   if (e == cudaSuccess) e = launch_batch_reduce(b->s_red, b->s_nred, b->s_partial, b->active_d, b->s_z, nullptr, st);
   if (e == cudaSuccess) e = launch_batch_screen_out(b->s_outs, b->s_nouts, b->s_z, b->active_d, grad, st);
@@ -578,12 +606,22 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
     return errf(CVQ_EINVAL, "gate tables need %zu bytes of shared memory", smem);
   }
   b->smem = smem;
+  {
+    int64_t dmax = 0;
+    for (int i = 0; i < n_inst; ++i) dmax = std::max<int64_t>(dmax, b->S[i].dim);
+    b->smem = a256(smem);
+    // every instance has at most n_max segments
+    const size_t need = batch_small_smem(b->smem, std::max(n_max, 1), dmax);
+    b->small = need <= (size_t)kSmallSmem;
+    b->small_smem = need;
+  }
   cudaDeviceProp prop;
   cudaError_t e = cudaGetDeviceProperties(&prop, b->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&b->state, total);
   if (e == cudaSuccess) e = cudaMalloc(&b->inst_d, sizeof(BInst) * n_inst);
-  if (e == cudaSuccess) e = set_batch_smem_limit((int)smem);
+  if (e == cudaSuccess) e = set_batch_smem_limit((int)b->smem);
+  if (e == cudaSuccess && b->small) e = set_batch_small_smem_limit(kSmallSmem);
   if (e != cudaSuccess) {
     cvq_batch_destroy(b);
     return cuda_err(e, "batch allocation");
@@ -687,7 +725,7 @@ extern "C" int cvq_batch_info(const cvq_batch* b, int* kernels_per_eval, int* it
   if (!b) return errf(CVQ_EINVAL, "null argument");
   int nk = 0;
   for (int n : b->layer_n) nk += n > 0;
-  if (kernels_per_eval) *kernels_per_eval = nk + (b->n_gates > 0) + (b->n_red > 0);
+  if (kernels_per_eval) *kernels_per_eval = b->small ? 1 + (b->n_gates > 0) : nk + (b->n_gates > 0) + (b->n_red > 0);
   if (items) *items = b->n_items;
   if (layers) *layers = (int)b->layer_n.size();
   if (n_params) *n_params = b->n_theta;

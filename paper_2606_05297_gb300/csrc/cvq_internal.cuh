@@ -251,29 +251,37 @@ struct PoolDev {
   const double* lam;
 };
 
-// Tiled block gates.  For one gate structure (modes, move) every block of
-// two or more members is listed once in a table of sector indices, grouped by
-// block class ("region": all blocks of one size, one unitary and one set of
-// generator factors).  A region is cut into tiles of T = TILE_T x S slots (S
-// slots per thread of a CTA) holding nbt = T / b whole blocks, member-major
-// within the tile: slot a * nbt + k is member a of the tile's block k, so
-// consecutive slots are the same member of neighbouring blocks.  Unused
-// slots hold -1.  Large sectors take S = TILE_S_LARGE, so that each thread
-// keeps several loads in flight from HBM; small ones S = 1, so that every
-// CTA gets work.
+// Tiled block gates.  For one gate structure (modes, move) the sector indices
+// of every block of two or more members are listed in a table, orbit group by
+// orbit group.  Orbits of one class ("region": same block structure) are cut
+// into tiles of G whole orbits, G = T / (members per orbit), T = TILE_T x S
+// slots (S slots per thread of a CTA), so that a tile holds every amplitude of
+// its orbits and neighbouring amplitudes are loaded by the same tile.  Within
+// a tile the blocks of one class ("sub-block" c of the region, size b_c) take
+// b_c G consecutive slots from off_c, member-major: slot off_c + a G + k is
+// member a of the block of orbit k.  Unused slots hold -1.  Large sectors take
+// S = TILE_S_LARGE, so that each thread keeps several loads in flight from
+// HBM; small ones S = 1, so that every CTA gets work.
 constexpr int TILE_T = NTHREADS;
 constexpr int TILE_S_LARGE = 4;
 constexpr int64_t TILE_LARGE_DIM = 1 << 22;
-struct TileRegion {
-  int b, nbt, count;     // block size, blocks per tile, blocks in the region
+constexpr int TILE_MAX_SUB = 32;  // block classes of one orbit class
+struct TileSub {
+  int b, off;            // block size, first slot within the tile
   int u_off, f_off;      // the class's unitary (within a gate's U) and generator factors (within the type's F)
-  int bi, cls, pad;      // block index within the type's list, orbit class (table build only)
+  int bi, pad;           // block index within the type's list (table build only)
+};
+struct TileRegion {
+  int G, count;          // orbits per tile, orbits in the region
+  int sub0, nsub;        // its sub-blocks: subs[sub0 .. sub0 + nsub)
+  int cls, pad;          // orbit class (table build only)
   int64_t tile0;         // first tile of the region
 };
 struct TileMap {
   const int* idx;           // ntiles x (TILE_T x slots) sector indices; null: the gate has no table
   const TileRegion* reg;    // nreg regions, in tile order
-  int nreg, slots;          // slots: S, the tile slots per thread
+  const TileSub* sub;       // nsub sub-blocks of all regions
+  int nreg, nsub, slots;    // slots: S, the tile slots per thread
   int64_t ntiles;
 };
 
@@ -346,6 +354,7 @@ struct BInst {
   cdf *psi, *lam, *U;   // df state, adjoint state, block unitaries (n_max x ustride)
   const double2* psi0;  // reference state (complex128)
   int ustride, ids_off, theta_off;
+  int seg0, nseg;       // the instance's segments in the plan (nseg = -1: left out)
 };
 
 // One segment of one instance's ansatz: a block gate (m = 1) or a run of m
@@ -392,6 +401,16 @@ cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const 
 cudaError_t set_batch_smem_limit(int bytes);
 cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, const int* active, double* E,
                                 double* grad, cudaStream_t st);
+// Batches whose sectors all fit in shared memory: one CTA per instance runs
+// the whole evaluation with the states in shared memory.  Mode 0: energy and
+// gradient into E and grad; mode 1: the forward sweep and lambda = H psi
+// only, both written to the instance's global psi and lambda buffers (the
+// batched screen reads them).
+size_t batch_small_smem(size_t tab_bytes, int seg_cap, int64_t dim_max);
+cudaError_t launch_batch_small(int kind, int mode, int n_inst, size_t tab_bytes, int seg_cap, size_t smem_total,
+                               const BInst* insts, const BSeg* segs, const int* ids, const double* theta,
+                               const int* active, double* E, double* grad, cudaStream_t st);
+cudaError_t set_batch_small_smem_limit(int bytes);
 cudaError_t launch_batch_screen(int kind, int grid, const BInst* insts, const BItem* items, int nitems, int* counter,
                                 const int* active, const BScreen* screens, const int4* desc, double* partial,
                                 cudaStream_t st);
@@ -434,7 +453,8 @@ cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const c
 // Tiled gates: the table of one gate structure, and the in-place forward gate
 // and reverse step that read it (k_tile.cu).
 cudaError_t launch_tile_build(const SectorDev& S, int i, int j, const TypeDesc& t, PoolDev P, const TileRegion* reg_dev,
-                              int nreg, int64_t max_count, int tile_slots, int* idx, int* bad, cudaStream_t st);
+                              const TileSub* sub_dev, int nreg, int64_t max_count, int tile_slots, int* idx, int* bad,
+                              cudaStream_t st);
 cudaError_t launch_tile_gate(const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial, bool adjoint,
                              cudaStream_t st);
 cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial,

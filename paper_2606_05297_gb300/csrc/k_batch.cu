@@ -287,6 +287,161 @@ cudaError_t launch_batch_screen_out(const BScreenOut* outs, int n, const double*
   return cudaGetLastError();
 }
 
+// One CTA per instance: the instance's whole evaluation with psi and lambda
+// in shared memory (the sector must fit; the host checks).  Every segment's
+// descriptor and generator structure is copied into shared memory once, at
+// the start, so a segment only waits for its gate tables (staged in front of
+// the states) before it runs.  Every partial sum of the instance lives in
+// this CTA, so energies and gradients are written directly (2 x the
+// fixed-order CTA sum for the gradients).
+// Shared layout: [tables: tab_bytes][BSeg x seg_cap][TypeDesc x seg_cap][gi, gj x seg_cap][psi][lambda].
+__host__ __device__ __forceinline__ size_t small_meta_bytes(int seg_cap) {
+  const size_t b = (size_t)seg_cap * (sizeof(BSeg) + sizeof(TypeDesc) + sizeof(int2));
+  return (b + 255) & ~(size_t)255;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_batch_small(int mode, size_t tab_bytes, int seg_cap, const BInst* __restrict__ insts,
+                  const BSeg* __restrict__ segs, const int* __restrict__ ids, const double* __restrict__ theta,
+                  const int* __restrict__ active, double* __restrict__ E, double* __restrict__ grad) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ SectorDev S;
+  __shared__ int64_t G64[LMAX][DMAX + 1];
+  __shared__ int32_t G32[LMAX][DMAX + 1];
+  const int i = blockIdx.x;
+  if (!active[i]) return;
+  const BInst& I = insts[i];
+  const int nseg = I.nseg;
+  if (nseg < 0 || nseg > seg_cap) return;  // left out (the host sizes seg_cap for every instance)
+  BSeg* sg_all = reinterpret_cast<BSeg*>(smem + tab_bytes);
+  TypeDesc* td_all = reinterpret_cast<TypeDesc*>(sg_all + seg_cap);
+  int2* ij_all = reinterpret_cast<int2*>(td_all + seg_cap);
+  cdf* psi = reinterpret_cast<cdf*>(smem + tab_bytes + small_meta_bytes(seg_cap));
+  const int64_t dim = I.S.dim;
+  cdf* lam = psi + dim;
+  copy_words(&S, &I.S, sizeof(SectorDev));
+  copy_words(sg_all, segs + I.seg0, (int)(sizeof(BSeg) * nseg));
+  for (int64_t x = threadIdx.x; x < dim; x += NTHREADS) {
+    const double2 v = I.psi0[x];
+    psi[x] = make_cdf(df_from_double(v.x), df_from_double(v.y));
+  }
+  __syncthreads();
+  if (KIND == CVQ_BH) {
+    load_G(G64, S);
+    load_G(G32, S);
+  }
+  // generator structure and modes of every block-gate segment, fetched together
+  for (int k = 0; k < nseg; ++k) {
+    if (sg_all[k].isdiag) continue;
+    const GateArg& ga = I.ops[ids[I.ids_off + sg_all[k].k0]];
+    copy_words(&td_all[k], &ga.t, sizeof(TypeDesc));
+    if (threadIdx.x == 0) ij_all[k] = make_int2(ga.i, ga.t.single ? -1 : ga.j);
+  }
+  __syncthreads();
+  auto segment = [&](int k, bool adj) {
+    const BSeg& sg = sg_all[k];
+    if (sg.isdiag) {
+      cdf(*T)[DMAX] = reinterpret_cast<cdf(*)[DMAX]>(smem);
+      cdf(*TP)[DMAX * DMAX] = reinterpret_cast<cdf(*)[DMAX * DMAX]>(smem + sizeof(cdf) * LMAX * DMAX);
+      diag_tables(sg, S, theta + I.theta_off + sg.k0, T, TP);
+      __syncthreads();
+      dfacc acc[BATCH_RUN];
+#pragma unroll
+      for (int q = 0; q < BATCH_RUN; ++q) acc_zero(acc[q]);
+      if (adj) diag_run_range<KIND, true, BATCH_RUN>(S, G64, T, TP, sg, psi, psi, lam, threadIdx.x, dim, NTHREADS, acc);
+      else diag_run_range<KIND, false, BATCH_RUN>(S, G64, T, TP, sg, psi, psi, lam, threadIdx.x, dim, NTHREADS, acc);
+      if (adj) {
+#pragma unroll
+        for (int q = 0; q < BATCH_RUN; ++q) {
+          if (q < sg.m) {
+            const double s = block_sum(acc_to_double(acc[q]));
+            if (threadIdx.x == 0) grad[I.theta_off + sg.k0 + q] = 2.0 * s;
+          }
+        }
+      }
+    } else {
+      const TypeDesc& t = td_all[k];
+      const int gi = ij_all[k].x, gj = ij_all[k].y;
+      const GateSmem m = gate_smem(smem, t);
+      if (adj) stage_gate<true>(m, t, I.U + (size_t)sg.k0 * I.ustride, I.P);
+      else stage_gate<false>(m, t, I.U + (size_t)sg.k0 * I.ustride, I.P);
+      __syncthreads();
+      dfacc gacc;
+      acc_zero(gacc);
+      if (KIND == CVQ_BKC) {
+        const int64_t items = bkc_items(S, t.single ? 1 : 2);
+        if (adj) {
+          if (t.realu) bkc_gate_range<true, true>(S, gi, gj, t, m, threadIdx.x, items, NTHREADS, psi, psi, lam, gacc);
+          else bkc_gate_range<true, false>(S, gi, gj, t, m, threadIdx.x, items, NTHREADS, psi, psi, lam, gacc);
+        } else {
+          if (t.realu) bkc_gate_range<false, true>(S, gi, gj, t, m, threadIdx.x, items, NTHREADS, psi, psi, lam, gacc);
+          else bkc_gate_range<false, false>(S, gi, gj, t, m, threadIdx.x, items, NTHREADS, psi, psi, lam, gacc);
+        }
+      } else {
+        for (int c = 0; c < t.nchunks; ++c) {
+          const int4 ch = I.P.chunks[t.chunk_base + c];
+          if (adj) {
+            if (t.realu) bh_gate_chunk<true, true>(S, G32, gi, gj, t, m, ch, psi, psi, lam, gacc);
+            else bh_gate_chunk<true, false>(S, G32, gi, gj, t, m, ch, psi, psi, lam, gacc);
+          } else {
+            if (t.realu) bh_gate_chunk<false, true>(S, G32, gi, gj, t, m, ch, psi, psi, lam, gacc);
+            else bh_gate_chunk<false, false>(S, G32, gi, gj, t, m, ch, psi, psi, lam, gacc);
+          }
+        }
+      }
+      if (adj) {
+        const double s = block_sum(acc_to_double(gacc));
+        if (threadIdx.x == 0) grad[I.theta_off + sg.k0] = 2.0 * s;
+      }
+    }
+    __syncthreads();  // the state is complete and the shared tables are free again
+  };
+  for (int k = 0; k < nseg; ++k) segment(k, false);
+  {
+    HSmem& H = *reinterpret_cast<HSmem*>(smem);
+    load_htabs(H, S);
+    __syncthreads();
+    dfacc eacc;
+    acc_zero(eacc);
+    apply_H_range<KIND>(S, G64, H, psi, lam, threadIdx.x, dim, NTHREADS, eacc);
+    const double s = block_sum(acc_to_double(eacc));
+    if (threadIdx.x == 0 && mode == 0) E[i] = s;
+    __syncthreads();
+  }
+  if (mode == 1) {  // the forward state and H psi for the screen layer
+    for (int64_t x = threadIdx.x; x < dim; x += NTHREADS) {
+      I.psi[x] = psi[x];
+      I.lam[x] = lam[x];
+    }
+    return;
+  }
+  for (int k = nseg - 1; k >= 0; --k) segment(k, true);
+}
+
+size_t batch_small_smem(size_t tab_bytes, int seg_cap, int64_t dim_max) {
+  return tab_bytes + small_meta_bytes(seg_cap) + 2 * sizeof(cdf) * (size_t)dim_max;
+}
+
+cudaError_t launch_batch_small(int kind, int mode, int n_inst, size_t tab_bytes, int seg_cap, size_t smem_total,
+                               const BInst* insts, const BSeg* segs, const int* ids, const double* theta,
+                               const int* active, double* E, double* grad, cudaStream_t st) {
+  if (n_inst <= 0) return cudaSuccess;
+  if (kind == CVQ_BH)
+    k_batch_small<CVQ_BH><<<n_inst, NTHREADS, smem_total, st>>>(mode, tab_bytes, seg_cap, insts, segs, ids, theta,
+                                                               active, E, grad);
+  else
+    k_batch_small<CVQ_BKC><<<n_inst, NTHREADS, smem_total, st>>>(mode, tab_bytes, seg_cap, insts, segs, ids, theta,
+                                                                active, E, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t set_batch_small_smem_limit(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_small<CVQ_BH>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_small<CVQ_BKC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
 cudaError_t launch_batch_build(const BInst* insts, const int2* gates, int ngates, int maxblk, const int* ids,
                                const double* theta, const int* active, cudaStream_t st) {
   if (ngates <= 0 || maxblk <= 0) return cudaSuccess;

@@ -39,6 +39,29 @@ struct MlpDev {
 
 __device__ __forceinline__ float bf(bf16 v) { return __bfloat162float(v); }
 
+// Gradient of one parameter other than W2 (p outside [O_W2, O_B2)) as a sum
+// over rows in row order.
+__device__ __forceinline__ void param_grad(const MlpDev& m, const float* __restrict__ X, int rows,
+                                           const float* __restrict__ ds, int p) {
+  float g = 0.f;
+  if (p < O_B1) {  // W1[u][f] = sum_r dH1[r][u] x[r][f]
+    const int u = p / MF, f = p % MF;
+    for (int r = 0; r < rows; ++r) g = fmaf(m.dH1[(size_t)r * MH + u], X[(size_t)r * MF + f], g);
+  } else if (p < O_W2) {
+    const int u = p - O_B1;
+    for (int r = 0; r < rows; ++r) g += m.dH1[(size_t)r * MH + u];
+  } else if (p < O_W3) {
+    const int v = p - O_B2;
+    for (int r = 0; r < rows; ++r) g += m.dH2[(size_t)r * MH + v];
+  } else if (p < O_B3) {  // w3[v] = sum_r ds[r] h2[r][v]
+    const int v = p - O_W3;
+    for (int r = 0; r < rows; ++r) g = fmaf(ds[r], m.H2[(size_t)r * MH + v], g);
+  } else {
+    for (int r = 0; r < rows; ++r) g += ds[r];
+  }
+  m.G[p] = g;
+}
+
 // ------------------------------------------------------------ tensor-core layers
 //
 // The two 256 x 256 products (the hidden layer forward, and its transpose and
@@ -215,8 +238,17 @@ __global__ void __launch_bounds__(MH) k_mlp_bwd_rows_tc(MlpDev m, int rows, cons
 
 // dW2[v][u] = sum_r dH2[r][v] H1[r][u] on the tensor cores: each CTA one
 // 64 x 64 output tile, rows taken 16 at a time in order.
-constexpr int DW_T = 64;
-__global__ void __launch_bounds__(MH) k_mlp_dw2_tc(MlpDev m, int rows) {
+// CTAs past the 16 tiles compute every other parameter's gradient on the CUDA
+// cores (one thread per parameter), so the whole weight gradient is one launch.
+constexpr int DW_T = 64, DW_TILES = (MH / DW_T) * (MH / DW_T);
+constexpr int DW_OTHER = O_W2 + (NPARAM - O_B2);  // parameters outside W2
+__global__ void __launch_bounds__(MH) k_mlp_dw2_tc(MlpDev m, const float* __restrict__ X, int rows,
+                                                   const float* __restrict__ ds) {
+  if (blockIdx.x >= DW_TILES) {
+    const int q = (blockIdx.x - DW_TILES) * blockDim.x + threadIdx.x;
+    if (q < DW_OTHER) param_grad(m, X, rows, ds, q < O_W2 ? q : q - O_W2 + O_B2);
+    return;
+  }
   __shared__ __align__(16) bf16 Ah[DW_T][16 + TC_PAD], Al[DW_T][16 + TC_PAD];  // [v][r]
   __shared__ __align__(16) bf16 Bh[DW_T][16 + TC_PAD], Bl[DW_T][16 + TC_PAD];  // [u][r]
   const int v0 = (blockIdx.x / (MH / DW_T)) * DW_T, u0 = (blockIdx.x % (MH / DW_T)) * DW_T;
@@ -267,33 +299,6 @@ __global__ void __launch_bounds__(MH) k_mlp_dw2_tc(MlpDev m, int rows) {
       m.G[O_W2 + v * MH + u + 1] = c[j][2 * h + 1];
     }
   }
-}
-
-// Weight gradients as sums over rows in row order: one thread per parameter
-// (W2 comes from k_mlp_dw2_tc).
-__global__ void __launch_bounds__(MH) k_mlp_bwd_weights(MlpDev m, const float* __restrict__ X, int rows,
-                                                        const float* __restrict__ ds) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= NPARAM) return;
-  float g = 0.f;
-  if (p < O_B1) {  // W1[u][f] = sum_r dH1[r][u] x[r][f]
-    const int u = p / MF, f = p % MF;
-    for (int r = 0; r < rows; ++r) g = fmaf(m.dH1[(size_t)r * MH + u], X[(size_t)r * MF + f], g);
-  } else if (p < O_W2) {
-    const int u = p - O_B1;
-    for (int r = 0; r < rows; ++r) g += m.dH1[(size_t)r * MH + u];
-  } else if (p < O_B2) {  // W2: written by the tensor-core kernel
-    return;
-  } else if (p < O_W3) {
-    const int v = p - O_B2;
-    for (int r = 0; r < rows; ++r) g += m.dH2[(size_t)r * MH + v];
-  } else if (p < O_B3) {  // w3[v] = sum_r ds[r] h2[r][v]
-    const int v = p - O_W3;
-    for (int r = 0; r < rows; ++r) g = fmaf(ds[r], m.H2[(size_t)r * MH + v], g);
-  } else {
-    for (int r = 0; r < rows; ++r) g += ds[r];
-  }
-  m.G[p] = g;
 }
 
 // Adam on the master weights, then the bf16 copies.
@@ -516,14 +521,11 @@ extern "C" int cvq_mlp_backward(cvq_mlp* m, const float* X_dev, int rows, const 
     internal_prof_end(pi, st);
   }
   {
-    const int pi = internal_prof_mlp_begin(st, 8.0 * rows * 2 * MH + 4.0 * MH * MH, 2.0 * rows * MH * MH);
-    k_mlp_dw2_tc<<<(MH / DW_T) * (MH / DW_T), MH, 0, st>>>(m->d, rows);
+    const int pi = internal_prof_mlp_begin(st, 4.0 * NPARAM + 4.0 * rows * (MF + 1 + 4 * MH),
+                                           2.0 * rows * (MF * MH + MH * MH + MH));
+    k_mlp_dw2_tc<<<DW_TILES + (DW_OTHER + MH - 1) / MH, MH, 0, st>>>(m->d, X_dev, rows, dscores_dev);
     internal_prof_end(pi, st);
   }
-  const int pi = internal_prof_mlp_begin(st, 4.0 * NPARAM + 4.0 * rows * (MF + 1 + 2 * MH),
-                                         2.0 * rows * (MF * MH + MH));
-  k_mlp_bwd_weights<<<(NPARAM + MH - 1) / MH, MH, 0, st>>>(m->d, X_dev, rows, dscores_dev);
-  internal_prof_end(pi, st);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CVQ_OK : cuda_err(e, "mlp backward");
 }

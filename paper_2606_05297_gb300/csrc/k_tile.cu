@@ -4,15 +4,17 @@
 //
 // A gate acts block-diagonally (the blocks of one orbit are chains of
 // occupation pairs joined by the generator's move).  Here a CTA takes one
-// tile of TILE_T table slots at a time: each thread loads one sector index
-// (coalesced) and the amplitude it names, the tile is staged in shared
-// memory, and each thread then forms one output amplitude of its block from
-// the staged members and the block unitary (also in shared memory).  No
-// thread computes a rank, every load of a tile is in flight at once, and the
-// next tile's loads are issued before the current tile is multiplied.  The
-// blocks of one tile are disjoint from every other tile's, so the gate runs
-// in place.  Blocks of one member (zero generator: identity) are not in the
-// table and are never touched.
+// tile at a time: G whole orbits of one class, every block of two or more
+// members of them, TILE_T x S table slots.  Each thread loads the S sector
+// indices of its slots (coalesced) and the amplitudes they name, the tile is
+// staged in shared memory, and each thread then forms the output amplitudes
+// of its slots from the staged members of their blocks and the block
+// unitary (also in shared memory).  No thread computes a rank, every load of
+// a tile is in flight at once, neighbouring amplitudes (whole orbits) are
+// loaded by the same tile, and the next tile's loads are issued before the
+// current tile is multiplied.  The blocks of one tile are disjoint from every
+// other tile's, so the gate runs in place.  Blocks of one member (zero
+// generator: identity) are not in the table and are never touched.
 #include "cvq_internal.cuh"
 #include "k_gate_impl.cuh"
 
@@ -20,17 +22,18 @@ namespace cvq {
 
 // ------------------------------------------------------------ table build
 
-// For region blockIdx.y: the sector index of every member of every block.
+// For region blockIdx.y: the sector index of every member of every block of
+// every orbit of the region's class.
 template <int KIND>
 __global__ void __launch_bounds__(NTHREADS) k_tile_build(const __grid_constant__ SectorDev S, int i, int j,
                                                          const __grid_constant__ TypeDesc t, PoolDev P,
-                                                         const TileRegion* __restrict__ reg, int T,
+                                                         const TileRegion* __restrict__ reg,
+                                                         const TileSub* __restrict__ subs, int T,
                                                          int* __restrict__ idx, int* __restrict__ bad) {
   __shared__ int64_t G[LMAX][DMAX + 1];
   if (KIND == CVQ_BH) load_G(G, S);
   __syncthreads();
   const TileRegion R = reg[blockIdx.y];
-  const int2* mem = P.mem + t.mem_base + P.blk[t.blk_base + R.bi].mem_off;
   const int nm = (j >= 0) ? 2 : 1;
   // an index outside the sector would make the gate kernels read and write
   // out of bounds: it is stored as an unused slot and counted instead
@@ -43,31 +46,37 @@ __global__ void __launch_bounds__(NTHREADS) k_tile_build(const __grid_constant__
     }
   };
   for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < R.count; o += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t pos0 = (R.tile0 + o / R.nbt) * T + (o % R.nbt);
+    const int64_t tpos = (R.tile0 + o / R.G) * T + (o % R.G);
+    BkcIdx kx;
+    BhIdx hx;
     if (KIND == CVQ_BKC) {
-      BkcIdx ix;
-      ix.si = S.stride[i];
-      ix.sj = (j >= 0) ? S.stride[j] : 0;
+      kx.si = S.stride[i];
+      kx.sj = (j >= 0) ? S.stride[j] : 0;
       const int64_t items = bkc_items(S, nm);
       const int64_t tg = (S.L == nm) ? 0 : (int64_t)R.cls * (items / 2) + o;
       int q;
-      bkc_orbit(S, i, j, tg, items, ix.f0, q);
-      for (int l = 0; l < R.b; ++l) put(pos0 + (int64_t)l * R.nbt, ix(mem[l]));
+      bkc_orbit(S, i, j, tg, items, kx.f0, q);
     } else {
-      const uint64_t w0 = bh_orbit_of_class(S, G, i, j, R.cls, o);
-      const BhIdx ix = bh_idx_of<int64_t>(S, G, i, j, w0);
-      for (int l = 0; l < R.b; ++l) put(pos0 + (int64_t)l * R.nbt, ix(mem[l]));
+      hx = bh_idx_of<int64_t>(S, G, i, j, bh_orbit_of_class(S, G, i, j, R.cls, o));
+    }
+    for (int c = R.sub0; c < R.sub0 + R.nsub; ++c) {
+      const TileSub u = subs[c];
+      const int2* mem = P.mem + t.mem_base + P.blk[t.blk_base + u.bi].mem_off;
+      for (int l = 0; l < u.b; ++l)
+        put(tpos + u.off + (int64_t)l * R.G, KIND == CVQ_BKC ? kx(mem[l]) : hx(mem[l]));
     }
   }
 }
 
 cudaError_t launch_tile_build(const SectorDev& S, int i, int j, const TypeDesc& t, PoolDev P, const TileRegion* reg_dev,
-                              int nreg, int64_t max_count, int tile_slots, int* idx, int* bad, cudaStream_t st) {
+                              const TileSub* sub_dev, int nreg, int64_t max_count, int tile_slots, int* idx, int* bad,
+                              cudaStream_t st) {
   if (nreg <= 0) return cudaSuccess;
   const int64_t want = (max_count + NTHREADS - 1) / NTHREADS;
   const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 4 * NBLK)), (unsigned)nreg);
-  if (S.kind == CVQ_BH) k_tile_build<CVQ_BH><<<grid, NTHREADS, 0, st>>>(S, i, j, t, P, reg_dev, TILE_T * tile_slots, idx, bad);
-  else k_tile_build<CVQ_BKC><<<grid, NTHREADS, 0, st>>>(S, i, j, t, P, reg_dev, TILE_T * tile_slots, idx, bad);
+  const int T = TILE_T * tile_slots;
+  if (S.kind == CVQ_BH) k_tile_build<CVQ_BH><<<grid, NTHREADS, 0, st>>>(S, i, j, t, P, reg_dev, sub_dev, T, idx, bad);
+  else k_tile_build<CVQ_BKC><<<grid, NTHREADS, 0, st>>>(S, i, j, t, P, reg_dev, sub_dev, T, idx, bad);
   return cudaGetLastError();
 }
 
@@ -76,15 +85,15 @@ cudaError_t launch_tile_build(const SectorDev& S, int i, int j, const TypeDesc& 
 // Shared memory of a tiled gate: the gate's block unitaries, the generator
 // factors (reverse), the regions, then the staged amplitudes of one tile
 // (psi, and lambda in the reverse step).
-__host__ __device__ __forceinline__ size_t tile_head_bytes(const TypeDesc& t, int nreg, bool adj) {
+__host__ __device__ __forceinline__ size_t tile_head_bytes(const TypeDesc& t, int nreg, int nsub, bool adj) {
   size_t b = (size_t)t.nu * sizeof(cdf);
   b += (((size_t)(adj ? t.nf : 0) * sizeof(float2)) + 15) & ~(size_t)15;
-  b += (size_t)nreg * sizeof(TileRegion);
+  b += (size_t)nreg * sizeof(TileRegion) + (size_t)nsub * sizeof(TileSub);
   return (b + 15) & ~(size_t)15;
 }
 
-__host__ __device__ __forceinline__ size_t tile_smem_bytes(const TypeDesc& t, int nreg, bool adj, int slots) {
-  return tile_head_bytes(t, nreg, adj) + (size_t)TILE_T * slots * sizeof(cdf) * (adj ? 2 : 1);
+__host__ __device__ __forceinline__ size_t tile_smem_bytes(const TypeDesc& t, int nreg, int nsub, bool adj, int slots) {
+  return tile_head_bytes(t, nreg, nsub, adj) + (size_t)TILE_T * slots * sizeof(cdf) * (adj ? 2 : 1);
 }
 
 // The S slots of one thread in one tile (slot threadIdx.x + q TILE_T), as
@@ -128,19 +137,20 @@ __global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ ? 2 : 3)) k_tile_g
                                                                        cdf* psi, cdf* lam,
                                                                        double* __restrict__ partial) {
   extern __shared__ __align__(16) char smem[];
-  constexpr int T = TILE_T * S;
   const TypeDesc& t = g.t;
   const TileMap& tm = g.tm;
   cdf* Us = reinterpret_cast<cdf*>(smem);
   float2* Fs = reinterpret_cast<float2*>(Us + t.nu);
   char* after_f = reinterpret_cast<char*>(Fs) + ((((size_t)(ADJ ? t.nf : 0) * sizeof(float2)) + 15) & ~(size_t)15);
   TileRegion* Rs = reinterpret_cast<TileRegion*>(after_f);
-  cdf* Sp = reinterpret_cast<cdf*>(smem + tile_head_bytes(t, tm.nreg, ADJ));
-  cdf* Sl = Sp + T;
+  TileSub* Ss = reinterpret_cast<TileSub*>(Rs + tm.nreg);
+  cdf* Sp = reinterpret_cast<cdf*>(smem + tile_head_bytes(t, tm.nreg, tm.nsub, ADJ));
+  cdf* Sl = Sp + TILE_T * S;
   for (int e = threadIdx.x; e < t.nu; e += blockDim.x) Us[e] = g.U[e];
   if (ADJ)
     for (int e = threadIdx.x; e < t.nf; e += blockDim.x) Fs[e] = P.F[t.f_base + e];
   for (int e = threadIdx.x; e < tm.nreg; e += blockDim.x) Rs[e] = tm.reg[e];
+  for (int e = threadIdx.x; e < tm.nsub; e += blockDim.x) Ss[e] = tm.sub[e];
   __syncthreads();
   const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
   dfacc gacc;
@@ -148,6 +158,13 @@ __global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ ? 2 : 3)) k_tile_g
   int64_t tile = blockIdx.x;
   TileSlots<S> cur;
   if (tile < tm.ntiles) tile_load<ADJ, S>(cur, tm, tile, psi, lam);
+  // Where each of this thread's slots sits in its tile depends only on the
+  // region (the tiles of a CTA climb through the regions in order), so it is
+  // worked out once per region: the block class c, member a and block k of
+  // slot threadIdx.x + q TILE_T, packed as c | a << 6 | k << 10.
+  int reg = -1, G = 1;
+  int64_t reg_end = -1;
+  int dec[S];
   while (tile < tm.ntiles) {
     const int64_t next = tile + gridDim.x;
     __syncthreads();  // every thread has finished reading the previous tile
@@ -160,27 +177,43 @@ __global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ ? 2 : 3)) k_tile_g
     }
     __syncthreads();
     if (next < tm.ntiles) tile_load<ADJ, S>(cur, tm, next, psi, lam);  // in flight during the multiply
-    const TileRegion R = Rs[tile_region(Rs, tm.nreg, tile)];
-    const int b = R.b, nbt = R.nbt;
-    const cdf* Ub = Us + R.u_off;
+    if (tile >= reg_end) {
+      reg = tile_region(Rs, tm.nreg, tile);
+      const TileRegion R = Rs[reg];
+      G = R.G;
+      reg_end = (reg + 1 < tm.nreg) ? Rs[reg + 1].tile0 : tm.ntiles;
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const int slot = threadIdx.x + q * TILE_T;
+        int c = R.sub0 + R.nsub - 1;  // the block class whose slots hold this one
+        while (c > R.sub0 && Ss[c].off > slot) --c;
+        const int rel = slot - Ss[c].off;
+        const int a = rel / G;
+        dec[q] = c | (a << 6) | ((rel - a * G) << 10);
+      }
+    }
 #pragma unroll
     for (int q = 0; q < S; ++q) {
       const int x = xs[q];
       if (x < 0) continue;
-      const int slot = threadIdx.x + q * TILE_T;
-      const int a = slot / nbt, k = slot - a * nbt;
+      const int c = dec[q] & 63, a = (dec[q] >> 6) & 15, k = dec[q] >> 10;
+      const TileSub u = Ss[c];
+      const int b = u.b;
+      const cdf* Ub = Us + u.u_off;
+      const cdf* Pk = Sp + u.off + k;  // member l of this block at Pk[l * G]
       if (!ADJ) {
         dfacc ar, ai;
         acc_zero(ar);
         acc_zero(ai);
-        for (int l = 0; l < b; ++l) cmac_cb<REALU, false>(ar, ai, Ub[a * b + l], Sp[l * nbt + k], (a ^ l) & 1);
+        for (int l = 0; l < b; ++l) cmac_cb<REALU, false>(ar, ai, Ub[a * b + l], Pk[l * G], (a ^ l) & 1);
         psi[x] = make_cdf(acc_get(ar), acc_get(ai));
         continue;
       }
+      const cdf* Lk = Sl + u.off + k;
       if (a + 1 < b) {  // gradient term of the generator entries (a, a+1) and (a+1, a)
-        const cdf lk = Sl[slot], lk1 = Sl[(a + 1) * nbt + k];
-        const cdf pk = Sp[slot], pk1 = Sp[(a + 1) * nbt + k];
-        const df Fk = df_make(Fs[R.f_off + a].x, Fs[R.f_off + a].y);
+        const cdf lk = Lk[a * G], lk1 = Lk[(a + 1) * G];
+        const cdf pk = Pk[a * G], pk1 = Pk[(a + 1) * G];
+        const df Fk = df_make(Fs[u.f_off + a].x, Fs[u.f_off + a].y);
         if (cpr != 0.f) {  // Re z_a
           dfacc z;
           acc_zero(z);
@@ -208,10 +241,10 @@ __global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ ? 2 : 3)) k_tile_g
       acc_zero(br);
       acc_zero(bi);
       for (int l = 0; l < b; ++l) {  // psi <- U^dag psi, lambda <- U^dag lambda
-        const cdf u = Ub[l * b + a];
+        const cdf uu = Ub[l * b + a];
         const int odd = (a ^ l) & 1;
-        cmac_cb<REALU, true>(ar, ai, u, Sp[l * nbt + k], odd);
-        cmac_cb<REALU, true>(br, bi, u, Sl[l * nbt + k], odd);
+        cmac_cb<REALU, true>(ar, ai, uu, Pk[l * G], odd);
+        cmac_cb<REALU, true>(br, bi, uu, Lk[l * G], odd);
       }
       psi[x] = make_cdf(acc_get(ar), acc_get(ai));
       lam[x] = make_cdf(acc_get(br), acc_get(bi));
@@ -226,7 +259,7 @@ __global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ ? 2 : 3)) k_tile_g
 
 template <bool ADJ, int S>
 static cudaError_t launch_tile_impl(const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial, cudaStream_t st) {
-  const size_t sm = tile_smem_bytes(g.t, g.tm.nreg, ADJ, S);
+  const size_t sm = tile_smem_bytes(g.t, g.tm.nreg, g.tm.nsub, ADJ, S);
   constexpr int kMaxSmem = 110 * 1024;
   if (sm > (size_t)kMaxSmem) return cudaErrorInvalidValue;
   static bool attr_set = false;  // one opt-in to the largest dynamic shared memory a gate can need

@@ -7,6 +7,8 @@ Workloads: bh12 (Bose-Hubbard L=12, N=12 periodic, 1,352,078 amplitudes),
 bkc8 (Kitaev chain + Kerr L=8, d=8, 8,388,608 amplitudes), bkc10 (L=10, d=6,
 30,233,088 amplitudes).  Each repetition runs one cvq_energy_and_grad call
 (depth forward gates, one H psi, depth reverse steps) and one pool screen.
+mlp: each repetition runs one forward and one backward of the proposal
+scorer on a 210-row pool (the L=10 Kitaev pool's size).
 """
 from __future__ import annotations
 
@@ -36,7 +38,7 @@ def make(workload: str):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="bh12", choices=["bh12", "bkc8", "bkc10"])
+    ap.add_argument("--workload", default="bh12", choices=["bh12", "bkc8", "bkc10", "mlp"])
     ap.add_argument("--depth", type=int, default=40)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
@@ -49,6 +51,24 @@ def main():
     from paper_2606_05297_gb300 import build, cvq
     from paper_2606_05297_gb300 import workloads as W
     build.build()
+    if a.workload == "mlp":
+        sc = cvq.Scorer(210, seed=a.seed)
+        X = torch.from_numpy(W.scorer_inputs(210, a.seed + 1)).cuda()
+        ds = torch.ones(210, dtype=torch.float32, device="cuda")
+        for _ in range(a.warm):
+            sc.forward(X)
+            sc.backward(X, ds)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        t0 = time.perf_counter()
+        for _ in range(a.reps):
+            out = sc.forward(X)
+            sc.backward(X, ds)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"mlp: rows=210 reps={a.reps} score[0]={out[0].item():.6f} "
+              f"{(time.perf_counter() - t0) / a.reps * 1e6:.1f} us/rep (forward + backward)")
+        return
     m, pool = make(a.workload)
     s = cvq.Sector(m)
     p = cvq.ProjectedPool(s, pool, a.projected) if a.projected else cvq.Pool(s, pool)

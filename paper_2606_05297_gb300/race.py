@@ -64,7 +64,7 @@ def run_arm(make, E0, max_ops, grad_tol=1e-6):
     return a, hist, reached, time.perf_counter() - t0
 
 
-def sweep_instances(count: int, seed: int, Ls=(4, 5), U_range=(1.0, 4.0)):
+def sweep_instances(count: int, seed: int, Ls=(4,), U_range=(1.0, 4.0)):
     """A U/J sweep of small open Bose-Hubbard chains (N = L, Eq. BoseHubbard in
     its literal sign), all-pairs pool, Mott start plus the HVA warm start:
     instances on which ADAPT reaches |E - E0| < 1e-6 within the paper's budget
@@ -201,7 +201,7 @@ def main(argv=None):
             E0s.append(adapt.ground_energy(cvq.Sector(m)))
         arms = race_sweep(insts, E0s, scorer, tr, max_ops=a.max_ops, hessian_recycling=a.hessian_recycling,
                           top_k=a.top_k, full_every=a.full_every)
-        out = dict(target=dict(model="open Bose-Hubbard chains L in {4, 5}, N = L, U/J log-uniform [1, 4]",
+        out = dict(target=dict(model="open Bose-Hubbard chains L = 4, N = 4, U/J log-uniform [1, 4]",
                                instances=[x[0].name for x in insts], E0=E0s, pool="all pairs",
                                tolerance=1e-6),
                    training=dict(lists=len(tr.X), rows=tr.rows(), seconds=t_train,
