@@ -187,18 +187,20 @@ class BatchedAdapt:
             self.Hinv[i] = r.Hinv
             self.trace[i].append(dict(kind="warm", E=r.f, nfev=r.nfev, nit=r.nit, status=r.status))
 
-    def screen_all(self, subsets=None):
-        """Eq. (grad) on the current state of every instance that has not
-        converged, all in one batched launch (cvq_batch_screen): the pool
-        operators of subsets[i] (default: the whole pool without the warm-start
-        gates).  Returns {instance: host gradient vector}."""
+    def screen_all(self, subsets=None, which=None):
+        """Eq. (grad) on the current state of the instances in `which` (default:
+        every instance that has not converged), all in one batched launch
+        (cvq_batch_screen): the pool operators of subsets[i] (default: the
+        whole pool without the warm-start gates).  Returns {instance: host
+        gradient vector}."""
         n = len(self.ids)
         if not self.batch_ready:
             self._structure()
-        live = [i for i in range(n) if not self.done[i]]
-        self.batch.set_active([not self.done[i] for i in range(n)])
+        live = [i for i in range(n) if not self.done[i] and (which is None or i in which)]
+        on = set(live)
+        self.batch.set_active([i in on for i in range(n)])
         self._load_theta({i: self.theta[i] for i in live})
-        subs = [(list(range(self.K[i])) if subsets is None else list(subsets[i])) if not self.done[i] else []
+        subs = [(list(range(self.K[i])) if subsets is None else list(subsets[i])) if i in on else []
                 for i in range(n)]
         need = sum(len(q) for q in subs)
         if self._gout is None or self._gout.numel() < max(need, 1):
@@ -208,12 +210,13 @@ class BatchedAdapt:
         self.screens += 1
         return {i: h[off[i]:off[i + 1]].copy() for i in live}
 
-    def choose(self, grad_tol: float):
-        """The operator each live instance appends: {instance: (pool index, |g|)}
-        (plain rule: largest exact gradient of a full screen).  Instances whose
-        largest |g| is below grad_tol are marked done."""
+    def choose(self, grad_tol: float, which=None):
+        """The operator each live instance (of `which`, default all) appends:
+        {instance: (pool index, |g|)} (plain rule: largest exact gradient of a
+        full screen).  Instances whose largest |g| is below grad_tol are marked
+        done."""
         chosen = {}
-        gs = self.screen_all()
+        gs = self.screen_all(which=which)
         for i, g in gs.items():
             k, gmax = select(g)
             if gmax < grad_tol or len(self.ids[i]) + 1 > self.n_max:
@@ -251,6 +254,71 @@ class BatchedAdapt:
                                       status=r.status, n=len(self.ids[i])))
         self.after_step(grown)
         return len(grown)
+
+    def run(self, max_ops: int = 160, grad_tol: float = 1e-6, max_iter: int = 1000, stop_after=None,
+            on_iteration=None):
+        """ADAPT on every instance with asynchronous rounds: each round screens
+        (one batched screen) and grows every instance whose last minimisation
+        has finished, then evaluates every pending BFGS point with one batched
+        launch, so no instance waits for the slowest one's BFGS.  An instance
+        ends on max|g| < grad_tol, after max_ops operators, or when
+        stop_after(i, record) returns True.  on_iteration(i, record) sees
+        every finished iteration."""
+        n = len(self.ids)
+        if not self.batch_ready:
+            self._structure()
+        count = [0] * n
+        gens, xs, grown = {}, {}, {}
+        ready = [i for i in range(n) if not self.done[i]]
+        while True:
+            ready = [i for i in ready if not self.done[i]]
+            if ready:
+                chosen = self.choose(grad_tol, which=set(ready))
+                for i, (k, gm) in chosen.items():
+                    self.ids[i].append(k)
+                    self.theta[i] = np.append(self.theta[i], 0.0)
+                    H0 = None
+                    if self.hessian_recycling and self.Hinv[i] is not None:
+                        H0 = np.eye(self.theta[i].size)
+                        H0[:-1, :-1] = self.Hinv[i]
+                    gens[i] = BFGS(None).steps(self.theta[i], gtol=min(1e-6, gm * 1e-5), max_iter=max_iter, Hinv0=H0)
+                    grown[i] = (k, gm)
+                if chosen:
+                    self._structure()
+                    for i in chosen:
+                        xs[i] = next(gens[i])
+                ready = []
+            if not xs:
+                break
+            self.batch.set_active([i in xs for i in range(n)])
+            self._load_theta(xs)
+            E, G = self.batch.energy_and_grad()
+            hE = E.cpu().numpy()
+            hG = G.cpu().numpy()
+            off = self.batch.offsets
+            self.rounds += 1
+            self.evals += len(xs)
+            for i in list(xs):
+                try:
+                    xs[i] = gens[i].send((float(hE[i]), hG[off[i]:off[i + 1]].copy()))
+                except StopIteration as st:
+                    r = st.value
+                    del xs[i], gens[i]
+                    self.theta[i] = r.x
+                    self.Hinv[i] = r.Hinv
+                    k, gm = grown.pop(i)
+                    rec = dict(kind="adapt", op=k, gmax=gm, E=r.f, nfev=r.nfev, nit=r.nit, status=r.status,
+                               n=len(self.ids[i]))
+                    self.trace[i].append(rec)
+                    self.after_step({i: (k, gm)})
+                    count[i] += 1
+                    if on_iteration is not None:
+                        on_iteration(i, rec)
+                    if count[i] >= max_ops or (stop_after is not None and stop_after(i, rec)):
+                        self.done[i] = True
+                    else:
+                        ready.append(i)
+        return dict(iterations=count, rounds=self.rounds, evals=self.evals)
 
     def after_step(self, grown):
         """Hook for drivers that keep per-iteration state (the learned proposal)."""

@@ -596,7 +596,7 @@ static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
   };
   std::vector<Plan> plans;
   std::map<std::array<int, 7>, int> where;
-  const int slots = (S.dim >= TILE_LARGE_DIM) ? TILE_S_LARGE : 1;
+  const int slots = (S.dim >= TILE_LARGE_DIM) ? TILE_S_LARGE : (S.dim >= TILE_MID_DIM) ? TILE_S_MID : 1;
   const int T = TILE_T * slots;
   std::vector<int> plan_of(p->K, -1);
   auto orbits = [&](const TypeDesc& t, int cls) -> int64_t {

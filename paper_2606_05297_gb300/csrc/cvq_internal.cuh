@@ -260,11 +260,11 @@ struct PoolDev {
 // a tile the blocks of one class ("sub-block" c of the region, size b_c) take
 // b_c G consecutive slots from off_c, member-major: slot off_c + a G + k is
 // member a of the block of orbit k.  Unused slots hold -1.  Large sectors take
-// S = TILE_S_LARGE, so that each thread keeps several loads in flight from
-// HBM; small ones S = 1, so that every CTA gets work.
+// S = TILE_S_LARGE (medium ones TILE_S_MID), so that each thread keeps
+// several loads in flight; small ones S = 1, so that every CTA gets work.
 constexpr int TILE_T = NTHREADS;
-constexpr int TILE_S_LARGE = 4;
-constexpr int64_t TILE_LARGE_DIM = 1 << 22;
+constexpr int TILE_S_LARGE = 4, TILE_S_MID = 2;
+constexpr int64_t TILE_LARGE_DIM = 1 << 22, TILE_MID_DIM = 1 << 19;
 constexpr int TILE_MAX_SUB = 32;  // block classes of one orbit class
 struct TileSub {
   int b, off;            // block size, first slot within the tile

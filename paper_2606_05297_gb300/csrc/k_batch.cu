@@ -378,16 +378,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (t.realu) bkc_gate_range<false, true>(S, gi, gj, t, m, threadIdx.x, items, NTHREADS, psi, psi, lam, gacc);
           else bkc_gate_range<false, false>(S, gi, gj, t, m, threadIdx.x, items, NTHREADS, psi, psi, lam, gacc);
         }
-      } else {
-        for (int c = 0; c < t.nchunks; ++c) {
-          const int4 ch = I.P.chunks[t.chunk_base + c];
-          if (adj) {
-            if (t.realu) bh_gate_chunk<true, true>(S, G32, gi, gj, t, m, ch, psi, psi, lam, gacc);
-            else bh_gate_chunk<true, false>(S, G32, gi, gj, t, m, ch, psi, psi, lam, gacc);
-          } else {
-            if (t.realu) bh_gate_chunk<false, true>(S, G32, gi, gj, t, m, ch, psi, psi, lam, gacc);
-            else bh_gate_chunk<false, false>(S, G32, gi, gj, t, m, ch, psi, psi, lam, gacc);
-          }
+      } else {  // every orbit of every class at once: one pass of the CTA for small sectors
+        const int64_t norb = S.bh2_off[S.N + 1];
+        if (adj) {
+          if (t.realu) bh_gate_orbits<true, true>(S, G64, gi, gj, t, m, threadIdx.x, norb, NTHREADS, psi, psi, lam, gacc);
+          else bh_gate_orbits<true, false>(S, G64, gi, gj, t, m, threadIdx.x, norb, NTHREADS, psi, psi, lam, gacc);
+        } else {
+          if (t.realu) bh_gate_orbits<false, true>(S, G64, gi, gj, t, m, threadIdx.x, norb, NTHREADS, psi, psi, lam, gacc);
+          else bh_gate_orbits<false, false>(S, G64, gi, gj, t, m, threadIdx.x, norb, NTHREADS, psi, psi, lam, gacc);
         }
       }
       if (adj) {

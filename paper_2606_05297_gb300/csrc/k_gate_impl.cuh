@@ -321,6 +321,29 @@ __device__ __forceinline__ void bh_gate_chunk(const SectorDev& S, const int32_t 
   }
 }
 
+// Bose-Hubbard: every orbit t = first, first + step, ... < end of the
+// two-mode gate on (gi, gj), classes in increasing pair occupation M, each
+// orbit unranked on its own (for sectors small enough that one pass of
+// threads covers them, where the chunk schedule would leave most threads of
+// a CTA idle).
+template <bool ADJ, bool REALU>
+__device__ __forceinline__ void bh_gate_orbits(const SectorDev& S, const int64_t (*G)[DMAX + 1], int gi, int gj,
+                                               const TypeDesc& t, const GateSmem& m, int64_t first, int64_t end,
+                                               int64_t step, const cdf* src, cdf* dst, cdf* lam, dfacc& gacc) {
+  const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
+  for (int64_t u = first; u < end; u += step) {
+    int M;
+    const uint64_t w0 = bh_orbit(S, G, gi, gj, u, M);
+    const BhIdx idx = bh_idx_of<int64_t>(S, G, gi, gj, w0);
+    for (int bi = t.class_off[M]; bi < t.class_off[M + 1]; ++bi) {
+      const BlockDesc bd = m.B[bi];
+      if (bd.bext < 2) continue;  // zero generator: identity, no gradient term
+      apply_block<ADJ, REALU, true>(bd.size, m.U + bd.u_off, m.M + bd.mem_off, m.F + bd.f_off, cpr, cpi, idx, src,
+                                    dst, lam, m.stg, m.sx, gacc);
+    }
+  }
+}
+
 // U_g = (W V) exp(i theta Lambda) (W V)^dag for every block of one gate,
 // formed in FP64 by the calling CTA and stored as df complex.  Every
 // generator here has phases that are multiples of pi/2 and a zero-diagonal

@@ -133,7 +133,7 @@ __device__ __forceinline__ int tile_region(const TileRegion* Rs, int nreg, int64
 }
 
 template <bool ADJ, bool REALU, int S>
-__global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ ? 2 : 3)) k_tile_gate(const __grid_constant__ GateArg g, PoolDev P,
+__global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (S == 2 ? 3 : (ADJ ? 2 : 3))) k_tile_gate(const __grid_constant__ GateArg g, PoolDev P,
                                                                        cdf* psi, cdf* lam,
                                                                        double* __restrict__ partial) {
   extern __shared__ __align__(16) char smem[];
@@ -283,6 +283,9 @@ cudaError_t launch_tile_gate(const GateArg& g, PoolDev P, cdf* psi, cdf* lam, do
   if (g.tm.slots == TILE_S_LARGE)
     return adjoint ? launch_tile_impl<true, TILE_S_LARGE>(g, P, psi, lam, partial, st)
                    : launch_tile_impl<false, TILE_S_LARGE>(g, P, psi, nullptr, nullptr, st);
+  if (g.tm.slots == TILE_S_MID)
+    return adjoint ? launch_tile_impl<true, TILE_S_MID>(g, P, psi, lam, partial, st)
+                   : launch_tile_impl<false, TILE_S_MID>(g, P, psi, nullptr, nullptr, st);
   if (g.tm.slots != 1) return cudaErrorInvalidValue;
   return adjoint ? launch_tile_impl<true, 1>(g, P, psi, lam, partial, st)
                  : launch_tile_impl<false, 1>(g, P, psi, nullptr, nullptr, st);

@@ -370,10 +370,10 @@ class LearnedBatchedAdapt(BatchedAdapt):
             self.trainer.add(X, g)
         return k, gmax
 
-    def choose(self, grad_tol: float):
+    def choose(self, grad_tol: float, which=None):
         torch = self.torch
         n = len(self.ids)
-        live = [i for i in range(n) if not self.done[i]]
+        live = [i for i in range(n) if not self.done[i] and (which is None or i in which)]
         if not live:
             return {}
         rows = self._rows(live)
@@ -389,7 +389,7 @@ class LearnedBatchedAdapt(BatchedAdapt):
         subs = [[] for _ in range(n)]
         for i in live:
             subs[i] = list(range(self.K[i])) if full[i] else [int(t) for t in top[i]]
-        gs = self.screen_all(subs)
+        gs = self.screen_all(subs, which=set(live))
         chosen, confirm, trained = {}, [], False
         for i in live:
             g = gs[i]
@@ -409,7 +409,7 @@ class LearnedBatchedAdapt(BatchedAdapt):
             chosen[i] = (min(sub[j] for j in np.nonzero(a >= m * (1.0 - TIE_REL))[0]), m)
         if confirm:
             subs2 = [list(range(self.K[i])) if i in confirm else [] for i in range(n)]
-            gs2 = self.screen_all(subs2)
+            gs2 = self.screen_all(subs2, which=set(confirm))
             for i in confirm:
                 chosen[i] = self._full_screen(i, rows[i], gs2[i], None)
                 trained = True

@@ -101,7 +101,8 @@ def race_sweep(insts, E0s, scorer, trainer, max_ops=160, hessian_recycling=True,
                tol=1e-6):
     """Wall time to |E - E0| < tol on every instance of a sweep: plain
     full-screen ADAPT run instance after instance, the same method on the
-    batched engine (lockstep BFGS, batched screens), and the learned proposal
+    batched engine (asynchronous rounds: every pending BFGS point of every
+    instance in one batched launch, batched screens), and the learned proposal
     on the batched engine."""
     from . import adapt, batched, learned
     n = len(insts)
@@ -133,19 +134,15 @@ def race_sweep(insts, E0s, scorer, trainer, max_ops=160, hessian_recycling=True,
         its = [0] * n
         for i in range(n):
             _reach(reached[i], dE[i], time.perf_counter() - t0, 0)
-        for _ in range(max_ops):
-            stop = [d < tol for d in dE]
-            if all(stop):
-                break
-            last = [len(B.trace[i]) for i in range(n)]
-            if B.step(stop=stop) == 0:
-                break
-            t = time.perf_counter() - t0
-            for i in range(n):
-                if len(B.trace[i]) > last[i]:
-                    its[i] += 1
-                    dE[i] = abs(B.trace[i][-1]["E"] - E0s[i])
-                    _reach(reached[i], dE[i], t, its[i])
+            if dE[i] < tol:
+                B.done[i] = True
+
+        def on_it(i, rec):
+            its[i] += 1
+            dE[i] = abs(rec["E"] - E0s[i])
+            _reach(reached[i], dE[i], time.perf_counter() - t0, its[i])
+
+        B.run(max_ops=max_ops, stop_after=lambda i, rec: abs(rec["E"] - E0s[i]) < tol, on_iteration=on_it)
         per = [dict(dE=dE[i], iterations=its[i], reached=reached[i]) for i in range(n)]
         return B, _summary(per, time.perf_counter() - t0, n)
 

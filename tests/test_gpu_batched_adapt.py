@@ -1,4 +1,4 @@
-"""Lockstep batched ADAPT against the plain single-instance driver: the same
+"""Lockstep and asynchronous batched ADAPT against the plain single-instance driver: the same
 operator selections and energies on every instance, with every BFGS
 evaluation of a round issued as one batched graph launch; and the 64-instance
 sweep's batched evaluation against the per-instance calls.
@@ -41,6 +41,40 @@ def test_batched_adapt_matches_plain():
         for rp, rb in zip(a.trace, ba.trace[i]):
             assert abs(rp["E"] - rb["E"]) <= 1e-7 * max(1.0, abs(rp["E"])), (i, rp["E"], rb["E"])
     assert ba.rounds < ba.evals  # rounds really were shared between instances
+
+
+def test_asynchronous_batched_adapt_matches_plain():
+    """The asynchronous rounds of BatchedAdapt.run (each instance screens and
+    grows as soon as its own BFGS ends) make the same choices as the plain
+    driver, with Hessian recycling on both sides; a stop rule ends one
+    instance early."""
+    from paper_2606_05297_gb300 import adapt, batched, build
+    build.build()
+    models = [W.c1_model(), W.bose_hubbard(5, 5, J=1.0, U=3.4, periodic=True),
+              W.bose_hubbard(4, 4, J=1.0, U=3.4, periodic=True)]
+    pools = [W.pool_for(m) for m in models]
+    occ = [W.initial_occupation(m) for m in models]
+    warm = [W.hva_layer(m) for m in models]
+    wth = [W.warm_start_thetas(len(w), 3) for w in warm]
+    ba = batched.BatchedAdapt(models, pools, occ, warm, wth, n_max=40, hessian_recycling=True)
+    ba.optimise_warm_start()
+    seen = []
+    out = ba.run(max_ops=5, stop_after=lambda i, rec: i == 2 and rec["n"] >= len(warm[2]) + 2,
+                 on_iteration=lambda i, rec: seen.append(i))
+    assert out["iterations"] == [5, 5, 2]
+    assert sorted(seen) == [0] * 5 + [1] * 5 + [2] * 2
+    for i, m in enumerate(models):
+        a = adapt.Adapt(m, pools[i], occ[i], warm[i], wth[i], n_max=40, hessian_recycling=True)
+        a.optimise_warm_start()
+        for _ in range(out["iterations"][i]):
+            if a.step() is None:
+                break
+        ops_p = [r["op"] for r in a.trace if r["kind"] == "adapt"]
+        ops_b = [r["op"] for r in ba.trace[i] if r["kind"] == "adapt"]
+        assert ops_p == ops_b, (i, ops_p, ops_b)
+        for rp, rb in zip(a.trace, ba.trace[i]):
+            assert abs(rp["E"] - rb["E"]) <= 1e-7 * max(1.0, abs(rp["E"])), (i, rp["E"], rb["E"])
+    assert ba.rounds < ba.evals
 
 
 def test_c4_batched_matches_sequential():
