@@ -596,7 +596,7 @@ static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
   };
   std::vector<Plan> plans;
   std::map<std::array<int, 7>, int> where;
-  const int slots = (S.dim >= TILE_LARGE_DIM) ? TILE_S_LARGE : (S.dim >= TILE_MID_DIM) ? TILE_S_MID : 1;
+  const int slots = (S.dim >= TILE_LARGE_DIM) ? TILE_S_LARGE : 1;
   const int T = TILE_T * slots;
   std::vector<int> plan_of(p->K, -1);
   auto orbits = [&](const TypeDesc& t, int cls) -> int64_t {
@@ -809,7 +809,13 @@ static int set_pool(const cvq_sector* s, const cvq_op* ops, int K, int dc, cvq_p
   // Tiled gates need int32 sector indices; projected pools keep the orbit
   // kernels.  The tables are built from the pool tables uploaded above.
   if (dc == 0 && S.dim <= (int64_t)INT32_MAX) {
-    if (int rc = build_tiles(p, pb)) {
+    int rc = build_tiles(p, pb);
+    if (rc == CVQ_OK) {  // the device op table carries each operator's tiles (batched engine)
+      for (int k = 0; k < K; ++k) ga[k].tm = p->op_tiles[k];
+      e = up(o_ops, ga.data(), (size_t)K * sizeof(GateArg));
+      if (e != cudaSuccess) rc = cuda_fail(e, "op table upload");
+    }
+    if (rc) {
       if (p->tile_blob) cudaFree(p->tile_blob);
       cudaFree(p->blob);
       delete p;
@@ -1562,8 +1568,9 @@ int internal_screen_plan(const cvq_pool* p, const int* subset, int n_subset, Scr
 // Host-side view of a pool for the batched engine.
 int internal_pool_host(const cvq_pool* p, const cvq_sector** sec, const TypeDesc** types, int* ntypes,
                        const int** op_type, const int** op_i, const int** op_j, int* K, PoolDev* P, int* ustride,
-                       const GateArg** ops_dev) {
+                       const GateArg** ops_dev, const TileMap** op_tiles) {
   if (!p) return fail(CVQ_EINVAL, "null pool");
+  *op_tiles = p->op_tiles.empty() ? nullptr : p->op_tiles.data();
   *sec = p->sec;
   *types = p->types.data();
   *ntypes = (int)p->types.size();

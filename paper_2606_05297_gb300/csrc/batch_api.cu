@@ -10,6 +10,7 @@
 
 #include "cvq_internal.cuh"
 #include "k_ham_impl.cuh"
+#include "k_tile_impl.cuh"
 
 namespace cvq {
 int internal_fail(int code, const char* msg);
@@ -17,7 +18,7 @@ const SectorDev* internal_sector(const cvq_sector* s);
 int internal_sector_device(const cvq_sector* s);
 int internal_pool_host(const cvq_pool* p, const cvq_sector** sec, const TypeDesc** types, int* ntypes,
                        const int** op_type, const int** op_i, const int** op_j, int* K, PoolDev* P, int* ustride,
-                       const GateArg** ops_dev);
+                       const GateArg** ops_dev, const TileMap** op_tiles);
 int internal_screen_plan(const cvq_pool* p, const int* subset, int n_subset, ScreenArg* sa, ScreenMap* sm);
 }  // namespace cvq
 
@@ -32,6 +33,7 @@ struct PoolView {
   const int *op_type, *op_i, *op_j;
   PoolDev P;
   const GateArg* ops_dev;
+  const TileMap* op_tiles;  // host copy of each operator's tiles (NULL: no tiles)
 };
 
 int errf(int code, const char* fmt, ...) {
@@ -200,6 +202,17 @@ void items_of(const cvq_batch* b, int inst, int seg, const BSeg* sg, int kind, s
   // the pool operator of this block gate
   const int op = b->ids[(size_t)b->inst[inst].ids_off + sg->k0];
   const TypeDesc& t = p.types[p.op_type[op]];
+  // tiled gate of one slot per thread (the layer kernel's register budget
+  // holds no more): ranges of about `tile` table slots
+  if (p.op_tiles && p.op_tiles[op].idx && p.op_tiles[op].slots == 1) {
+    const TileMap& tm = p.op_tiles[op];
+    const int64_t per = std::max<int64_t>(1, b->tile / ((int64_t)TILE_T * tm.slots));
+    for (int64_t u = 0; u < tm.ntiles; u += per) {
+      push(u, std::min<int64_t>(tm.ntiles, u + per));
+      out.back().kind = BI_TILE;
+    }
+    return;
+  }
   if (S.kind == CVQ_BKC) {
     const int nm = t.single ? 1 : 2;
     int64_t items = 1, per_orbit = 1;
@@ -575,7 +588,7 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
   for (int i = 0; i < n_inst; ++i) {
     PoolView& p = b->pv[i];
     int rc = internal_pool_host(pools[i], &p.sec, &p.types, &p.ntypes, &p.op_type, &p.op_i, &p.op_j, &p.K, &p.P,
-                                &p.ustride, &p.ops_dev);
+                                &p.ustride, &p.ops_dev, &p.op_tiles);
     if (rc || p.sec != sectors[i]) {
       delete b;
       return rc ? rc : errf(CVQ_EINVAL, "pool %d belongs to another sector", i);
@@ -598,6 +611,10 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
         smem = std::max(smem, gate_smem_bytes(p.types[t], S->kind));
         b->maxblk = std::max(b->maxblk, p.types[t].nblocks);
       }
+    for (int k = 0; p.op_tiles && k < p.K; ++k) {
+      const TileMap& tm = p.op_tiles[k];
+      if (tm.idx && tm.slots == 1) smem = std::max(smem, tile_smem_bytes(p.types[p.op_type[k]], tm.nreg, tm.nsub, true, 1));
+    }
     offs[i] = total;
     total += 2 * a256(sizeof(cdf) * (size_t)S->dim) + a256(sizeof(cdf) * (size_t)std::max(n_max, 1) * p.ustride);
   }

@@ -99,6 +99,19 @@ __host__ __device__ __forceinline__ T bh_move_delta(uint64_t w, uint64_t wR, int
   return d;
 }
 
+// Rank change of the hop x -> x + e_r - e_{r+1} on a chain of L modes holding
+// N bosons when the suffix sum R_{r+1} = n_{r+1} + ... + n_{L-1} equals Q:
+// only the terms of positions r and r+1 change, and within them the parts
+// that involve n_r and n_{r+1} cancel (0 outside 0 <= r <= L-2, 1 <= Q <= N).
+template <class T>
+__host__ __device__ __forceinline__ T bh_hop_delta(const T (*G)[DMAX + 1], int L, int N, int r, int Q) {
+  if (r < 0 || r > L - 2 || Q < 1 || Q > N) return 0;
+  const int p = L - 1 - r;
+  T d = G[p][Q] - G[p][Q - 1];
+  if (r + 1 <= L - 2) d += G[p - 1][Q - 1] - G[p - 1][Q];
+  return d;
+}
+
 // Inverse of bh_rank for a chain of Lc modes holding Nc bosons; the tuple is
 // written to consecutive nibbles starting at nibble 0, its suffix sums to *wR.
 template <class T>
@@ -139,6 +152,54 @@ __host__ __device__ __forceinline__ bool comp_next(uint64_t& w, int Lc) {
   w += 1ull << (4 * p);
   w |= (uint64_t)(S - 1) << (4 * (Lc - 1));
   return true;
+}
+
+// Bose-Hubbard sector indices [x0, x1) visited by the warps of a grid, each
+// tuple stepped to rather than unranked: the range is cut into chunks of 32 R
+// consecutive indices (R <= WALK_RMAX, odd), warp w of the grid taking chunks
+// w, w + nw, ...  In a chunk, lane l unranks index base + l R and steps R - 1
+// times to the next composition in lexicographic order (the order of the
+// ranks), leaving the tuples in the warp's part of wbuf (32 WALK_RMAX
+// entries per warp of the CTA); the warp then visits indices base + l + 32 i,
+// so its amplitude accesses stay coalesced while one index in R is unranked.
+// f(x, w) is called once for every index.
+constexpr int WALK_RMAX = 9;
+
+__host__ __device__ __forceinline__ int walk_r(int64_t n, int64_t nwarps) {
+  if (n <= 0) return 1;
+  const int64_t per = (n + 32 * nwarps - 1) / (32 * nwarps);  // indices per lane over all passes
+  const int64_t passes = (per + WALK_RMAX - 1) / WALK_RMAX;
+  const int r = (int)((per + passes - 1) / passes);
+  return (r & 1) ? r : r + 1;  // odd: the lanes' buffer writes fall on distinct bank pairs
+}
+
+template <class T, class F>
+__device__ __forceinline__ void bh_walk(const SectorDev& S, const T (*G)[DMAX + 1], uint64_t* wbuf, int64_t x0,
+                                        int64_t x1, F&& f) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int R = walk_r(x1 - x0, nw);
+  const int64_t ch = 32 * (int64_t)R;
+  uint64_t* buf = wbuf + (threadIdx.x >> 5) * (32 * WALK_RMAX);
+  for (int64_t base = x0 + warp * ch; base < x1; base += nw * ch) {  // uniform over the warp
+    const int64_t xs = base + (int64_t)lane * R;
+    if (xs < x1) {
+      uint64_t w = bh_unrank<T>((T)xs, S.L, S.N, G);
+      buf[lane * R] = w;
+      const int n = (int)((x1 - xs < R) ? x1 - xs : R);
+      for (int i = 1; i < n; ++i) {
+        comp_next(w, S.L);
+        buf[lane * R + i] = w;
+      }
+    }
+    __syncwarp();
+    for (int i = 0; i < R; ++i) {
+      const int64_t x = base + lane + 32 * i;
+      if (x < x1) f(x, buf[lane + 32 * i]);
+    }
+    __syncwarp();
+  }
 }
 
 // Insert two empty nibbles at modes lo < hi: the packed tuple of the other
@@ -260,11 +321,12 @@ struct PoolDev {
 // a tile the blocks of one class ("sub-block" c of the region, size b_c) take
 // b_c G consecutive slots from off_c, member-major: slot off_c + a G + k is
 // member a of the block of orbit k.  Unused slots hold -1.  Large sectors take
-// S = TILE_S_LARGE (medium ones TILE_S_MID), so that each thread keeps
-// several loads in flight; small ones S = 1, so that every CTA gets work.
+// S = TILE_S_LARGE, so that each thread keeps several loads in flight; smaller
+// ones S = 1, so that every CTA gets work (two slots on the 1.35M-amplitude
+// Bose-Hubbard sector were 17 % slower than one).
 constexpr int TILE_T = NTHREADS;
-constexpr int TILE_S_LARGE = 4, TILE_S_MID = 2;
-constexpr int64_t TILE_LARGE_DIM = 1 << 22, TILE_MID_DIM = 1 << 19;
+constexpr int TILE_S_LARGE = 4;
+constexpr int64_t TILE_LARGE_DIM = 1 << 22;
 constexpr int TILE_MAX_SUB = 32;  // block classes of one orbit class
 struct TileSub {
   int b, off;            // block size, first slot within the tile
@@ -344,7 +406,7 @@ struct DiagRunArg {
 // ------------------------------------------------------------- batched engine
 
 constexpr int BATCH_RUN = 8;  // diagonal gates per run in the batched engine
-enum BItemKind { BI_TODF = 0, BI_GATE = 1, BI_DIAG = 2, BI_APPLYH = 3 };
+enum BItemKind { BI_TODF = 0, BI_GATE = 1, BI_DIAG = 2, BI_APPLYH = 3, BI_TILE = 4 };  // BI_TILE: a range of gate tiles
 
 // One instance of a batch: its sector, pool tables and device buffers.
 struct BInst {

@@ -13,7 +13,8 @@
 // The host captures the whole sequence in a CUDA graph once per ansatz
 // structure and replays it for every theta.
 //
-// Work items are disjoint ranges of one segment of one instance (BH gates:
+// Work items are disjoint ranges of one segment of one instance (block gates
+// of pools with tile tables: ranges of the gate's tiles; other BH gates:
 // ranges of the pool type's equal-work chunks; everything else: ranges of
 // sector indices or orbits).  Each item leaves its partial sums in its own
 // slots, so every result is independent of which CTA ran which item.
@@ -21,6 +22,7 @@
 #include "k_diag_impl.cuh"
 #include "k_gate_impl.cuh"
 #include "k_ham_impl.cuh"
+#include "k_tile_impl.cuh"
 
 namespace cvq {
 
@@ -43,6 +45,7 @@ __global__ void __launch_bounds__(128) k_batch_build(const BInst* __restrict__ i
 struct BShared {
   SectorDev S;
   TypeDesc t;
+  TileMap tm;
   BSeg seg;
   int item;
   int gi, gj;
@@ -148,6 +151,21 @@ __global__ void __launch_bounds__(NTHREADS, 2)
             if (threadIdx.x == 0) partial[it.slot + q] = s;
           }
         }
+      }
+    } else if (it.kind == BI_TILE) {  // tiles [a, b) of a block gate
+      const GateArg& ga = I.ops[ids[I.ids_off + segs[it.seg].k0]];
+      copy_words(&sh.t, &ga.t, sizeof(TypeDesc));
+      copy_words(&sh.tm, &ga.tm, sizeof(TileMap));
+      __syncthreads();
+      const cdf* U = I.U + (size_t)sh.seg.k0 * I.ustride;
+      dfacc gacc;
+      acc_zero(gacc);
+      // one slot per thread (the plan gives tiles of more slots to the orbit kernels)
+      if (sh.t.realu) tile_gate_range<ADJ, true, 1>(sh.t, sh.tm, U, I.P, it.a, it.b, 1, I.psi, I.lam, smem, gacc);
+      else tile_gate_range<ADJ, false, 1>(sh.t, sh.tm, U, I.P, it.a, it.b, 1, I.psi, I.lam, smem, gacc);
+      if (ADJ) {
+        const double s = block_sum(acc_to_double(gacc));
+        if (threadIdx.x == 0) partial[it.slot] = s;
       }
     } else {  // BI_GATE
       if (threadIdx.x == 0) {

@@ -1,0 +1,195 @@
+// k_tile_impl.cuh -- tiled block gates (Sec. IV.B, O_r = exp(theta_r A_r),
+// and the reverse step of the adjoint gradient), shared by the single-gate
+// kernel and the batched engine.
+//
+// A gate acts block-diagonally (the blocks of one orbit are chains of
+// occupation pairs joined by the generator's move).  A CTA takes one tile at
+// a time: G whole orbits of one class, every block of two or more members of
+// them, TILE_T x S table slots.  Each thread loads the S sector indices of its
+// slots (coalesced) and the amplitudes they name, the tile is staged in
+// shared memory, and each thread then forms the output amplitudes of its
+// slots from the staged members of their blocks and the block unitary (also
+// in shared memory).  No thread computes a rank, every load of a tile is in
+// flight at once, neighbouring amplitudes (whole orbits) are loaded by the
+// same tile, and the next tile's loads are issued before the current tile is
+// multiplied.  The blocks of one tile are disjoint from every other tile's, so
+// the gate runs in place.  Blocks of one member (zero generator: identity) are
+// not in the table and are never touched.
+#pragma once
+
+#include "cvq_internal.cuh"
+#include "k_gate_impl.cuh"
+
+namespace cvq {
+
+// Shared memory of a tiled gate: the gate's block unitaries, the generator
+// factors (reverse), the regions, then the staged amplitudes of one tile
+// (psi, and lambda in the reverse step).
+__host__ __device__ __forceinline__ size_t tile_head_bytes(const TypeDesc& t, int nreg, int nsub, bool adj) {
+  size_t b = (size_t)t.nu * sizeof(cdf);
+  b += (((size_t)(adj ? t.nf : 0) * sizeof(float2)) + 15) & ~(size_t)15;
+  b += (size_t)nreg * sizeof(TileRegion) + (size_t)nsub * sizeof(TileSub);
+  return (b + 15) & ~(size_t)15;
+}
+
+__host__ __device__ __forceinline__ size_t tile_smem_bytes(const TypeDesc& t, int nreg, int nsub, bool adj, int slots) {
+  return tile_head_bytes(t, nreg, nsub, adj) + (size_t)TILE_T * slots * sizeof(cdf) * (adj ? 2 : 1);
+}
+
+// The S slots of one thread in one tile (slot threadIdx.x + q TILE_T), as
+// loaded ahead of their multiply.
+template <int S>
+struct TileSlots {
+  int x[S];       // sector index, -1 if the slot is unused
+  cdf v[S], l[S]; // psi (and lambda) at x
+};
+
+template <bool ADJ, int S>
+__device__ __forceinline__ void tile_load(TileSlots<S>& s, const TileMap& tm, int64_t tile, const cdf* psi,
+                                          const cdf* lam) {
+  const int* ti = tm.idx + tile * (TILE_T * S);
+#pragma unroll
+  for (int q = 0; q < S; ++q) s.x[q] = __ldcs(ti + threadIdx.x + q * TILE_T);  // streamed once per gate
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    s.v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    s.l[q] = s.v[q];
+    if (s.x[q] >= 0) {
+      s.v[q] = psi[s.x[q]];
+      if (ADJ) s.l[q] = lam[s.x[q]];
+    }
+  }
+}
+
+// Region of a tile: the last one whose first tile is <= tile.
+__device__ __forceinline__ int tile_region(const TileRegion* Rs, int nreg, int64_t tile) {
+  int lo = 0, hi = nreg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (Rs[mid].tile0 <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Tiles t_begin, t_begin + t_step, ... < t_end of one gate (block unitaries U,
+// type t, tiles tm) applied in place to psi (ADJ: the reverse step on psi and
+// lambda, its gradient term added to gacc).  Stages the gate's tables in smem
+// (tile_smem_bytes of it); the caller synchronises before smem is reused.
+template <bool ADJ, bool REALU, int S>
+__device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap& tm, const cdf* U, const PoolDev& P,
+                                                int64_t t_begin, int64_t t_end, int64_t t_step, cdf* psi, cdf* lam,
+                                                char* smem, dfacc& gacc) {
+  cdf* Us = reinterpret_cast<cdf*>(smem);
+  float2* Fs = reinterpret_cast<float2*>(Us + t.nu);
+  char* after_f = reinterpret_cast<char*>(Fs) + ((((size_t)(ADJ ? t.nf : 0) * sizeof(float2)) + 15) & ~(size_t)15);
+  TileRegion* Rs = reinterpret_cast<TileRegion*>(after_f);
+  TileSub* Ss = reinterpret_cast<TileSub*>(Rs + tm.nreg);
+  cdf* Sp = reinterpret_cast<cdf*>(smem + tile_head_bytes(t, tm.nreg, tm.nsub, ADJ));
+  cdf* Sl = Sp + TILE_T * S;
+  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) Us[e] = U[e];
+  if (ADJ)
+    for (int e = threadIdx.x; e < t.nf; e += blockDim.x) Fs[e] = P.F[t.f_base + e];
+  for (int e = threadIdx.x; e < tm.nreg; e += blockDim.x) Rs[e] = tm.reg[e];
+  for (int e = threadIdx.x; e < tm.nsub; e += blockDim.x) Ss[e] = tm.sub[e];
+  __syncthreads();
+  const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
+  int64_t tile = t_begin;
+  TileSlots<S> cur;
+  if (tile < t_end) tile_load<ADJ, S>(cur, tm, tile, psi, lam);
+  // Where each of this thread's slots sits in its tile depends only on the
+  // region (the tiles of a CTA climb through the regions in order), so it is
+  // worked out once per region: the block class c, member a and block k of
+  // slot threadIdx.x + q TILE_T, packed as c | a << 6 | k << 10.
+  int reg = -1, G = 1;
+  int64_t reg_end = -1;
+  int dec[S];
+  while (tile < t_end) {
+    const int64_t next = tile + t_step;
+    __syncthreads();  // every thread has finished reading the previous tile
+    int xs[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      Sp[threadIdx.x + q * TILE_T] = cur.v[q];
+      if (ADJ) Sl[threadIdx.x + q * TILE_T] = cur.l[q];
+      xs[q] = cur.x[q];
+    }
+    __syncthreads();
+    if (next < t_end) tile_load<ADJ, S>(cur, tm, next, psi, lam);  // in flight during the multiply
+    if (tile >= reg_end) {
+      reg = tile_region(Rs, tm.nreg, tile);
+      const TileRegion R = Rs[reg];
+      G = R.G;
+      reg_end = (reg + 1 < tm.nreg) ? Rs[reg + 1].tile0 : tm.ntiles;
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const int slot = threadIdx.x + q * TILE_T;
+        int c = R.sub0 + R.nsub - 1;  // the block class whose slots hold this one
+        while (c > R.sub0 && Ss[c].off > slot) --c;
+        const int rel = slot - Ss[c].off;
+        const int a = rel / G;
+        dec[q] = c | (a << 6) | ((rel - a * G) << 10);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      const int x = xs[q];
+      if (x < 0) continue;
+      const int c = dec[q] & 63, a = (dec[q] >> 6) & 15, k = dec[q] >> 10;
+      const TileSub u = Ss[c];
+      const int b = u.b;
+      const cdf* Ub = Us + u.u_off;
+      const cdf* Pk = Sp + u.off + k;  // member l of this block at Pk[l * G]
+      if (!ADJ) {
+        dfacc ar, ai;
+        acc_zero(ar);
+        acc_zero(ai);
+        for (int l = 0; l < b; ++l) cmac_cb<REALU, false>(ar, ai, Ub[a * b + l], Pk[l * G], (a ^ l) & 1);
+        psi[x] = make_cdf(acc_get(ar), acc_get(ai));
+        continue;
+      }
+      const cdf* Lk = Sl + u.off + k;
+      if (a + 1 < b) {  // gradient term of the generator entries (a, a+1) and (a+1, a)
+        const cdf lk = Lk[a * G], lk1 = Lk[(a + 1) * G];
+        const cdf pk = Pk[a * G], pk1 = Pk[(a + 1) * G];
+        const df Fk = df_make(Fs[u.f_off + a].x, Fs[u.f_off + a].y);
+        if (cpr != 0.f) {  // Re z_a
+          dfacc z;
+          acc_zero(z);
+          acc_mac(z, re_of(lk), re_of(pk1));
+          acc_mac(z, im_of(lk), im_of(pk1));
+          acc_mac(z, df_neg(re_of(lk1)), re_of(pk));
+          acc_mac(z, df_neg(im_of(lk1)), im_of(pk));
+          const df zr = acc_get(z);
+          acc_mac(gacc, Fk, df_make(zr.h * cpr, zr.l * cpr));
+        }
+        if (cpi != 0.f) {  // -Im z_a
+          dfacc z;
+          acc_zero(z);
+          acc_mac(z, re_of(lk), im_of(pk1));
+          acc_mac(z, df_neg(im_of(lk)), re_of(pk1));
+          acc_mac(z, df_neg(im_of(lk1)), re_of(pk));
+          acc_mac(z, re_of(lk1), im_of(pk));
+          const df zi = acc_get(z);
+          acc_mac(gacc, Fk, df_make(-zi.h * cpi, -zi.l * cpi));
+        }
+      }
+      dfacc ar, ai, br, bi;
+      acc_zero(ar);
+      acc_zero(ai);
+      acc_zero(br);
+      acc_zero(bi);
+      for (int l = 0; l < b; ++l) {  // psi <- U^dag psi, lambda <- U^dag lambda
+        const cdf uu = Ub[l * b + a];
+        const int odd = (a ^ l) & 1;
+        cmac_cb<REALU, true>(ar, ai, uu, Pk[l * G], odd);
+        cmac_cb<REALU, true>(br, bi, uu, Lk[l * G], odd);
+      }
+      psi[x] = make_cdf(acc_get(ar), acc_get(ai));
+      lam[x] = make_cdf(acc_get(br), acc_get(bi));
+    }
+    tile = next;
+  }
+}
+
+}  // namespace cvq

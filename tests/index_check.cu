@@ -4,7 +4,8 @@
 // For small Bose-Hubbard and Kitaev-chain sectors it enumerates every tuple in
 // lexicographic order (mode 0 most significant) and checks:
 //   * rank/unrank round trips and suffix sums;
-//   * the rank change of every number-conserving move (bh_move_delta);
+//   * the rank change of every number-conserving move (bh_move_delta) and of
+//     the bond hops of the matvec (bh_hop_delta);
 //   * for every two-mode and single-mode gate, that the orbits of the gate
 //     kernels, with every member allowed by the orbit's class, cover each
 //     sector index exactly once.
@@ -107,6 +108,22 @@ static void check_bh(int L, int N) {
           CHECK(x + bh_move_delta(w, wR, r, s, dr, L, G) == y, "move L=%d N=%d r=%d s=%d dr=%d", L, N, r, s, dr);
         }
       }
+    // hops along the bonds (r, r+1) from the tables of the matvec
+    for (int r = 0; r + 1 < L; ++r) {
+      const int Q = occ_get(wR, r + 1);
+      std::vector<int> t = tup[x];
+      if (t[r + 1] >= 1) {
+        t[r] += 1;
+        t[r + 1] -= 1;
+        CHECK(x + bh_hop_delta(G, L, N, r, Q) == bh_rank(pack(t), L, N, G), "hop L=%d N=%d r=%d", L, N, r);
+      }
+      t = tup[x];
+      if (t[r] >= 1) {
+        t[r] -= 1;
+        t[r + 1] += 1;
+        CHECK(x - bh_hop_delta(G, L, N, r, Q + 1) == bh_rank(pack(t), L, N, G), "reverse hop L=%d N=%d r=%d", L, N, r);
+      }
+    }
   }
   // lexicographic successor of compositions, and the nibble spread used by the gate kernels
   for (int Lc = 0; Lc <= L; ++Lc) {
@@ -231,12 +248,26 @@ static void check_bkc(int L, int d, int parity) {
     }
 }
 
+// Runs of the warp walk: odd, at most WALK_RMAX, and enough passes of
+// 32 R indices per warp to cover the range.
+static void check_walk() {
+  const int64_t nws[] = {1, 7, 4864};
+  for (int64_t nw : nws)
+    for (int64_t n = 1; n < 3000000; n = n * 3 + 1) {
+      const int R = walk_r(n, nw);
+      CHECK(R >= 1 && R <= WALK_RMAX && (R & 1), "walk_r(%lld, %lld) = %d", (long long)n, (long long)nw, R);
+      const int64_t per = (n + 32 * nw - 1) / (32 * nw);
+      CHECK(R * ((per + R - 1) / R) >= per, "walk cover");
+    }
+}
+
 int main() {
   const int bh[][2] = {{2, 3}, {3, 1}, {3, 4}, {4, 4}, {5, 3}, {5, 6}, {6, 5}};
   for (auto& c : bh) check_bh(c[0], c[1]);
   const int bkc[][3] = {{1, 4, 0}, {1, 6, 1}, {2, 2, 0}, {2, 4, 1}, {3, 4, 0}, {3, 6, 1}, {4, 4, 0}, {4, 2, 1}};
   for (auto& c : bkc) check_bkc(c[0], c[1], c[2]);
   check_div();
+  check_walk();
   printf("%s (%d failures)\n", failures ? "FAILED" : "OK", failures);
   return failures ? 1 : 0;
 }
