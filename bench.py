@@ -326,8 +326,19 @@ def fixed_ansatz_leg(reps=20):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # the same with the forward states kept for the reverse sweep
+    states = torch.empty(max(cvq.stored_states_bytes(s, p, ids), 1), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        cvq.energy_and_grad_stored(s, p, ids, th, psi0, states=states, E=E, grad=g, ws=ws)
+    e0.record()
+    for _ in range(reps):
+        cvq.energy_and_grad_stored(s, p, ids, th, psi0, states=states, E=E, grad=g, ws=ws)
+    e1.record()
+    e1.synchronize()
+    ms_st = e0.elapsed_time(e1) / reps
     return {"workload": "bose_hubbard_pbc_L12_N12_UJ3.4, random_ansatz(210, 40, seed 15), random state",
-            "evals_per_s": 1e3 / ms, "ms_per_eval": ms, "reps": reps}
+            "evals_per_s": 1e3 / ms, "ms_per_eval": ms, "reps": reps,
+            "stored_states": {"evals_per_s": 1e3 / ms_st, "ms_per_eval": ms_st, "bytes": states.numel()}}
 
 
 def c5_kernel_leg(hbm, depth=20, reps=2):

@@ -179,6 +179,27 @@ int cvq_energy_and_grad_ckpt(const cvq_sector *s, const cvq_pool *p, const int *
                              const cvq_c128 *psi0, double *E_dev, double *grad_dev, int every, void *ckpt,
                              size_t ckpt_bytes, void *workspace, size_t workspace_bytes, void *stream);
 
+/* cvq_energy_and_grad with the forward states kept instead of recomputed
+ * (Sec. IV.B adjoint gradient, the same E and g): during the forward sweep
+ * each segment (a block gate, or a run of diagonal gates) leaves what the
+ * reverse sweep needs of psi at its output in `states`: the amplitudes a
+ * block gate changes, in the order of its tile table (blocks of one member
+ * are unchanged and have no gradient term), or the whole df state after a
+ * run of diagonal gates or an untiled block gate.  The reverse sweep then
+ * forms each gradient term from the stored psi and updates only lambda, so
+ * it reads and writes half the state traffic and does half the block
+ * arithmetic of cvq_energy_and_grad, in exchange for device memory.
+ *   cvq_stored_states_bytes: size of `states` for this ansatz (host op ids);
+ *     it depends on which operators are block gates and on their tables.
+ *   cvq_energy_and_grad_stored: states is a device buffer of at least that
+ *     many bytes, 256-byte aligned (may be NULL when the size is 0), owned by
+ *     the caller and overwritten.  Errors as cvq_energy_and_grad, plus
+ *     EINVAL for a short or misaligned buffer or a projected pool. */
+int cvq_stored_states_bytes(const cvq_sector *s, const cvq_pool *p, const int *op_ids, int n, size_t *bytes);
+int cvq_energy_and_grad_stored(const cvq_sector *s, const cvq_pool *p, const int *op_ids, const double *theta, int n,
+                               const cvq_c128 *psi0, double *E_dev, double *grad_dev, void *states,
+                               size_t states_bytes, void *workspace, size_t workspace_bytes, void *stream);
+
 /* Projected gates (Sec. V.A): each gate's matrix elements are those of the
  * untruncated gate between states inside the cutoff, and the state is
  * renormalised after every gate that the cutoff makes non-unitary (the block

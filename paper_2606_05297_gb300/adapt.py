@@ -190,7 +190,7 @@ class Adapt:
 
     def __init__(self, model: Model, pool_ops: Sequence[Op], init_occ: Sequence[int], warm_ops: Sequence[Op] = (),
                  warm_theta: Sequence[float] = (), n_max: int = 256, stream=None, hessian_recycling: bool = False,
-                 fix_warm: bool = False):
+                 fix_warm: bool = False, stored_states: Optional[bool] = None):
         import torch
         self.torch = torch
         self.model = model
@@ -216,12 +216,34 @@ class Adapt:
         self._g = torch.empty(self.K, dtype=torch.float64, device="cuda")
         self._subset = list(range(self.K))
         self.nfev_total = 0
+        # The reverse sweep reads the forward states kept in device memory
+        # (cvq_energy_and_grad_stored) instead of recomputing them, when their
+        # worst case (one full state per gate) fits in a quarter of the free
+        # device memory, or when asked to.
+        if stored_states is None:
+            free, _ = torch.cuda.mem_get_info()
+            stored_states = n_max * self.sector.dim * 16 <= free // 4
+        self.stored_states = bool(stored_states)
+        self._states = None
+        self._states_key = None
 
     # energy and gradient of the current ansatz structure at theta (host vectors)
     def fg(self, theta):
         n = len(self.ids)
-        E, g = cvq.energy_and_grad(self.sector, self.pool, self.ids, theta, self.psi0, E=self._out[0:1],
-                                   grad=self._out[1:n + 1] if n else self._out[1:2], ws=self.ws, stream=self.stream)
+        if self.stored_states:
+            key = tuple(self.ids)
+            if self._states_key != key:  # the ansatz changed: size the stored states for it
+                need = cvq.stored_states_bytes(self.sector, self.pool, self.ids)
+                if self._states is None or self._states.numel() < need:
+                    self._states = self.torch.empty(max(need, 1), dtype=self.torch.uint8, device="cuda")
+                self._states_key = key
+            E, g = cvq.energy_and_grad_stored(self.sector, self.pool, self.ids, theta, self.psi0, states=self._states,
+                                              E=self._out[0:1], grad=self._out[1:n + 1] if n else self._out[1:2],
+                                              ws=self.ws, stream=self.stream)
+        else:
+            E, g = cvq.energy_and_grad(self.sector, self.pool, self.ids, theta, self.psi0, E=self._out[0:1],
+                                       grad=self._out[1:n + 1] if n else self._out[1:2], ws=self.ws,
+                                       stream=self.stream)
         h = self._host[: n + 1]
         h.copy_(self._out[: n + 1], non_blocking=True)
         (self.stream or self.torch.cuda.current_stream()).synchronize()

@@ -884,6 +884,7 @@ static int check_ws(const cvq_sector* s, const cvq_pool* p, int n, void* ws, siz
 // with lambda (3 b - 2).  Diagonal gates: 1 (forward) or 3 (reverse) per amplitude.
 struct OpCost {
   double fb, ff, ab, af;
+  double amps;  // amplitudes the gate changes
 };
 
 static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
@@ -893,6 +894,7 @@ static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
   const double dim = (double)S.dim;
   c.fb = 32.0 * dim;
   c.ab = 64.0 * dim;
+  c.amps = dim;
   if (t.diag) {
     c.ff = 8.0 * dim;
     c.af = 24.0 * dim;
@@ -924,6 +926,7 @@ static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
   }
   c.fb = 32.0 * amps;
   c.ab = 64.0 * amps;
+  c.amps = amps;
   c.ff = ff;
   c.af = af;
   return c;
@@ -1220,9 +1223,28 @@ struct Ckpt {
   std::vector<int> seg_of;  // segment index at which each slot was taken
 };
 
+// Stored forward states: for every segment of the ansatz, what the reverse
+// sweep needs of psi at the segment's output, so that it does not recompute
+// psi by undoing the gates: the output amplitudes of a tiled block gate in
+// table-slot order (only those the gate changes; its gradient term and its
+// U^dag lambda need no others), the whole state after a diagonal run or an
+// untiled block gate.  Slot si starts at off[si] bytes into buf.
+struct Stored {
+  cdf* buf = nullptr;
+  std::vector<size_t> off;
+};
+
+static size_t stored_seg_bytes(const cvq_sector* s, const cvq_pool* p, const int* ids, const Seg& g) {
+  if (!g.diag && !p->op_tiles.empty() && p->op_tiles[ids[g.k0]].idx) {
+    const TileMap& tm = p->op_tiles[ids[g.k0]];
+    return al256((size_t)tm.ntiles * TILE_T * tm.slots * sizeof(cdf));
+  }
+  return al256((size_t)s->S.dim * sizeof(cdf));
+}
+
 // U_n ... U_1 applied in place to the df state psi.
 static int forward_sweep(const cvq_sector* s, const cvq_pool* p, const int* ids, const double* theta, int n,
-                         const cdf* U, cdf* psi, cudaStream_t st, Ckpt* ck = nullptr) {
+                         const cdf* U, cdf* psi, cudaStream_t st, Ckpt* ck = nullptr, const Stored* sv = nullptr) {
   const double dim = (double)s->S.dim;
   const std::vector<Seg> segs = segments(p, ids, n);
   for (size_t si = 0; si < segs.size(); ++si) {
@@ -1235,13 +1257,29 @@ static int forward_sweep(const cvq_sector* s, const cvq_pool* p, const int* ids,
     if (g.diag) {
       DiagRunArg a;
       diag_run_arg(s, p, ids, theta, g, a);
-      ProfScope ps(KK_GATE_DIAG, st, 32.0 * dim, dim * (8.0 * s->S.L + 8.0 * a.npair));
-      CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, nullptr, nullptr, false, st), "diagonal run");
+      {
+        ProfScope ps(KK_GATE_DIAG, st, 32.0 * dim, dim * (8.0 * s->S.L + 8.0 * a.npair));
+        CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, nullptr, nullptr, false, st), "diagonal run");
+      }
+      if (sv)
+        CVQ_CUDA(cudaMemcpyAsync((char*)sv->buf + sv->off[si], psi, sizeof(cdf) * (size_t)s->S.dim,
+                                 cudaMemcpyDeviceToDevice, st), "stored state copy");
     } else {
       const GateArg ga = gate_arg(p, ids[g.k0], U + (size_t)g.k0 * p->ustride);
       const OpCost c = op_cost(s, p, ids[g.k0]);
-      ProfScope ps(KK_GATE, st, c.fb, c.ff);
-      CVQ_CUDA(launch_gate(s->S, ga, p->P, psi, psi, st), "gate");
+      if (sv && ga.tm.idx) {
+        ProfScope ps(KK_GATE, st, c.fb + 16.0 * (double)c.amps, c.ff);
+        CVQ_CUDA(launch_tile_gate(ga, p->P, psi, nullptr, nullptr, false, st, (cdf*)((char*)sv->buf + sv->off[si])),
+                 "gate");
+        continue;
+      }
+      {
+        ProfScope ps(KK_GATE, st, c.fb, c.ff);
+        CVQ_CUDA(launch_gate(s->S, ga, p->P, psi, psi, st), "gate");
+      }
+      if (sv)
+        CVQ_CUDA(cudaMemcpyAsync((char*)sv->buf + sv->off[si], psi, sizeof(cdf) * (size_t)s->S.dim,
+                                 cudaMemcpyDeviceToDevice, st), "stored state copy");
     }
   }
   return CVQ_OK;
@@ -1265,7 +1303,47 @@ extern "C" int cvq_apply_ansatz(const cvq_sector* s, const cvq_pool* p, const in
 
 static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
                            const cvq_c128* psi0, double* E_dev, double* grad_dev, void* ws, size_t wsb,
-                           void* stream, Ckpt* ck);
+                           void* stream, Ckpt* ck, const Stored* sv = nullptr);
+
+// Byte offsets of the stored-state slots of an ansatz (one per segment).
+static int stored_layout(const cvq_sector* s, const cvq_pool* p, const int* op_ids, int n, std::vector<size_t>& off,
+                         size_t& total) {
+  if (n < 0 || n > MAX_GATES) return fail(CVQ_EINVAL, "ansatz length %d outside [0, %d]", n, MAX_GATES);
+  if (n > 0 && !op_ids) return fail(CVQ_EINVAL, "null op_ids");
+  for (int k = 0; k < n; ++k)
+    if (op_ids[k] < 0 || op_ids[k] >= p->K) return fail(CVQ_EINVAL, "op_ids[%d] = %d outside the pool", k, op_ids[k]);
+  off.clear();
+  total = 0;
+  for (const Seg& g : segments(p, op_ids, n)) {
+    off.push_back(total);
+    total += stored_seg_bytes(s, p, op_ids, g);
+  }
+  return CVQ_OK;
+}
+
+extern "C" int cvq_stored_states_bytes(const cvq_sector* s, const cvq_pool* p, const int* op_ids, int n,
+                                       size_t* bytes) {
+  if (!s || !p || !bytes) return fail(CVQ_EINVAL, "null argument");
+  if (p->dc) return fail(CVQ_EINVAL, "a projected pool keeps its states with cvq_projected_states_bytes");
+  std::vector<size_t> off;
+  return stored_layout(s, p, op_ids, n, off, *bytes);
+}
+
+extern "C" int cvq_energy_and_grad_stored(const cvq_sector* s, const cvq_pool* p, const int* op_ids,
+                                          const double* theta, int n, const cvq_c128* psi0, double* E_dev,
+                                          double* grad_dev, void* states, size_t states_bytes, void* ws, size_t wsb,
+                                          void* stream) {
+  if (!s || !p) return fail(CVQ_EINVAL, "null argument");
+  if (p->dc) return fail(CVQ_EINVAL, "a projected pool needs cvq_energy_and_grad_projected");
+  Stored sv;
+  size_t need = 0;
+  if (int rc = stored_layout(s, p, op_ids, n, sv.off, need)) return rc;
+  if (need > 0 && (!states || ((uintptr_t)states & 255)))
+    return fail(CVQ_EINVAL, "stored-state buffer NULL or not 256-byte aligned");
+  if (states_bytes < need) return fail(CVQ_EINVAL, "stored-state buffer of %zu bytes, %zu needed", states_bytes, need);
+  sv.buf = (cdf*)states;
+  return energy_and_grad(s, p, op_ids, theta, n, psi0, E_dev, grad_dev, ws, wsb, stream, nullptr, &sv);
+}
 
 extern "C" int cvq_energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta,
                                    int n, const cvq_c128* psi0, double* E_dev, double* grad_dev, void* ws, size_t wsb,
@@ -1296,7 +1374,7 @@ extern "C" int cvq_energy_and_grad_ckpt(const cvq_sector* s, const cvq_pool* p, 
 
 static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op_ids, const double* theta, int n,
                            const cvq_c128* psi0, double* E_dev, double* grad_dev, void* ws, size_t wsb,
-                           void* stream, Ckpt* ck) {
+                           void* stream, Ckpt* ck, const Stored* sv) {
   if (!s || !p || !psi0 || !E_dev || (n > 0 && !grad_dev)) return fail(CVQ_EINVAL, "null argument");
   if (p->dc) return fail(CVQ_EINVAL, "a projected pool needs cvq_energy_and_grad_projected");
   if (p->sec != s) return fail(CVQ_EINVAL, "pool belongs to another sector");
@@ -1309,7 +1387,7 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
   double* partial = (double*)((char*)ws + l.partial);
   if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
   if (int rc = to_df(s, psi0, psi, st)) return rc;
-  if (int rc = forward_sweep(s, p, op_ids, theta, n, U, psi, st, ck)) return rc;
+  if (int rc = forward_sweep(s, p, op_ids, theta, n, U, psi, st, ck, sv)) return rc;
   double* pE = partial + (size_t)n * NBLK;
   if (int rc = run_apply_H(s, psi, lam, pE, st)) return rc;
   {
@@ -1321,9 +1399,12 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
   int slot = ck ? (int)ck->seg_of.size() - 1 : -1;
   for (int si = (int)segs.size() - 1; si >= 0; --si) {
     const Seg& g = segs[si];
+    // stored output state of this segment (whole state, or a tiled gate's slots)
+    cdf* sto = sv ? (cdf*)((char*)sv->buf + sv->off[si]) : nullptr;
     if (g.diag) {
       DiagRunArg a;
       diag_run_arg(s, p, op_ids, theta, g, a);
+      cdf* pst = sto ? sto : psi;  // psi at the run's output
       // gradients of gates DIAG_ACC.. at the run's output state, before the reverse pass undoes the phases
       for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_ACC) {
         DiagGradArg ga;
@@ -1335,14 +1416,23 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
           ga.gj[q] = a.gj[q0 + q];
         }
         ProfScope ps(KK_ADJ_DIAG, st, 32.0 * dim, dim * (16.0 + 4.0 * ga.m));
-        CVQ_CUDA(launch_diag_grad(s->S, ga, psi, lam, partial + (size_t)(g.k0 + q0) * NBLK, st), "diagonal-run gradients");
+        CVQ_CUDA(launch_diag_grad(s->S, ga, pst, lam, partial + (size_t)(g.k0 + q0) * NBLK, st), "diagonal-run gradients");
       }
-      ProfScope ps(KK_ADJ_DIAG, st, 64.0 * dim,
+      ProfScope ps(KK_ADJ_DIAG, st, sto ? 48.0 * dim : 64.0 * dim,
                    dim * (8.0 * s->S.L + 8.0 * a.npair + 24.0 + 4.0 * std::min(g.m, DIAG_ACC)));
-      CVQ_CUDA(launch_diag_run(s->S, a, psi, psi, lam, partial + (size_t)g.k0 * NBLK, true, st), "adjoint diagonal run");
+      CVQ_CUDA(launch_diag_run(s->S, a, pst, pst, lam, partial + (size_t)g.k0 * NBLK, true, st, sto != nullptr),
+               "adjoint diagonal run");
     } else {
       const GateArg ga = gate_arg(p, op_ids[g.k0], U + (size_t)g.k0 * p->ustride);
       const OpCost c = op_cost(s, p, op_ids[g.k0]);
+      if (sto && ga.tm.idx) {  // psi from the stored slots, lambda only
+        ProfScope ps(KK_ADJ, st, 48.0 * c.amps, c.af);
+        CVQ_CUDA(launch_tile_gate_stored(ga, p->P, sto, lam, partial + (size_t)g.k0 * NBLK, st), "adjoint gate");
+        continue;
+      }
+      if (sto)  // untiled gate: the stored state replaces the working one, which the gate then undoes
+        CVQ_CUDA(cudaMemcpyAsync(psi, sto, sizeof(cdf) * (size_t)s->S.dim, cudaMemcpyDeviceToDevice, st),
+                 "stored state restore");
       ProfScope ps(KK_ADJ, st, c.ab, c.af);
       CVQ_CUDA(launch_gate_adjoint(s->S, ga, p->P, psi, lam, partial + (size_t)g.k0 * NBLK, st), "adjoint gate");
     }

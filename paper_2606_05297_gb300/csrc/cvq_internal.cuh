@@ -517,8 +517,14 @@ cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const c
 cudaError_t launch_tile_build(const SectorDev& S, int i, int j, const TypeDesc& t, PoolDev P, const TileRegion* reg_dev,
                               const TileSub* sub_dev, int nreg, int64_t max_count, int tile_slots, int* idx, int* bad,
                               cudaStream_t st);
+// store (forward, may be NULL): each output amplitude also written there in
+// slot order (ntiles x TILE_T x slots entries).
 cudaError_t launch_tile_gate(const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial, bool adjoint,
-                             cudaStream_t st);
+                             cudaStream_t st, cdf* store = nullptr);
+// The reverse step with psi at the gate's output read from store (as written
+// by the forward gate): the gradient term and lambda <- U^dag lambda only.
+cudaError_t launch_tile_gate_stored(const GateArg& g, PoolDev P, const cdf* store, cdf* lam, double* partial,
+                                    cudaStream_t st);
 cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial,
                                 cudaStream_t st);
 // Gradient-only pass over up to DIAG_ACC gates of a diagonal run (their f type and modes).
@@ -528,8 +534,10 @@ struct DiagGradArg {
 };
 cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf* psi, const cdf* lam, double* partial,
                              cudaStream_t st);
+// keep_psi (reverse only): dst holds the stored output state of the run,
+// which is read and left unchanged; only lam is multiplied.
 cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
-                            double* partial, bool adjoint, cudaStream_t st);
+                            double* partial, bool adjoint, cudaStream_t st, bool keep_psi = false);
 cudaError_t launch_dot_re(int64_t dim, const cdf* a, const cdf* b, double* partial, cudaStream_t st);
 cudaError_t launch_scale_inv_sqrt(int64_t dim, cdf* v, const double* n2, cudaStream_t st);
 cudaError_t launch_gate_proj_adj(const SectorDev& S, const GateArg& g, const cdf* D, PoolDev P, const cdf* prev,

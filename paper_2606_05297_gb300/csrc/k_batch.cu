@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       dfacc gacc;
       acc_zero(gacc);
       // one slot per thread (the plan gives tiles of more slots to the orbit kernels)
-      if (sh.t.realu) tile_gate_range<ADJ, true, 1>(sh.t, sh.tm, U, I.P, it.a, it.b, 1, I.psi, I.lam, smem, gacc);
-      else tile_gate_range<ADJ, false, 1>(sh.t, sh.tm, U, I.P, it.a, it.b, 1, I.psi, I.lam, smem, gacc);
+      if (sh.t.realu) tile_gate_range<ADJ, true, 1>(sh.t, sh.tm, U, I.P, it.a, it.b, 1, I.psi, I.lam, nullptr, smem, gacc);
+      else tile_gate_range<ADJ, false, 1>(sh.t, sh.tm, U, I.P, it.a, it.b, 1, I.psi, I.lam, nullptr, smem, gacc);
       if (ADJ) {
         const double s = block_sum(acc_to_double(gacc));
         if (threadIdx.x == 0) partial[it.slot] = s;

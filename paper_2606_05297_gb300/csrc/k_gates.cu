@@ -107,12 +107,13 @@ cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P,
 // ------------------------------------------------------------ diagonal runs
 
 // One run per launch, phase tables built on the host in FP64.
-template <int KIND, bool ADJ>
+template <int KIND, bool ADJ, bool KEEP>
 __global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ SectorDev S, const __grid_constant__ DiagRunArg a,
                                                        const cdf* src, cdf* dst, cdf* lam, double* partial) {
   __shared__ int64_t Gs[LMAX][DMAX + 1];
   __shared__ cdf T[LMAX][DMAX];
   __shared__ cdf TP[MAX_RUN_PAIRS][DMAX * DMAX];
+  __shared__ uint64_t wbuf[(KIND == CVQ_BH) ? NTHREADS / 32 * 32 * WALK_RMAX : 1];
   if (KIND == CVQ_BH) load_G(Gs, S);
   for (int e = threadIdx.x; e < LMAX * DMAX; e += blockDim.x) T[e / DMAX][e % DMAX] = a.T[e / DMAX][e % DMAX];
   for (int e = threadIdx.x; e < a.npair * DMAX * DMAX; e += blockDim.x)
@@ -123,8 +124,12 @@ __global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ S
   dfacc acc[DIAG_ACC];
 #pragma unroll
   for (int k = 0; k < DIAG_ACC; ++k) acc_zero(acc[k]);
-  diag_run_range<KIND, ADJ, DIAG_ACC>(S, Gs, T, TP, a, src, dst, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                      S.dim, (int64_t)gridDim.x * blockDim.x, acc);
+  if (KIND == CVQ_BH)
+    bh_walk(S, Gs, wbuf, 0, S.dim,
+            [&](int64_t x, uint64_t w) { diag_run_one<ADJ, DIAG_ACC, DiagRunArg, KEEP>(S, T, TP, a, src, dst, lam, x, w, acc); });
+  else
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x)
+      diag_run_one<ADJ, DIAG_ACC, DiagRunArg, KEEP>(S, T, TP, a, src, dst, lam, x, bkc_unrank(x, S), acc);
   if (ADJ) {
 #pragma unroll
     for (int k = 0; k < DIAG_ACC; ++k) {
@@ -141,13 +146,17 @@ __global__ void __launch_bounds__(NTHREADS) k_diag_grad(const __grid_constant__ 
                                                         const __grid_constant__ DiagGradArg a, const cdf* psi,
                                                         const cdf* lam, double* partial) {
   __shared__ int64_t Gs[LMAX][DMAX + 1];
+  __shared__ uint64_t wbuf[(KIND == CVQ_BH) ? NTHREADS / 32 * 32 * WALK_RMAX : 1];
   if (KIND == CVQ_BH) load_G(Gs, S);
   __syncthreads();
   dfacc acc[DIAG_ACC];
 #pragma unroll
   for (int k = 0; k < DIAG_ACC; ++k) acc_zero(acc[k]);
-  diag_grad_range<KIND, DIAG_ACC>(S, Gs, a, psi, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
-                                  (int64_t)gridDim.x * blockDim.x, acc);
+  if (KIND == CVQ_BH)
+    bh_walk(S, Gs, wbuf, 0, S.dim, [&](int64_t x, uint64_t w) { diag_grad_one<DIAG_ACC>(a, psi, lam, x, w, acc); });
+  else
+    diag_grad_range<KIND, DIAG_ACC>(S, Gs, a, psi, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
+                                    (int64_t)gridDim.x * blockDim.x, acc);
 #pragma unroll
   for (int k = 0; k < DIAG_ACC; ++k) {
     if (k < a.m) {
@@ -165,13 +174,16 @@ cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf
 }
 
 cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
-                            double* partial, bool adjoint, cudaStream_t st) {
+                            double* partial, bool adjoint, cudaStream_t st, bool keep_psi) {
+  if (keep_psi && !adjoint) return cudaErrorInvalidValue;
   if (S.kind == CVQ_BH) {
-    if (adjoint) k_diag_run<CVQ_BH, true><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
-    else k_diag_run<CVQ_BH, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    if (keep_psi) k_diag_run<CVQ_BH, true, true><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    else if (adjoint) k_diag_run<CVQ_BH, true, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    else k_diag_run<CVQ_BH, false, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
   } else {
-    if (adjoint) k_diag_run<CVQ_BKC, true><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
-    else k_diag_run<CVQ_BKC, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    if (keep_psi) k_diag_run<CVQ_BKC, true, true><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    else if (adjoint) k_diag_run<CVQ_BKC, true, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    else k_diag_run<CVQ_BKC, false, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
   }
   return cudaGetLastError();
 }

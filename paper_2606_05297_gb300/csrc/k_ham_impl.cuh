@@ -45,70 +45,94 @@ __device__ __forceinline__ void load_htabs(HSmem& h, const SectorDev& S) {
   }
 }
 
-// sigma[x] = (H psi)[x] for x = x0, x0 + step, ... < x1; eacc += Re conj(psi[x]) sigma[x].
+// Bose-Hubbard hops along a bond (r, r+1) change the rank by an amount that
+// depends only on r and the suffix sum R_{r+1} = n_{r+1} + ... + n_{L-1}: the
+// rank terms of the positions other than r and r+1 do not change, and at r
+// and r+1 the two combinatorial terms that involve n_r and n_{r+1} cancel.
+// Dp[r][Q] is the change for x -> x + e_r - e_{r+1} at R_{r+1} = Q; the
+// reverse hop x -> x - e_r + e_{r+1} changes the rank by -Dp[r][R_{r+1} + 1].
+__device__ __forceinline__ void load_dhop(int32_t (*Dp)[DMAX + 1], const int64_t (*G)[DMAX + 1], const SectorDev& S) {
+  for (int e = threadIdx.x; e < LMAX * (DMAX + 1); e += blockDim.x)
+    Dp[e / (DMAX + 1)][e % (DMAX + 1)] = (int32_t)bh_hop_delta(G, S.L, S.N, e / (DMAX + 1), e % (DMAX + 1));
+}
+
+// sigma[x] = (H psi)[x] at sector index x (occupation tuple w); eacc +=
+// Re conj(psi[x]) sigma[x].  Dp (Bose-Hubbard, may be NULL): the hop rank
+// changes of load_dhop, used for the bonds (r, r+1).
+template <int KIND>
+__device__ __forceinline__ void apply_H_one(const SectorDev& S, const int64_t (*Gs)[DMAX + 1],
+                                            const int32_t (*Dp)[DMAX + 1], const HSmem& H,
+                                            const cdf* __restrict__ psi, cdf* __restrict__ sigma, int64_t x,
+                                            uint64_t w, dfacc& eacc) {
+  const int L = S.L, Dm1 = S.D - 1;
+  const uint64_t wR = (KIND == CVQ_BH) ? bh_suffix(w, L) : 0;
+  const int64_t f = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
+  const cdf p = psi[x];
+  dfacc dg;
+  acc_zero(dg);
+  for (int r = 0; r < L; ++r) {
+    const float2 e = H.dE[r][occ_get(w, r)];
+    acc_add(dg, df_make(e.x, e.y));
+  }
+  const df d = acc_get(dg);
+  dfacc ar, ai;
+  acc_zero(ar);
+  acc_zero(ai);
+  acc_mac(ar, d, re_of(p));
+  acc_mac(ai, d, im_of(p));
+  for (int b = 0; b < S.nb; ++b) {
+    const int r = b, s = (b + 1 == L) ? 0 : b + 1;
+    const int nr = occ_get(w, r), ns = occ_get(w, s);
+    const bool adj = (KIND == CVQ_BH) && Dp && s == r + 1;
+    const df h = df_make(H.hop[b].x, H.hop[b].y);
+    if (h.h != 0.f) {
+      if (ns >= 1 && nr < Dm1) {  // neighbour x + e_r - e_s: sqrt((n_r + 1) n_s)
+        const df c = df_mul(h, df_make(H.P[0][nr][ns].x, H.P[0][nr][ns].y));
+        const int64_t xn = adj ? x + Dp[r][occ_get(wR, s)] : moved_index<KIND>(x, w, wR, f, r, +1, s, -1, S, Gs);
+        const cdf q = psi[xn];
+        acc_mac(ar, c, re_of(q));
+        acc_mac(ai, c, im_of(q));
+      }
+      if (nr >= 1 && ns < Dm1) {  // neighbour x - e_r + e_s: sqrt(n_r (n_s + 1))
+        const df c = df_mul(h, df_make(H.P[1][nr][ns].x, H.P[1][nr][ns].y));
+        const int64_t xn = adj ? x - Dp[r][occ_get(wR, s) + 1] : moved_index<KIND>(x, w, wR, f, r, -1, s, +1, S, Gs);
+        const cdf q = psi[xn];
+        acc_mac(ar, c, re_of(q));
+        acc_mac(ai, c, im_of(q));
+      }
+    }
+    if (KIND == CVQ_BKC) {
+      const df pc = df_make(H.pair[b].x, H.pair[b].y);
+      if (pc.h != 0.f) {
+        if (nr < Dm1 && ns < Dm1) {  // neighbour x + e_r + e_s (a_r a_s lowers it to x)
+          const df c = df_mul(pc, df_make(H.P[2][nr][ns].x, H.P[2][nr][ns].y));
+          const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, +1, s, +1, S, Gs)];
+          acc_mac(ar, c, re_of(q));
+          acc_mac(ai, c, im_of(q));
+        }
+        if (nr >= 1 && ns >= 1) {  // neighbour x - e_r - e_s
+          const df c = df_mul(pc, df_make(H.P[3][nr][ns].x, H.P[3][nr][ns].y));
+          const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, -1, s, -1, S, Gs)];
+          acc_mac(ar, c, re_of(q));
+          acc_mac(ai, c, im_of(q));
+        }
+      }
+    }
+  }
+  const df sr = acc_get(ar), si = acc_get(ai);
+  sigma[x] = make_cdf(sr, si);
+  acc_mac(eacc, re_of(p), sr);
+  acc_mac(eacc, im_of(p), si);
+}
+
+// apply_H_one for x = x0, x0 + step, ... < x1, each index unranked on its own.
 template <int KIND>
 __device__ __forceinline__ void apply_H_range(const SectorDev& S, const int64_t (*Gs)[DMAX + 1], const HSmem& H,
                                               const cdf* __restrict__ psi, cdf* __restrict__ sigma, int64_t x0,
-                                              int64_t x1, int64_t step,
-                                              dfacc& eacc) {
-  const int L = S.L, Dm1 = S.D - 1;
+                                              int64_t x1, int64_t step, dfacc& eacc) {
   for (int64_t x = x0; x < x1; x += step) {
-    uint64_t wR = 0;
-    const uint64_t w = unrank<KIND>(x, S, Gs, &wR);
-    const int64_t f = (KIND == CVQ_BKC) ? 2 * x + (occ_get(w, L - 1) & 1) : 0;
-    const cdf p = psi[x];
-    dfacc dg;
-    acc_zero(dg);
-    for (int r = 0; r < L; ++r) {
-      const float2 e = H.dE[r][occ_get(w, r)];
-      acc_add(dg, df_make(e.x, e.y));
-    }
-    const df d = acc_get(dg);
-    dfacc ar, ai;
-    acc_zero(ar);
-    acc_zero(ai);
-    acc_mac(ar, d, re_of(p));
-    acc_mac(ai, d, im_of(p));
-    for (int b = 0; b < S.nb; ++b) {
-      const int r = b, s = (b + 1 == L) ? 0 : b + 1;
-      const int nr = occ_get(w, r), ns = occ_get(w, s);
-      const df h = df_make(H.hop[b].x, H.hop[b].y);
-      if (h.h != 0.f) {
-        if (ns >= 1 && nr < Dm1) {  // neighbour x + e_r - e_s: sqrt((n_r + 1) n_s)
-          const df c = df_mul(h, df_make(H.P[0][nr][ns].x, H.P[0][nr][ns].y));
-          const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, +1, s, -1, S, Gs)];
-          acc_mac(ar, c, re_of(q));
-          acc_mac(ai, c, im_of(q));
-        }
-        if (nr >= 1 && ns < Dm1) {  // neighbour x - e_r + e_s: sqrt(n_r (n_s + 1))
-          const df c = df_mul(h, df_make(H.P[1][nr][ns].x, H.P[1][nr][ns].y));
-          const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, -1, s, +1, S, Gs)];
-          acc_mac(ar, c, re_of(q));
-          acc_mac(ai, c, im_of(q));
-        }
-      }
-      if (KIND == CVQ_BKC) {
-        const df pc = df_make(H.pair[b].x, H.pair[b].y);
-        if (pc.h != 0.f) {
-          if (nr < Dm1 && ns < Dm1) {  // neighbour x + e_r + e_s (a_r a_s lowers it to x)
-            const df c = df_mul(pc, df_make(H.P[2][nr][ns].x, H.P[2][nr][ns].y));
-            const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, +1, s, +1, S, Gs)];
-            acc_mac(ar, c, re_of(q));
-            acc_mac(ai, c, im_of(q));
-          }
-          if (nr >= 1 && ns >= 1) {  // neighbour x - e_r - e_s
-            const df c = df_mul(pc, df_make(H.P[3][nr][ns].x, H.P[3][nr][ns].y));
-            const cdf q = psi[moved_index<KIND>(x, w, wR, f, r, -1, s, -1, S, Gs)];
-            acc_mac(ar, c, re_of(q));
-            acc_mac(ai, c, im_of(q));
-          }
-        }
-      }
-    }
-    const df sr = acc_get(ar), si = acc_get(ai);
-    sigma[x] = make_cdf(sr, si);
-    acc_mac(eacc, re_of(p), sr);
-    acc_mac(eacc, im_of(p), si);
+    const uint64_t w = unrank<KIND>(x, S, Gs, nullptr);
+    apply_H_one<KIND>(S, Gs, nullptr, H, psi, sigma, x, w, eacc);
   }
 }
 

@@ -17,13 +17,21 @@ __global__ void __launch_bounds__(NTHREADS) k_apply_H(const __grid_constant__ Se
                                                       cdf* __restrict__ sigma, double* __restrict__ partial) {
   __shared__ int64_t Gs[LMAX][DMAX + 1];
   __shared__ HSmem H;
+  __shared__ int32_t Dp[(KIND == CVQ_BH) ? LMAX : 1][DMAX + 1];
+  __shared__ uint64_t wbuf[(KIND == CVQ_BH) ? NTHREADS / 32 * 32 * WALK_RMAX : 1];
   if (KIND == CVQ_BH) load_G(Gs, S);
   load_htabs(H, S);
   __syncthreads();
+  if (KIND == CVQ_BH) load_dhop(Dp, Gs, S);
+  __syncthreads();
   dfacc eacc;
   acc_zero(eacc);
-  apply_H_range<KIND>(S, Gs, H, psi, sigma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
-                      (int64_t)gridDim.x * blockDim.x, eacc);
+  if (KIND == CVQ_BH)
+    bh_walk(S, Gs, wbuf, 0, S.dim,
+            [&](int64_t x, uint64_t w) { apply_H_one<KIND>(S, Gs, Dp, H, psi, sigma, x, w, eacc); });
+  else
+    apply_H_range<KIND>(S, Gs, H, psi, sigma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
+                        (int64_t)gridDim.x * blockDim.x, eacc);
   if (partial) {
     const double s = block_sum(acc_to_double(eacc));
     if (threadIdx.x == 0) partial[blockIdx.x] = s;

@@ -69,49 +69,60 @@ cudaError_t launch_tile_build(const SectorDev& S, int i, int j, const TypeDesc& 
 
 // ------------------------------------------------------------ gates
 
-template <bool ADJ, bool REALU, int S>
-__global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ ? 2 : 3)) k_tile_gate(const __grid_constant__ GateArg g, PoolDev P,
-                                                                       cdf* psi, cdf* lam,
-                                                                       double* __restrict__ partial) {
+template <bool ADJ, bool REALU, int S, bool STORED>
+__global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ && !STORED ? 2 : 3))
+    k_tile_gate(const __grid_constant__ GateArg g, PoolDev P, cdf* psi, cdf* lam, cdf* store,
+                double* __restrict__ partial) {
   extern __shared__ __align__(16) char smem[];
   dfacc gacc;
   acc_zero(gacc);
-  tile_gate_range<ADJ, REALU, S>(g.t, g.tm, g.U, P, blockIdx.x, g.tm.ntiles, gridDim.x, psi, lam, smem, gacc);
+  tile_gate_range<ADJ, REALU, S, STORED>(g.t, g.tm, g.U, P, blockIdx.x, g.tm.ntiles, gridDim.x, psi, lam, store, smem,
+                                         gacc);
   if (ADJ) {
     const double s = block_sum(acc_to_double(gacc));
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
   }
 }
 
-template <bool ADJ, int S>
-static cudaError_t launch_tile_impl(const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial, cudaStream_t st) {
+template <bool ADJ, int S, bool STORED>
+static cudaError_t launch_tile_impl(const GateArg& g, PoolDev P, cdf* psi, cdf* lam, cdf* store, double* partial,
+                                    cudaStream_t st) {
   const size_t sm = tile_smem_bytes(g.t, g.tm.nreg, g.tm.nsub, ADJ, S);
   constexpr int kMaxSmem = 110 * 1024;
   if (sm > (size_t)kMaxSmem) return cudaErrorInvalidValue;
   static bool attr_set = false;  // one opt-in to the largest dynamic shared memory a gate can need
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_gate<ADJ, true, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    cudaFuncSetAttribute(k_tile_gate<ADJ, false, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_tile_gate<ADJ, true, S, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_tile_gate<ADJ, false, S, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     attr_set = true;
   }
   // The reverse step leaves one partial sum per CTA in each of the NBLK slots
   // of its gradient row (CTAs without a tile write 0); the forward gate needs
   // no more CTAs than tiles.
   const int grid = ADJ ? NBLK : (int)std::max<int64_t>(1, std::min<int64_t>(g.tm.ntiles, NBLK));
-  if (g.t.realu) k_tile_gate<ADJ, true, S><<<grid, NTHREADS, sm, st>>>(g, P, psi, lam, partial);
-  else k_tile_gate<ADJ, false, S><<<grid, NTHREADS, sm, st>>>(g, P, psi, lam, partial);
+  if (g.t.realu) k_tile_gate<ADJ, true, S, STORED><<<grid, NTHREADS, sm, st>>>(g, P, psi, lam, store, partial);
+  else k_tile_gate<ADJ, false, S, STORED><<<grid, NTHREADS, sm, st>>>(g, P, psi, lam, store, partial);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_gate(const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial, bool adjoint,
-                             cudaStream_t st) {
+                             cudaStream_t st, cdf* store) {
   if (!g.tm.idx || g.t.diag) return cudaErrorInvalidValue;
   if (g.tm.slots == TILE_S_LARGE)
-    return adjoint ? launch_tile_impl<true, TILE_S_LARGE>(g, P, psi, lam, partial, st)
-                   : launch_tile_impl<false, TILE_S_LARGE>(g, P, psi, nullptr, nullptr, st);
+    return adjoint ? launch_tile_impl<true, TILE_S_LARGE, false>(g, P, psi, lam, nullptr, partial, st)
+                   : launch_tile_impl<false, TILE_S_LARGE, false>(g, P, psi, nullptr, store, nullptr, st);
   if (g.tm.slots != 1) return cudaErrorInvalidValue;
-  return adjoint ? launch_tile_impl<true, 1>(g, P, psi, lam, partial, st)
-                 : launch_tile_impl<false, 1>(g, P, psi, nullptr, nullptr, st);
+  return adjoint ? launch_tile_impl<true, 1, false>(g, P, psi, lam, nullptr, partial, st)
+                 : launch_tile_impl<false, 1, false>(g, P, psi, nullptr, store, nullptr, st);
+}
+
+cudaError_t launch_tile_gate_stored(const GateArg& g, PoolDev P, const cdf* store, cdf* lam, double* partial,
+                                    cudaStream_t st) {
+  if (!g.tm.idx || g.t.diag || !store) return cudaErrorInvalidValue;
+  cdf* sv = const_cast<cdf*>(store);  // read only on this path
+  if (g.tm.slots == TILE_S_LARGE) return launch_tile_impl<true, TILE_S_LARGE, true>(g, P, nullptr, lam, sv, partial, st);
+  if (g.tm.slots != 1) return cudaErrorInvalidValue;
+  return launch_tile_impl<true, 1, true>(g, P, nullptr, lam, sv, partial, st);
 }
 
 }  // namespace cvq

@@ -44,9 +44,11 @@ struct TileSlots {
   cdf v[S], l[S]; // psi (and lambda) at x
 };
 
-template <bool ADJ, int S>
+// STORED: psi comes from the gate's stored output values, in slot order
+// (stored[tile TILE_T S + slot]), rather than from the state.
+template <bool ADJ, bool STORED, int S>
 __device__ __forceinline__ void tile_load(TileSlots<S>& s, const TileMap& tm, int64_t tile, const cdf* psi,
-                                          const cdf* lam) {
+                                          const cdf* lam, const cdf* stored) {
   const int* ti = tm.idx + tile * (TILE_T * S);
 #pragma unroll
   for (int q = 0; q < S; ++q) s.x[q] = __ldcs(ti + threadIdx.x + q * TILE_T);  // streamed once per gate
@@ -55,7 +57,7 @@ __device__ __forceinline__ void tile_load(TileSlots<S>& s, const TileMap& tm, in
     s.v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     s.l[q] = s.v[q];
     if (s.x[q] >= 0) {
-      s.v[q] = psi[s.x[q]];
+      s.v[q] = STORED ? __ldcs(stored + tile * (TILE_T * S) + threadIdx.x + q * TILE_T) : psi[s.x[q]];
       if (ADJ) s.l[q] = lam[s.x[q]];
     }
   }
@@ -76,10 +78,14 @@ __device__ __forceinline__ int tile_region(const TileRegion* Rs, int nreg, int64
 // type t, tiles tm) applied in place to psi (ADJ: the reverse step on psi and
 // lambda, its gradient term added to gacc).  Stages the gate's tables in smem
 // (tile_smem_bytes of it); the caller synchronises before smem is reused.
-template <bool ADJ, bool REALU, int S>
+// Stored states (forward): when store is not NULL, each output amplitude is
+// also written to store in slot order.  STORED (reverse): psi at the gate's
+// output is read from store in slot order, the gradient term and lambda <-
+// U^dag lambda are formed, and psi itself is neither read nor written.
+template <bool ADJ, bool REALU, int S, bool STORED = false>
 __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap& tm, const cdf* U, const PoolDev& P,
                                                 int64_t t_begin, int64_t t_end, int64_t t_step, cdf* psi, cdf* lam,
-                                                char* smem, dfacc& gacc) {
+                                                cdf* store, char* smem, dfacc& gacc) {
   cdf* Us = reinterpret_cast<cdf*>(smem);
   float2* Fs = reinterpret_cast<float2*>(Us + t.nu);
   char* after_f = reinterpret_cast<char*>(Fs) + ((((size_t)(ADJ ? t.nf : 0) * sizeof(float2)) + 15) & ~(size_t)15);
@@ -96,7 +102,7 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
   int64_t tile = t_begin;
   TileSlots<S> cur;
-  if (tile < t_end) tile_load<ADJ, S>(cur, tm, tile, psi, lam);
+  if (tile < t_end) tile_load<ADJ, STORED, S>(cur, tm, tile, psi, lam, store);
   // Where each of this thread's slots sits in its tile depends only on the
   // region (the tiles of a CTA climb through the regions in order), so it is
   // worked out once per region: the block class c, member a and block k of
@@ -115,7 +121,7 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
       xs[q] = cur.x[q];
     }
     __syncthreads();
-    if (next < t_end) tile_load<ADJ, S>(cur, tm, next, psi, lam);  // in flight during the multiply
+    if (next < t_end) tile_load<ADJ, STORED, S>(cur, tm, next, psi, lam, store);  // in flight during the multiply
     if (tile >= reg_end) {
       reg = tile_region(Rs, tm.nreg, tile);
       const TileRegion R = Rs[reg];
@@ -145,7 +151,9 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
         acc_zero(ar);
         acc_zero(ai);
         for (int l = 0; l < b; ++l) cmac_cb<REALU, false>(ar, ai, Ub[a * b + l], Pk[l * G], (a ^ l) & 1);
-        psi[x] = make_cdf(acc_get(ar), acc_get(ai));
+        const cdf o = make_cdf(acc_get(ar), acc_get(ai));
+        psi[x] = o;
+        if (store) __stcs(store + tile * (TILE_T * S) + threadIdx.x + q * TILE_T, o);
         continue;
       }
       const cdf* Lk = Sl + u.off + k;
@@ -173,6 +181,14 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
           const df zi = acc_get(z);
           acc_mac(gacc, Fk, df_make(-zi.h * cpi, -zi.l * cpi));
         }
+      }
+      if (STORED) {  // lambda <- U^dag lambda
+        dfacc br, bi;
+        acc_zero(br);
+        acc_zero(bi);
+        for (int l = 0; l < b; ++l) cmac_cb<REALU, true>(br, bi, Ub[l * b + a], Lk[l * G], (a ^ l) & 1);
+        lam[x] = make_cdf(acc_get(br), acc_get(bi));
+        continue;
       }
       dfacc ar, ai, br, bi;
       acc_zero(ar);

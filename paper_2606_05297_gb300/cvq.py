@@ -554,6 +554,45 @@ def energy_and_grad_ckpt(sector: Sector, pool: Pool, op_ids, theta, psi0, every:
     return E, grad[:n]
 
 
+def stored_states_bytes(sector: Sector, pool: Pool, op_ids) -> int:
+    """Device bytes of the stored forward states of this ansatz (cvq_stored_states_bytes)."""
+    L = lib()
+    L.cvq_stored_states_bytes.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_int,
+                                          C.POINTER(C.c_size_t)]
+    n = len(op_ids)
+    ids = (C.c_int * max(n, 1))(*[int(k) for k in op_ids])
+    need = C.c_size_t()
+    _check(L.cvq_stored_states_bytes(sector.h, pool.h, ids, n, C.byref(need)), "cvq_stored_states_bytes")
+    return int(need.value)
+
+
+def energy_and_grad_stored(sector: Sector, pool: Pool, op_ids, theta, psi0, states=None, E=None, grad=None, ws=None,
+                           stream=None):
+    """cvq_energy_and_grad with the forward states kept for the reverse sweep
+    (see the header); states: a uint8 device buffer of at least
+    stored_states_bytes(...) bytes, allocated here when None."""
+    import torch
+    L = lib()
+    L.cvq_energy_and_grad_stored.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                             C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                             C.c_void_p, C.c_size_t, C.c_void_p]
+    n, ids, th = _ids_theta(op_ids, theta)
+    if E is None:
+        E = torch.empty(1, dtype=torch.float64, device=psi0.device)
+    if grad is None:
+        grad = torch.empty(max(n, 1), dtype=torch.float64, device=psi0.device)
+    ws, wsb = _ws(sector, pool, n, ws)
+    need = stored_states_bytes(sector, pool, op_ids)
+    if states is None:
+        states = torch.empty(max(need, 1), dtype=torch.uint8, device=psi0.device)
+    _check(L.cvq_energy_and_grad_stored(sector.h, pool.h, ids, th.ctypes.data_as(C.POINTER(C.c_double)), n,
+                                        _dev(psi0, "c128", sector.dim, "psi0"), _dev(E, "f64", 1, "E"),
+                                        _dev(grad, "f64", n, "grad"), _dev(states, "u8", need, "states"),
+                                        states.numel(), _dev(ws, "u8", 0, "workspace"), wsb, _stream(stream)),
+           "cvq_energy_and_grad_stored")
+    return E, grad[:n]
+
+
 def _proj_sigs(L):
     vp, ip, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)
     L.cvq_set_pool_projected.argtypes = [vp, C.POINTER(_Op), C.c_int, C.c_int, C.POINTER(vp)]

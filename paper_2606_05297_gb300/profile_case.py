@@ -1,7 +1,7 @@
 """A fixed, kernel-focused case for profilers: repeated energy-and-gradient
 evaluations of a random ansatz on one workload.
 
-    python -m paper_2606_05297_gb300.profile_case --workload bh12 --depth 40 --reps 3 [--warm 5]
+    python -m paper_2606_05297_gb300.profile_case --workload bh12 --depth 40 --reps 3 [--warm 5] [--stored]
 
 Workloads: bh12 (Bose-Hubbard L=12, N=12 periodic, 1,352,078 amplitudes),
 bkc8 (Kitaev chain + Kerr L=8, d=8, 8,388,608 amplitudes), bkc10 (L=10, d=6,
@@ -44,6 +44,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--warm", type=int, default=0, help="unprofiled repetitions before cudaProfilerStart")
     ap.add_argument("--kernels", action="store_true", help="print per-kernel event timings of the profiled range")
+    ap.add_argument("--stored", action="store_true",
+                    help="keep the forward states for the reverse sweep (cvq_energy_and_grad_stored)")
     ap.add_argument("--projected", type=int, default=0,
                     help="Kitaev workloads: projected gates with this inner cutoff (Sec. V.A) instead of truncated ones")
     a = ap.parse_args()
@@ -72,10 +74,18 @@ def main():
     m, pool = make(a.workload)
     s = cvq.Sector(m)
     p = cvq.ProjectedPool(s, pool, a.projected) if a.projected else cvq.Pool(s, pool)
-    eg = cvq.energy_and_grad_projected if a.projected else cvq.energy_and_grad
     ids, th = W.random_ansatz(len(pool), a.depth, a.seed, scale=0.2)
     psi0 = torch.from_numpy(W.random_state(s.dim, a.seed + 1)).cuda()
     ws = s.workspace(p, a.depth)
+    if a.projected:
+        eg = cvq.energy_and_grad_projected
+    elif a.stored:
+        states = torch.empty(max(cvq.stored_states_bytes(s, p, ids), 1), dtype=torch.uint8, device="cuda")
+
+        def eg(s_, p_, ids_, th_, psi0_, ws=None):
+            return cvq.energy_and_grad_stored(s_, p_, ids_, th_, psi0_, states=states, ws=ws)
+    else:
+        eg = cvq.energy_and_grad
     for _ in range(a.warm):
         eg(s, p, ids, th, psi0, ws=ws)
         cvq.screen_pool(s, p, psi0, ws=ws)

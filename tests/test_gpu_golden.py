@@ -90,11 +90,15 @@ def test_energy_and_gradient_at_full_size(torch_cuda, name):
         psi0 = s.basis_state(W.initial_occupation(m))
     else:
         psi0 = torch.from_numpy(psi0_of(s)).cuda()
-    E, g = cvq.energy_and_grad(s, P, ids, th, psi0)
-    E, g = E.item(), g.cpu().numpy()
     gref = np.array(d["grad"])
-    assert abs(E - d["E"]) <= E_REL * max(1.0, abs(d["E"])), (E, d["E"])
-    assert np.max(np.abs(g - gref)) < G_ABS, np.max(np.abs(g - gref))
+    for stored in (False, True):  # states recomputed in the reverse sweep, and kept from the forward one
+        if stored:
+            E, g = cvq.energy_and_grad_stored(s, P, ids, th, psi0)
+        else:
+            E, g = cvq.energy_and_grad(s, P, ids, th, psi0)
+        E, g = E.item(), g.cpu().numpy()
+        assert abs(E - d["E"]) <= E_REL * max(1.0, abs(d["E"])), (stored, E, d["E"])
+        assert np.max(np.abs(g - gref)) < G_ABS, (stored, np.max(np.abs(g - gref)))
     if name == "c5_depth10":
         psi = torch.from_numpy(W.random_state(s.dim, p["state_seed"])).cuda()
         gs = cvq.screen_pool(s, P, psi, subset=d["screen_subset"]).cpu().numpy()

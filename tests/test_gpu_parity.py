@@ -150,6 +150,13 @@ def test_energy_and_grad(torch_cuda, name):
     assert np.max(np.abs(_np(g) - gref)) < G_ABS
     E0, g0 = cvq.energy_and_grad(s, p, [], [], torch.from_numpy(psi0).cuda())
     assert abs(E0.item() - os_.energy(psi0)[0]) <= E_REL * max(1.0, abs(Eref))
+    # the same with the forward states kept for the reverse sweep
+    Es, gs = cvq.energy_and_grad_stored(s, p, ids, th, torch.from_numpy(psi0).cuda())
+    assert abs(Es.item() - Eref) <= E_REL * max(1.0, abs(Eref))
+    assert np.max(np.abs(_np(gs) - gref)) < G_ABS
+    assert cvq.stored_states_bytes(s, p, []) == 0
+    Es0, _ = cvq.energy_and_grad_stored(s, p, [], [], torch.from_numpy(psi0).cuda())
+    assert abs(Es0.item() - E0.item()) <= 1e-15 * max(1.0, abs(E0.item()))
 
 
 @pytest.mark.parametrize("name", ["bh_pbc_L5_N4", "bkck_L4_d6"])
@@ -174,6 +181,9 @@ def test_long_diagonal_runs(torch_cuda, name):
     Eref, gref = os_.energy_and_grad([ops[i] for i in ids], th, psi0)
     assert abs(E.item() - Eref) <= E_REL * max(1.0, abs(Eref))
     assert np.max(np.abs(_np(g) - gref)) < G_ABS
+    Es, gs = cvq.energy_and_grad_stored(s, p, ids, th, torch.from_numpy(psi0).cuda())
+    assert abs(Es.item() - Eref) <= E_REL * max(1.0, abs(Eref))
+    assert np.max(np.abs(_np(gs) - gref)) < G_ABS
     out = _np(cvq.apply_ansatz(s, p, ids, th, torch.from_numpy(psi0).cuda()))
     assert np.max(np.abs(out - os_.apply_ansatz([ops[i] for i in ids], th, psi0))) < PSI_ABS
 
