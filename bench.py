@@ -180,10 +180,10 @@ def sum_over_ranks(x, ws):
 # Sources each measured kernel is compiled from: a committed ncu figure stands
 # only while these are unchanged.
 KERNEL_SOURCES = {
-    "adjoint_block": ["k_tile.cu", "k_gate_impl.cuh", "k_gate_bh_adj.cu", "k_gate_bkc_adj.cu", "cvq_internal.cuh",
-                      "df.cuh"],
-    "gate_block": ["k_tile.cu", "k_gate_impl.cuh", "k_gate_bh_fwd.cu", "k_gate_bkc_fwd.cu", "cvq_internal.cuh",
-                   "df.cuh"],
+    "adjoint_block": ["k_tile.cu", "k_tile_impl.cuh", "k_gate_impl.cuh", "k_gate_bh_adj.cu", "k_gate_bkc_adj.cu",
+                      "cvq_internal.cuh", "df.cuh"],
+    "gate_block": ["k_tile.cu", "k_tile_impl.cuh", "k_gate_impl.cuh", "k_gate_bh_fwd.cu", "k_gate_bkc_fwd.cu",
+                   "cvq_internal.cuh", "df.cuh"],
     "apply_H": ["k_hamiltonian.cu", "k_ham_impl.cuh", "cvq_internal.cuh", "df.cuh"],
 }
 
@@ -201,9 +201,9 @@ def csrc_hash(files=None):
 
 
 def ncu_record(kernel, workload):
-    """The committed ncu figures of `kernel` on `workload` (DRAM bytes per
-    launch, pipe utilisations), if they were captured on the kernel's current
-    sources; None otherwise."""
+    """The committed ncu figures of `kernel` on `workload` (the ratio of DRAM
+    to algorithmic bytes, pipe utilisations), if they were captured on the
+    kernel's current sources; None otherwise."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
@@ -366,16 +366,34 @@ def c5_kernel_leg(hbm, depth=20, reps=2):
         cvq.screen_pool(s, p, psi0, ws=ws)
     torch.cuda.synchronize()
     stats = cvq.profile_stop()
-    out = {}
-    for k, st in stats.items():
-        if st["launches"] == 0 or st["ms"] <= 0:
-            continue
-        gbs = st["bytes"] / st["ms"] / 1e6
-        out[k] = {"launches": st["launches"], "us_per_launch": round(st["ms"] * 1e3 / st["launches"], 2),
-                  "algorithmic_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
-                  "algorithmic_TFLOPs_df": round(st["flops"] / st["ms"] / 1e9, 3)}
+
+    def table(stats):
+        out = {}
+        for k, st in stats.items():
+            if st["launches"] == 0 or st["ms"] <= 0:
+                continue
+            gbs = st["bytes"] / st["ms"] / 1e6
+            out[k] = {"launches": st["launches"], "us_per_launch": round(st["ms"] * 1e3 / st["launches"], 2),
+                      "algorithmic_GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                      "algorithmic_TFLOPs_df": round(st["flops"] / st["ms"] / 1e9, 3)}
+        return out
+
+    out = table(stats)
+    # the energy and gradient again with the forward states kept (the reverse
+    # block step then moves 48 bytes per changed amplitude, the forward 48)
+    states = torch.empty(max(cvq.stored_states_bytes(s, p, ids), 1), dtype=torch.uint8, device="cuda")
+    cvq.energy_and_grad_stored(s, p, ids, th, psi0, states=states, ws=ws)
+    torch.cuda.synchronize()
+    cvq.profile_start(1 << 16)
+    for _ in range(reps):
+        cvq.energy_and_grad_stored(s, p, ids, th, psi0, states=states, ws=ws)
+    torch.cuda.synchronize()
+    stored = table(cvq.profile_stop())
+    del states
     return {"workload": f"kitaev_kerr_open_L10_d6_dim{s.dim}, random_ansatz(210, {depth}, seed 0) + full "
-                        f"210-element screen, x{reps}", "kernels": out}
+                        f"210-element screen, x{reps}", "kernels": out,
+            "stored_states": {k: v for k, v in stored.items() if k in ("gate_block", "adjoint_block", "gate_diag",
+                                                                     "adjoint_diag")}}
 
 
 def mlp_leg(rows=210, reps=200):
@@ -529,8 +547,12 @@ def run_ours(args):
     bytes_per_launch = st["bytes"] / st["launches"]
     achieved = bytes_per_launch / per_launch_s / 1e9
     rec = ncu_record(name, "bh12")
+    # DRAM bytes per launch: the committed ncu ratio of DRAM to algorithmic
+    # bytes over every launch of this kind in one evaluation of the same
+    # workload, times this run's algorithmic bytes per launch
+    ratio = None if rec is None else rec.get("dram_bytes_per_algorithmic_byte")
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None if rec is None else rec.get("dram_bytes_per_launch"),
+            "traffic": None if ratio is None else ratio * bytes_per_launch,
             "kernel": name, "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs",
             "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_s * 1e6,
             "share_of_timed_region": st["ms"] / max(total_ms, 1e-9),

@@ -69,8 +69,15 @@ cudaError_t launch_tile_build(const SectorDev& S, int i, int j, const TypeDesc& 
 
 // ------------------------------------------------------------ gates
 
+// Resident CTAs per SM of the tiled gates: 5 at one slot per thread; at four,
+// 3, except the reverse step that updates both states, which keeps 2 so that
+// its larger staging leaves L1 room (measured faster).
+__host__ __device__ constexpr int tile_ctas_per_sm(bool adj, int slots, bool stored) {
+  return slots == 1 ? 5 : (adj && !stored ? 2 : 3);
+}
+
 template <bool ADJ, bool REALU, int S, bool STORED>
-__global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ && !STORED ? 2 : 3))
+__global__ void __launch_bounds__(NTHREADS, tile_ctas_per_sm(ADJ, S, STORED))
     k_tile_gate(const __grid_constant__ GateArg g, PoolDev P, cdf* psi, cdf* lam, cdf* store,
                 double* __restrict__ partial) {
   extern __shared__ __align__(16) char smem[];
@@ -81,6 +88,8 @@ __global__ void __launch_bounds__(NTHREADS, S == 1 ? 4 : (ADJ && !STORED ? 2 : 3
   if (ADJ) {
     const double s = block_sum(acc_to_double(gacc));
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (blockIdx.x == 0)  // the row's slots past the grid hold zeros for the fixed-order reduction
+      for (int e = gridDim.x + threadIdx.x; e < NBLK; e += blockDim.x) partial[e] = 0.0;
   }
 }
 
@@ -96,10 +105,14 @@ static cudaError_t launch_tile_impl(const GateArg& g, PoolDev P, cdf* psi, cdf* 
     cudaFuncSetAttribute(k_tile_gate<ADJ, false, S, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     attr_set = true;
   }
-  // The reverse step leaves one partial sum per CTA in each of the NBLK slots
-  // of its gradient row (CTAs without a tile write 0); the forward gate needs
-  // no more CTAs than tiles.
-  const int grid = ADJ ? NBLK : (int)std::max<int64_t>(1, std::min<int64_t>(g.tm.ntiles, NBLK));
+  // As many CTAs as fit on the SMs at once, so that no second partial wave
+  // runs, and for the forward gate no more than tiles.  The reverse step
+  // leaves one partial sum per CTA in its gradient row of NBLK slots (CTAs
+  // without a tile write 0, CTA 0 zeroes the slots past the grid), so it
+  // takes at most NBLK CTAs.
+  const int resident = (NBLK / 4) * tile_ctas_per_sm(ADJ, S, STORED);
+  const int grid = ADJ ? std::min(NBLK, resident)
+                       : (int)std::max<int64_t>(1, std::min<int64_t>(g.tm.ntiles, resident));
   if (g.t.realu) k_tile_gate<ADJ, true, S, STORED><<<grid, NTHREADS, sm, st>>>(g, P, psi, lam, store, partial);
   else k_tile_gate<ADJ, false, S, STORED><<<grid, NTHREADS, sm, st>>>(g, P, psi, lam, store, partial);
   return cudaGetLastError();

@@ -32,35 +32,52 @@ __host__ __device__ __forceinline__ size_t tile_head_bytes(const TypeDesc& t, in
   return (b + 15) & ~(size_t)15;
 }
 
+// Stages of the tile pipeline: the amplitudes of the next tile are copied
+// into one stage while the current tile is multiplied out of the other.
+constexpr int TILE_STAGES = 2;
+
 __host__ __device__ __forceinline__ size_t tile_smem_bytes(const TypeDesc& t, int nreg, int nsub, bool adj, int slots) {
-  return tile_head_bytes(t, nreg, nsub, adj) + (size_t)TILE_T * slots * sizeof(cdf) * (adj ? 2 : 1);
+  return tile_head_bytes(t, nreg, nsub, adj) + (size_t)TILE_STAGES * TILE_T * slots * sizeof(cdf) * (adj ? 2 : 1);
 }
 
-// The S slots of one thread in one tile (slot threadIdx.x + q TILE_T), as
-// loaded ahead of their multiply.
-template <int S>
-struct TileSlots {
-  int x[S];       // sector index, -1 if the slot is unused
-  cdf v[S], l[S]; // psi (and lambda) at x
-};
+// 16-byte copy from global to shared memory that completes asynchronously
+// (cp.async); copies are grouped per tile and waited for with
+// cp_async_wait<N> (all but the N most recent groups complete).  L1: through
+// L1 (the forward gate: the two halves of a 32-byte sector read by different
+// warps of a tile come from L2 once), else L2 only (the reverse step, whose
+// two gathered states would only evict each other from L1; measured faster).
+template <bool L1>
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (L1) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+  else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// STORED: psi comes from the gate's stored output values, in slot order
-// (stored[tile TILE_T S + slot]), rather than from the state.
-template <bool ADJ, bool STORED, int S>
-__device__ __forceinline__ void tile_load(TileSlots<S>& s, const TileMap& tm, int64_t tile, const cdf* psi,
-                                          const cdf* lam, const cdf* stored) {
+// The sector indices of this thread's S slots of one tile (streamed: each
+// table entry is read once per gate).
+template <int S>
+__device__ __forceinline__ void tile_idx(int (&x)[S], const TileMap& tm, int64_t tile) {
   const int* ti = tm.idx + tile * (TILE_T * S);
 #pragma unroll
-  for (int q = 0; q < S; ++q) s.x[q] = __ldcs(ti + threadIdx.x + q * TILE_T);  // streamed once per gate
+  for (int q = 0; q < S; ++q) x[q] = __ldcs(ti + threadIdx.x + q * TILE_T);
+}
+
+// Starts the copies of this thread's slots of one tile into a stage: psi (or,
+// STORED, the gate's stored output values, in slot order) and lambda (ADJ).
+template <bool ADJ, bool STORED, int S>
+__device__ __forceinline__ void tile_fetch(const int (&x)[S], int64_t tile, const cdf* psi, const cdf* lam,
+                                           const cdf* store, cdf* sp, cdf* sl) {
 #pragma unroll
   for (int q = 0; q < S; ++q) {
-    s.v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    s.l[q] = s.v[q];
-    if (s.x[q] >= 0) {
-      s.v[q] = STORED ? __ldcs(stored + tile * (TILE_T * S) + threadIdx.x + q * TILE_T) : psi[s.x[q]];
-      if (ADJ) s.l[q] = lam[s.x[q]];
-    }
+    const int slot = threadIdx.x + q * TILE_T;
+    if (x[q] < 0) continue;  // unused slot: no block reads it
+    cp_async16<!ADJ>(sp + slot, STORED ? store + tile * (TILE_T * S) + slot : psi + x[q]);
+    if (ADJ) cp_async16<false>(sl + slot, lam + x[q]);
   }
+  cp_async_commit();
 }
 
 // Region of a tile: the last one whose first tile is <= tile.
@@ -91,8 +108,8 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   char* after_f = reinterpret_cast<char*>(Fs) + ((((size_t)(ADJ ? t.nf : 0) * sizeof(float2)) + 15) & ~(size_t)15);
   TileRegion* Rs = reinterpret_cast<TileRegion*>(after_f);
   TileSub* Ss = reinterpret_cast<TileSub*>(Rs + tm.nreg);
-  cdf* Sp = reinterpret_cast<cdf*>(smem + tile_head_bytes(t, tm.nreg, tm.nsub, ADJ));
-  cdf* Sl = Sp + TILE_T * S;
+  cdf* Sbase = reinterpret_cast<cdf*>(smem + tile_head_bytes(t, tm.nreg, tm.nsub, ADJ));
+  constexpr int kStage = TILE_T * S * (ADJ ? 2 : 1);  // cdf entries of one stage: psi, then lambda
   for (int e = threadIdx.x; e < t.nu; e += blockDim.x) Us[e] = U[e];
   if (ADJ)
     for (int e = threadIdx.x; e < t.nf; e += blockDim.x) Fs[e] = P.F[t.f_base + e];
@@ -100,9 +117,19 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   for (int e = threadIdx.x; e < tm.nsub; e += blockDim.x) Ss[e] = tm.sub[e];
   __syncthreads();
   const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
+  // The pipeline: while the tile in stage stg is multiplied, the copies of the
+  // next tile into stage stg ^ 1 are in flight, and the table entries of the
+  // one after are being loaded into registers.
   int64_t tile = t_begin;
-  TileSlots<S> cur;
-  if (tile < t_end) tile_load<ADJ, STORED, S>(cur, tm, tile, psi, lam, store);
+  int xa[S], xb[S];  // sector indices of the slots of the current and the next tile
+#pragma unroll
+  for (int q = 0; q < S; ++q) xa[q] = xb[q] = -1;
+  if (tile < t_end) {
+    tile_idx<S>(xa, tm, tile);
+    tile_fetch<ADJ, STORED, S>(xa, tile, psi, lam, store, Sbase, Sbase + TILE_T * S);
+  }
+  if (tile + t_step < t_end) tile_idx<S>(xb, tm, tile + t_step);
+  int stg = 0;
   // Where each of this thread's slots sits in its tile depends only on the
   // region (the tiles of a CTA climb through the regions in order), so it is
   // worked out once per region: the block class c, member a and block k of
@@ -111,17 +138,24 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   int64_t reg_end = -1;
   int dec[S];
   while (tile < t_end) {
-    const int64_t next = tile + t_step;
-    __syncthreads();  // every thread has finished reading the previous tile
+    const int64_t next = tile + t_step, next2 = next + t_step;
+    cdf* const Sp = Sbase + stg * kStage;
+    cdf* const Sl = Sp + TILE_T * S;
+    if (next < t_end) {  // stage stg ^ 1 was last read before the barrier that ended the previous tile
+      cdf* const np = Sbase + (stg ^ 1) * kStage;
+      tile_fetch<ADJ, STORED, S>(xb, next, psi, lam, store, np, np + TILE_T * S);
+    } else {
+      cp_async_commit();  // an empty group keeps one group per tile for the wait below
+    }
+    int xc[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) xc[q] = -1;
+    if (next2 < t_end) tile_idx<S>(xc, tm, next2);
+    cp_async_wait<1>();  // this thread's copies of the current tile have landed,
+    __syncthreads();     // and every other thread's
     int xs[S];
 #pragma unroll
-    for (int q = 0; q < S; ++q) {
-      Sp[threadIdx.x + q * TILE_T] = cur.v[q];
-      if (ADJ) Sl[threadIdx.x + q * TILE_T] = cur.l[q];
-      xs[q] = cur.x[q];
-    }
-    __syncthreads();
-    if (next < t_end) tile_load<ADJ, STORED, S>(cur, tm, next, psi, lam, store);  // in flight during the multiply
+    for (int q = 0; q < S; ++q) xs[q] = xa[q];
     if (tile >= reg_end) {
       reg = tile_region(Rs, tm.nreg, tile);
       const TileRegion R = Rs[reg];
@@ -204,6 +238,13 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
       psi[x] = make_cdf(acc_get(ar), acc_get(ai));
       lam[x] = make_cdf(acc_get(br), acc_get(bi));
     }
+    __syncthreads();  // every thread has finished reading stage stg before it is refilled
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      xa[q] = xb[q];
+      xb[q] = xc[q];
+    }
+    stg ^= 1;
     tile = next;
   }
 }

@@ -167,6 +167,9 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--target", choices=["kitaev", "bh", "sweep"], default="kitaev")
     ap.add_argument("--count", type=int, default=8, help="instances of the sweep target")
+    ap.add_argument("--Ls", type=int, nargs="+", default=[4], help="chain lengths of the sweep target (N = L)")
+    ap.add_argument("--U-range", type=float, nargs=2, default=[1.0, 4.0],
+                    help="U/J of the sweep target, log-uniform in this range")
     ap.add_argument("--L", type=int, default=10)
     ap.add_argument("--U", type=float, default=3.4, help="U/J of the Bose-Hubbard target")
     ap.add_argument("--d", type=int, default=6)
@@ -192,13 +195,14 @@ def main(argv=None):
     t_train = time.perf_counter() - t0
 
     if a.target == "sweep":
-        insts = sweep_instances(a.count, 100)
+        insts = sweep_instances(a.count, 100, Ls=tuple(a.Ls), U_range=tuple(a.U_range))
         E0s = []
         for (m, *_rest) in insts:
             E0s.append(adapt.ground_energy(cvq.Sector(m)))
         arms = race_sweep(insts, E0s, scorer, tr, max_ops=a.max_ops, hessian_recycling=a.hessian_recycling,
                           top_k=a.top_k, full_every=a.full_every)
-        out = dict(target=dict(model="open Bose-Hubbard chains L = 4, N = 4, U/J log-uniform [1, 4]",
+        out = dict(target=dict(model=f"open Bose-Hubbard chains L = N in {list(a.Ls)}, U/J log-uniform "
+                                     f"[{a.U_range[0]}, {a.U_range[1]}]", max_ops=a.max_ops,
                                instances=[x[0].name for x in insts], E0=E0s, pool="all pairs",
                                tolerance=1e-6),
                    training=dict(lists=len(tr.X), rows=tr.rows(), seconds=t_train,
