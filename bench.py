@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--no-race", action="store_true", help="skip the learned-vs-plain wall-time race")
     ap.add_argument("--instances", type=int, default=len(U_VALUES),
                     help="use the first n of the U/J instances (profiling runs)")
+    ap.add_argument("--sequential", action="store_true",
+                    help="run the instances one after another on one stream instead of concurrently, one host "
+                         "thread and CUDA stream each")
     a = ap.parse_args()
     if not 1 <= a.instances <= len(U_VALUES):
         ap.error(f"--instances must be in [1, {len(U_VALUES)}]")
@@ -465,12 +468,30 @@ def run_ours(args):
     insts = make_instances(rank)[: args.instances]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def one_step():
-        recs = []
-        for A in insts:
+    # The instances are independent ADAPT runs: each runs its iteration on its
+    # own CUDA stream from its own host thread, so that one instance's kernels
+    # fill the SMs another's leave idle (latency-bound gates, host turns of
+    # BFGS).  Every library call goes to the calling thread's current stream.
+    from concurrent.futures import ThreadPoolExecutor
+    streams = [torch.cuda.Stream() for _ in insts]
+    workers = ThreadPoolExecutor(max_workers=len(insts))
+
+    def one_instance(i, pre=None, post=None):
+        A = insts[i]
+        with torch.cuda.stream(streams[i]):
             restore(A)
-            recs.append(A.step())
-        return recs
+            if pre is not None:
+                pre(i, A)
+            rec = A.step()
+            if post is not None:
+                post(i, A)
+            streams[i].synchronize()
+        return rec
+
+    def one_step(pre=None, post=None):
+        if args.sequential:
+            return [one_instance(i, pre, post) for i in range(len(insts))]
+        return list(workers.map(lambda i: one_instance(i, pre, post), range(len(insts))))
 
     for _ in range(args.warmup):
         one_step()
@@ -481,9 +502,23 @@ def run_ours(args):
     barrier(ws)
     torch.cuda.synchronize()
     sampler.start()
+    # With the instances concurrent, a launch's event-timed duration includes
+    # the other streams' kernels sharing the GPU, so the per-kernel figures
+    # (roofline, shares, launch count) come from a second pass of the same
+    # iteration with the instances one after another (below); the live
+    # profiler then runs in the timed region only when that is how it is run.
+    profile_timed = args.sequential
+
+    def profiled_steps(steps, body):
+        cvq.profile_sample(16)  # one event pair per 16 launches of a kind keeps the launch path short
+        cvq.profile_start(400000)
+        body(steps)
+        return cvq.profile_stop()
+
     torch.cuda.profiler.start()  # the timed region, for profilers started with --profile-from-start off
-    cvq.profile_sample(16)  # one event pair per 16 launches of a kind keeps the launch path short
-    cvq.profile_start(400000)
+    if profile_timed:
+        cvq.profile_sample(16)
+        cvq.profile_start(400000)
     total_ms = 0.0
     iters = 0
     nfev, ngates = [], []
@@ -500,7 +535,7 @@ def run_ours(args):
             iters += 1
             nfev.append(r["nfev"])
             ngates.append(r["n"])
-    stats = cvq.profile_stop()
+    stats = cvq.profile_stop() if profile_timed else None
     torch.cuda.profiler.stop()
     clocks = sampler.stop()
     torch.cuda.synchronize()
@@ -509,6 +544,24 @@ def run_ours(args):
     iters_all = sum_over_ranks(float(iters), ws)
     value = iters_all / t_max
     nfev_inst = [r["nfev"] for r in one_step()]  # the fixed iteration's evaluations, per instance
+    profile_ms = total_ms
+    if stats is None:  # the kernel figures: the same steps, instances one after another, live events
+        pms = [0.0]
+
+        def seq_steps(steps):
+            for k in range(steps):
+                flush.fill_(float(k))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for i in range(len(insts)):
+                    one_instance(i)
+                e1.record(stream)
+                e1.synchronize()
+                pms[0] += e0.elapsed_time(e1)
+
+        stats = profiled_steps(args.steps, seq_steps)
+        profile_ms = pms[0]
 
     # ---- e2e: same iteration through the public API with host buffers
     e2e = None
@@ -517,23 +570,27 @@ def run_ours(args):
         host_out = torch.empty(len(insts) * 161, dtype=torch.float64, pin_memory=True)
         bi = sum(h.numel() * 16 for h in host_psi)
         e_ms, e_it, bo = 0.0, 0, 0
+        out_bytes = [0] * len(insts)
+
+        def h2d(i, A):  # this step's reference state from pinned host memory
+            A.psi0.copy_(host_psi[i], non_blocking=True)
+
+        def d2h(i, A):  # energy and gradient back to pinned host memory
+            n = len(A.ids)
+            host_out[161 * i: 161 * i + n + 1].copy_(A._out[: n + 1], non_blocking=True)
+            out_bytes[i] = 8 * (n + 1)
+
         for k in range(args.steps):
             flush.fill_(float(k))
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            bo = 0
-            for A, hp in zip(insts, host_psi):
-                A.psi0.copy_(hp, non_blocking=True)
-                restore(A)
-                A.step()
-                n = len(A.ids)
-                host_out[bo // 8: bo // 8 + n + 1].copy_(A._out[: n + 1], non_blocking=True)
-                bo += 8 * (n + 1)
-                e_it += 1
+            one_step(h2d, d2h)
+            e_it += len(insts)
             e1.record(stream)
             e1.synchronize()
             e_ms += e0.elapsed_time(e1)
+            bo = sum(out_bytes)
         e_t = max_over_ranks(e_ms / 1e3, ws)
         e2e = {"value": sum_over_ranks(float(e_it), ws) / e_t, "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo,
@@ -542,6 +599,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel: algorithmic bytes over live launch time, against HBM
     hbm, src = peaks()
+    total_ms_kernels = profile_ms  # the time the per-kernel figures were taken over
     name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
     per_launch_s = st["ms"] / 1e3 / st["launches"]
     bytes_per_launch = st["bytes"] / st["launches"]
@@ -555,7 +613,9 @@ def run_ours(args):
             "traffic": None if ratio is None else ratio * bytes_per_launch,
             "kernel": name, "peak_source": f"{src} MEASURED_PEAKS.json hbm_gbs",
             "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_s * 1e6,
-            "share_of_timed_region": st["ms"] / max(total_ms, 1e-9),
+            "share_of_timed_region": st["ms"] / max(total_ms_kernels, 1e-9),
+            "measured_over": "the timed steps" if profile_timed else
+            "the same steps run again with the instances one after another (each kernel alone on the GPU)",
             "fp32_pipe": None if rec is None else {k: rec.get(k) for k in ("fma_pipe_pct", "alu_pipe_pct",
                                                                           "issue_active_pct", "warps_active_pct")},
             "note": "arithmetic is double-float on the FP32 pipe; the 21.6 MB states are L2-resident, so the "
@@ -611,7 +671,11 @@ def run_ours(args):
                        "pool": insts[0].K, "warm_start_gates": WARM_GATES, "adapt_ops_before": N_PRE,
                        "ansatz_len_in_bfgs": int(np.mean(ngates)), "bfgs_evals_per_iter": nfev_inst,
                        "l2": "256 MB buffer written between steps",
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}",
+                       "instances_run": "one after another on one stream" if args.sequential else
+                       "concurrently, one host thread and CUDA stream per instance",
+                       "energy_and_gradient": "stored forward states" if all(A.stored_states for A in insts)
+                       else "recomputed states"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "fixed_ansatz": fixed, "c5_kernels": c5, "c4_batched": c4, "mlp": mlp, "race": race_out,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in stats.items()},

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -89,7 +90,7 @@ struct ProfRec {
 };
 
 static std::mutex g_prof_mu;
-static bool g_prof_on = false;
+static std::atomic<bool> g_prof_on{false};  // read without the lock on every launch
 static std::vector<ProfRec> g_prof;
 static size_t g_prof_n = 0;
 static int g_prof_every = 1;                 // time one launch in this many of each kind
@@ -1406,10 +1407,10 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
       diag_run_arg(s, p, op_ids, theta, g, a);
       cdf* pst = sto ? sto : psi;  // psi at the run's output
       // gradients of gates DIAG_ACC.. at the run's output state, before the reverse pass undoes the phases
-      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_ACC) {
+      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_GRAD_ACC) {
         DiagGradArg ga;
         memset(&ga, 0, sizeof ga);
-        ga.m = std::min(DIAG_ACC, g.m - q0);
+        ga.m = std::min(DIAG_GRAD_ACC, g.m - q0);
         for (int q = 0; q < ga.m; ++q) {
           ga.diag[q] = a.diag[q0 + q];
           ga.gi[q] = a.gi[q0 + q];
@@ -1578,10 +1579,10 @@ extern "C" int cvq_energy_and_grad_projected(const cvq_sector* s, const cvq_pool
       DiagRunArg a;
       diag_run_arg(s, p, op_ids, theta, g, a);
       cdf* psi = slot(si + 1);
-      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_ACC) {
+      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_GRAD_ACC) {
         DiagGradArg ga;
         memset(&ga, 0, sizeof ga);
-        ga.m = std::min(DIAG_ACC, g.m - q0);
+        ga.m = std::min(DIAG_GRAD_ACC, g.m - q0);
         for (int q = 0; q < ga.m; ++q) {
           ga.diag[q] = a.diag[q0 + q];
           ga.gi[q] = a.gi[q0 + q];

@@ -527,10 +527,14 @@ cudaError_t launch_tile_gate_stored(const GateArg& g, PoolDev P, const cdf* stor
                                     cudaStream_t st);
 cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P, cdf* psi, cdf* lam, double* partial,
                                 cudaStream_t st);
-// Gradient-only pass over up to DIAG_ACC gates of a diagonal run (their f type and modes).
+// Gradient-only pass over up to DIAG_GRAD_ACC gates of a diagonal run (their
+// f type and modes): the gates of a run beyond the reverse pass's DIAG_ACC,
+// so that a run of up to DIAG_ACC + DIAG_GRAD_ACC gates (a warm-start layer's
+// Kerr and rotation gates on every mode) takes one extra pass.
+constexpr int DIAG_GRAD_ACC = 16;
 struct DiagGradArg {
   int m;
-  int diag[DIAG_ACC], gi[DIAG_ACC], gj[DIAG_ACC];
+  int diag[DIAG_GRAD_ACC], gi[DIAG_GRAD_ACC], gj[DIAG_GRAD_ACC];
 };
 cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf* psi, const cdf* lam, double* partial,
                              cudaStream_t st);

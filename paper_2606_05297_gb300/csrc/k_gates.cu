@@ -84,12 +84,14 @@ static cudaError_t launch_gate_impl(const SectorDev& S, const GateArg& g, PoolDe
   constexpr int kMaxSmem = 200 * 1024;
   const size_t sm = gate_smem_bytes(g.t, S.kind);
   if (sm > (size_t)kMaxSmem) return cudaErrorInvalidValue;
-  static bool attr_set = false;  // one opt-in to the largest dynamic shared memory a gate can need
-  if (!attr_set) {
+  // one opt-in to the largest dynamic shared memory a gate can need (a
+  // function-local static: done once, also when several host threads launch)
+  static const bool attr_set = [] {
     set_block_smem_limit<CVQ_BH, ADJ>(kMaxSmem);
     set_block_smem_limit<CVQ_BKC, ADJ>(kMaxSmem);
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   if (S.kind == CVQ_BH) launch_block<CVQ_BH, ADJ>(S, g, P, src, dst, lam, partial, sm, st);
   else launch_block<CVQ_BKC, ADJ>(S, g, P, src, dst, lam, partial, sm, st);
   return cudaGetLastError();
@@ -141,35 +143,40 @@ __global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ S
   }
 }
 
+// Two CTAs per SM (its 16 accumulators take about 120 registers), so half the
+// NBLK partial slots of each gradient row; CTA 0 zeroes the other half.
 template <int KIND>
-__global__ void __launch_bounds__(NTHREADS) k_diag_grad(const __grid_constant__ SectorDev S,
+__global__ void __launch_bounds__(NTHREADS, 2) k_diag_grad(const __grid_constant__ SectorDev S,
                                                         const __grid_constant__ DiagGradArg a, const cdf* psi,
                                                         const cdf* lam, double* partial) {
   __shared__ int64_t Gs[LMAX][DMAX + 1];
   __shared__ uint64_t wbuf[(KIND == CVQ_BH) ? NTHREADS / 32 * 32 * WALK_RMAX : 1];
   if (KIND == CVQ_BH) load_G(Gs, S);
   __syncthreads();
-  dfacc acc[DIAG_ACC];
+  dfacc acc[DIAG_GRAD_ACC];
 #pragma unroll
-  for (int k = 0; k < DIAG_ACC; ++k) acc_zero(acc[k]);
+  for (int k = 0; k < DIAG_GRAD_ACC; ++k) acc_zero(acc[k]);
   if (KIND == CVQ_BH)
-    bh_walk(S, Gs, wbuf, 0, S.dim, [&](int64_t x, uint64_t w) { diag_grad_one<DIAG_ACC>(a, psi, lam, x, w, acc); });
+    bh_walk(S, Gs, wbuf, 0, S.dim,
+            [&](int64_t x, uint64_t w) { diag_grad_one<DIAG_GRAD_ACC>(a, psi, lam, x, w, acc); });
   else
-    diag_grad_range<KIND, DIAG_ACC>(S, Gs, a, psi, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
-                                    (int64_t)gridDim.x * blockDim.x, acc);
+    diag_grad_range<KIND, DIAG_GRAD_ACC>(S, Gs, a, psi, lam, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim,
+                                         (int64_t)gridDim.x * blockDim.x, acc);
 #pragma unroll
-  for (int k = 0; k < DIAG_ACC; ++k) {
+  for (int k = 0; k < DIAG_GRAD_ACC; ++k) {
     if (k < a.m) {
       const double s = block_sum(acc_to_double(acc[k]));
       if (threadIdx.x == 0) partial[(size_t)k * NBLK + blockIdx.x] = s;
+      if (blockIdx.x == 0)
+        for (int e = gridDim.x + threadIdx.x; e < NBLK; e += blockDim.x) partial[(size_t)k * NBLK + e] = 0.0;
     }
   }
 }
 
 cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf* psi, const cdf* lam, double* partial,
                              cudaStream_t st) {
-  if (S.kind == CVQ_BH) k_diag_grad<CVQ_BH><<<NBLK, NTHREADS, 0, st>>>(S, a, psi, lam, partial);
-  else k_diag_grad<CVQ_BKC><<<NBLK, NTHREADS, 0, st>>>(S, a, psi, lam, partial);
+  if (S.kind == CVQ_BH) k_diag_grad<CVQ_BH><<<NBLK / 2, NTHREADS, 0, st>>>(S, a, psi, lam, partial);
+  else k_diag_grad<CVQ_BKC><<<NBLK / 2, NTHREADS, 0, st>>>(S, a, psi, lam, partial);
   return cudaGetLastError();
 }
 

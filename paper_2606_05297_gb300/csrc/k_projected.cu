@@ -136,12 +136,12 @@ cudaError_t launch_gate_proj_adj(const SectorDev& S, const GateArg& g, const cdf
   const size_t sm = proj_tables_bytes(g.t) + (size_t)NTHREADS * g.t.bmax * sizeof(cdf);
   constexpr int kMaxSmem = 200 * 1024;
   if (sm > (size_t)kMaxSmem) return cudaErrorInvalidValue;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static const bool attr_set = [] {  // once, also when several host threads launch
     cudaFuncSetAttribute(k_gate_proj_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_gate_proj_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   if (g.t.realu) k_gate_proj_adj<true><<<NBLK, NTHREADS, sm, st>>>(S, g, D, P, prev, cur, lam, rdot, n2, partial);
   else k_gate_proj_adj<false><<<NBLK, NTHREADS, sm, st>>>(S, g, D, P, prev, cur, lam, rdot, n2, partial);
   return cudaGetLastError();

@@ -99,12 +99,14 @@ static cudaError_t launch_tile_impl(const GateArg& g, PoolDev P, cdf* psi, cdf* 
   const size_t sm = tile_smem_bytes(g.t, g.tm.nreg, g.tm.nsub, ADJ, S);
   constexpr int kMaxSmem = 110 * 1024;
   if (sm > (size_t)kMaxSmem) return cudaErrorInvalidValue;
-  static bool attr_set = false;  // one opt-in to the largest dynamic shared memory a gate can need
-  if (!attr_set) {
+  // one opt-in to the largest dynamic shared memory a gate can need (a
+  // function-local static: done once, also when several host threads launch)
+  static const bool attr_set = [] {
     cudaFuncSetAttribute(k_tile_gate<ADJ, true, S, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_tile_gate<ADJ, false, S, STORED>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   // As many CTAs as fit on the SMs at once, so that no second partial wave
   // runs, and for the forward gate no more than tiles.  The reverse step
   // leaves one partial sum per CTA in its gradient row of NBLK slots (CTAs
