@@ -217,12 +217,14 @@ class Adapt:
         self._subset = list(range(self.K))
         self.nfev_total = 0
         # The reverse sweep reads the forward states kept in device memory
-        # (cvq_energy_and_grad_stored) instead of recomputing them, when their
-        # worst case (one full state per gate) fits in a quarter of the free
-        # device memory, or when asked to.
+        # (cvq_energy_and_grad_stored) instead of recomputing them, when asked
+        # to, or by default on sectors of at least 2^20 amplitudes (below that
+        # the launches, not the arithmetic, bound an evaluation, and the extra
+        # copies cost more than they save) whose worst case (one full state per
+        # gate) fits in a quarter of the free device memory.
         if stored_states is None:
             free, _ = torch.cuda.mem_get_info()
-            stored_states = n_max * self.sector.dim * 16 <= free // 4
+            stored_states = self.sector.dim >= (1 << 20) and n_max * self.sector.dim * 16 <= free // 4
         self.stored_states = bool(stored_states)
         self._states = None
         self._states_key = None
