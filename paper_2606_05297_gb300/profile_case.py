@@ -2,6 +2,7 @@
 evaluations of a random ansatz on one workload.
 
     python -m paper_2606_05297_gb300.profile_case --workload bh12 --depth 40 --reps 3 [--warm 5] [--stored]
+        [--op hop:6:7:1]
 
 Workloads: bh12 (Bose-Hubbard L=12, N=12 periodic, 1,352,078 amplitudes),
 bkc8 (Kitaev chain + Kerr L=8, d=8, 8,388,608 amplitudes), bkc10 (L=10, d=6,
@@ -44,6 +45,9 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--warm", type=int, default=0, help="unprofiled repetitions before cudaProfilerStart")
     ap.add_argument("--kernels", action="store_true", help="print per-kernel event timings of the profiled range")
+    ap.add_argument("--op", default=None,
+                    help="one pool element, type:i:j:phase (e.g. hop:6:7:1), repeated --depth times instead of a "
+                         "random ansatz")
     ap.add_argument("--stored", action="store_true",
                     help="keep the forward states for the reverse sweep (cvq_energy_and_grad_stored)")
     ap.add_argument("--projected", type=int, default=0,
@@ -75,6 +79,13 @@ def main():
     s = cvq.Sector(m)
     p = cvq.ProjectedPool(s, pool, a.projected) if a.projected else cvq.Pool(s, pool)
     ids, th = W.random_ansatz(len(pool), a.depth, a.seed, scale=0.2)
+    if a.op is not None:
+        t, i, j, ph = a.op.split(":")
+        want = (t, int(i), int(j) if j else -1, int(ph))
+        k = [q for q, o in enumerate(pool) if (o.type, o.i, o.j, o.phase) == want]
+        if not k:
+            raise SystemExit(f"no pool element {a.op}")
+        ids = [k[0]] * a.depth
     psi0 = torch.from_numpy(W.random_state(s.dim, a.seed + 1)).cuda()
     ws = s.workspace(p, a.depth)
     if a.projected:
