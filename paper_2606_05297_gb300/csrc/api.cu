@@ -886,6 +886,7 @@ static int check_ws(const cvq_sector* s, const cvq_pool* p, int n, void* ws, siz
 struct OpCost {
   double fb, ff, ab, af;
   double amps;  // amplitudes the gate changes
+  double af_stored;  // reverse step with psi read from the stored forward states (no U^dag psi)
 };
 
 static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
@@ -899,11 +900,12 @@ static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
   if (t.diag) {
     c.ff = 8.0 * dim;
     c.af = 24.0 * dim;
+    c.af_stored = 16.0 * dim;
     return c;
   }
   // Blocks of one member have a zero generator: the gate is the identity there
   // and the kernels skip them, so they count neither bytes nor flops.
-  double ff = 0.0, af = 0.0, amps = 0.0;
+  double ff = 0.0, af = 0.0, afs = 0.0, amps = 0.0;
   for (int cls = 0; cls < t.nclass; ++cls) {
     double orbits;
     if (S.kind == CVQ_BH) {
@@ -914,22 +916,25 @@ static OpCost op_cost(const cvq_sector* s, const cvq_pool* p, int op) {
       for (int r = 0; r < S.L - nm; ++r) items *= S.D;
       orbits = (S.L == nm) ? (cls == S.parity ? 1.0 : 0.0) : items / 2.0;
     }
-    double bf = 0.0, baf = 0.0;
+    double bf = 0.0, baf = 0.0, bafs = 0.0;
     for (int bi = t.class_off[cls]; bi < t.class_off[cls + 1]; ++bi) {
       const int b = p->blk_size[t.blk_base + bi];
       if (b < 2) continue;
       bf += 8.0 * b * b;
       baf += 8.0 * (2.0 * b * b + 3.0 * b - 2.0);
+      bafs += 8.0 * (1.0 * b * b + 3.0 * b - 2.0);
       amps += orbits * b;
     }
     ff += orbits * bf;
     af += orbits * baf;
+    afs += orbits * bafs;
   }
   c.fb = 32.0 * amps;
   c.ab = 64.0 * amps;
   c.amps = amps;
   c.ff = ff;
   c.af = af;
+  c.af_stored = afs;
   return c;
 }
 
@@ -1427,7 +1432,7 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
       const GateArg ga = gate_arg(p, op_ids[g.k0], U + (size_t)g.k0 * p->ustride);
       const OpCost c = op_cost(s, p, op_ids[g.k0]);
       if (sto && ga.tm.idx) {  // psi from the stored slots, lambda only
-        ProfScope ps(KK_ADJ, st, 48.0 * c.amps, c.af);
+        ProfScope ps(KK_ADJ, st, 48.0 * c.amps, c.af_stored);
         CVQ_CUDA(launch_tile_gate_stored(ga, p->P, sto, lam, partial + (size_t)g.k0 * NBLK, st), "adjoint gate");
         continue;
       }
