@@ -110,12 +110,6 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   TileSub* Ss = reinterpret_cast<TileSub*>(Rs + tm.nreg);
   cdf* Sbase = reinterpret_cast<cdf*>(smem + tile_head_bytes(t, tm.nreg, tm.nsub, ADJ));
   constexpr int kStage = TILE_T * S * (ADJ ? 2 : 1);  // cdf entries of one stage: psi, then lambda
-  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) Us[e] = U[e];
-  if (ADJ)
-    for (int e = threadIdx.x; e < t.nf; e += blockDim.x) Fs[e] = P.F[t.f_base + e];
-  for (int e = threadIdx.x; e < tm.nreg; e += blockDim.x) Rs[e] = tm.reg[e];
-  for (int e = threadIdx.x; e < tm.nsub; e += blockDim.x) Ss[e] = tm.sub[e];
-  __syncthreads();
   const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
   // The pipeline: while the tile in stage stg is multiplied, the copies of the
   // next tile into stage stg ^ 1 are in flight, and the table entries of the
@@ -124,11 +118,18 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   int xa[S], xb[S];  // sector indices of the slots of the current and the next tile
 #pragma unroll
   for (int q = 0; q < S; ++q) xa[q] = xb[q] = -1;
-  if (tile < t_end) {
-    tile_idx<S>(xa, tm, tile);
-    tile_fetch<ADJ, STORED, S>(xa, tile, psi, lam, store, Sbase, Sbase + TILE_T * S);
-  }
+  if (tile < t_end) tile_idx<S>(xa, tm, tile);
   if (tile + t_step < t_end) tile_idx<S>(xb, tm, tile + t_step);
+  // The gate's tables, while those table entries are in flight: the block
+  // unitaries by asynchronous copy (in the first tile's group), the rest
+  // directly; the barrier of the first tile orders them before any use.
+  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) cp_async16<true>(Us + e, U + e);
+  if (ADJ)
+    for (int e = threadIdx.x; e < t.nf; e += blockDim.x) Fs[e] = P.F[t.f_base + e];
+  for (int e = threadIdx.x; e < tm.nreg; e += blockDim.x) Rs[e] = tm.reg[e];
+  for (int e = threadIdx.x; e < tm.nsub; e += blockDim.x) Ss[e] = tm.sub[e];
+  if (tile < t_end) tile_fetch<ADJ, STORED, S>(xa, tile, psi, lam, store, Sbase, Sbase + TILE_T * S);
+  else cp_async_commit();
   int stg = 0;
   // Where each of this thread's slots sits in its tile depends only on the
   // region (the tiles of a CTA climb through the regions in order), so it is
@@ -247,6 +248,7 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
     stg ^= 1;
     tile = next;
   }
+  cp_async_wait<0>();  // nothing stays in flight into shared memory past the call
 }
 
 }  // namespace cvq
