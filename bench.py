@@ -59,7 +59,7 @@ DTYPE = "df64 (double-float: 2 x fp32, about 2^-48 relative) arithmetic on compl
 # BFGS evaluations of the fixed timed iteration of each instance (U/J = 1, 3.4,
 # 10), as the GPU arm measures them; the reference arm scales its sample with
 # these so that both arms describe the same iteration.
-FIXED_NFEV = (180, 215, 401)
+FIXED_NFEV = (180, 215, 274)
 
 
 def parse():

@@ -1411,8 +1411,8 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
       DiagRunArg a;
       diag_run_arg(s, p, op_ids, theta, g, a);
       cdf* pst = sto ? sto : psi;  // psi at the run's output
-      // gradients of gates DIAG_ACC.. at the run's output state, before the reverse pass undoes the phases
-      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_GRAD_ACC) {
+      // gradients of the gates past the reverse pass's accumulators, at the run's output state, before the reverse pass undoes the phases
+      for (int q0 = diag_run_acc(g.m); q0 < g.m; q0 += DIAG_GRAD_ACC) {
         DiagGradArg ga;
         memset(&ga, 0, sizeof ga);
         ga.m = std::min(DIAG_GRAD_ACC, g.m - q0);
@@ -1425,7 +1425,7 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
         CVQ_CUDA(launch_diag_grad(s->S, ga, pst, lam, partial + (size_t)(g.k0 + q0) * NBLK, st), "diagonal-run gradients");
       }
       ProfScope ps(KK_ADJ_DIAG, st, sto ? 48.0 * dim : 64.0 * dim,
-                   dim * (8.0 * s->S.L + 8.0 * a.npair + 24.0 + 4.0 * std::min(g.m, DIAG_ACC)));
+                   dim * (8.0 * s->S.L + 8.0 * a.npair + 24.0 + 4.0 * std::min(g.m, diag_run_acc(g.m))));
       CVQ_CUDA(launch_diag_run(s->S, a, pst, pst, lam, partial + (size_t)g.k0 * NBLK, true, st, sto != nullptr),
                "adjoint diagonal run");
     } else {
@@ -1584,7 +1584,7 @@ extern "C" int cvq_energy_and_grad_projected(const cvq_sector* s, const cvq_pool
       DiagRunArg a;
       diag_run_arg(s, p, op_ids, theta, g, a);
       cdf* psi = slot(si + 1);
-      for (int q0 = DIAG_ACC; q0 < g.m; q0 += DIAG_GRAD_ACC) {
+      for (int q0 = diag_run_acc(g.m); q0 < g.m; q0 += DIAG_GRAD_ACC) {
         DiagGradArg ga;
         memset(&ga, 0, sizeof ga);
         ga.m = std::min(DIAG_GRAD_ACC, g.m - q0);

@@ -393,7 +393,12 @@ struct BuildArgs {
 // per cross-Kerr gate (built on the host in FP64, passed by value).  The
 // reverse pass forms every gradient of the run from the same (psi, lambda).
 constexpr int MAX_RUN = 32, MAX_RUN_PAIRS = 4;
-constexpr int DIAG_ACC = 8;  // gradient accumulators of one diagonal-run reverse pass
+// Gradient accumulators of one diagonal-run reverse pass: 8, or 24 for runs of
+// more than 8 gates (a warm-start layer's Kerr and rotation gates on every
+// mode), whose kernel then runs two CTAs per SM; gates beyond that take
+// gradient-only passes.
+constexpr int DIAG_ACC = 8, DIAG_ACC_LONG = 24;
+__host__ __device__ constexpr int diag_run_acc(int m) { return m > DIAG_ACC ? DIAG_ACC_LONG : DIAG_ACC; }
 struct DiagRunArg {
   int m, npair;
   int diag[MAX_RUN], gi[MAX_RUN], gj[MAX_RUN];   // per gate: f type (1..4) and modes

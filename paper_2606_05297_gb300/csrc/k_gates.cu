@@ -108,10 +108,14 @@ cudaError_t launch_gate_adjoint(const SectorDev& S, const GateArg& g, PoolDev P,
 
 // ------------------------------------------------------------ diagonal runs
 
-// One run per launch, phase tables built on the host in FP64.
-template <int KIND, bool ADJ, bool KEEP>
-__global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ SectorDev S, const __grid_constant__ DiagRunArg a,
-                                                       const cdf* src, cdf* dst, cdf* lam, double* partial) {
+// One run per launch, phase tables built on the host in FP64.  NACC: the
+// gradient accumulators of the reverse pass (diag_run_acc); with 24 the
+// registers allow two CTAs per SM, so the grid is NBLK / 2 and CTA 0 zeroes
+// the other half of each gradient row's partial slots.
+template <int KIND, bool ADJ, bool KEEP, int NACC>
+__global__ void __launch_bounds__(NTHREADS, NACC > DIAG_ACC ? 2 : 4)
+    k_diag_run(const __grid_constant__ SectorDev S, const __grid_constant__ DiagRunArg a, const cdf* src, cdf* dst,
+               cdf* lam, double* partial) {
   __shared__ int64_t Gs[LMAX][DMAX + 1];
   __shared__ cdf T[LMAX][DMAX];
   __shared__ cdf TP[MAX_RUN_PAIRS][DMAX * DMAX];
@@ -121,23 +125,25 @@ __global__ void __launch_bounds__(NTHREADS) k_diag_run(const __grid_constant__ S
   for (int e = threadIdx.x; e < a.npair * DMAX * DMAX; e += blockDim.x)
     TP[e / (DMAX * DMAX)][e % (DMAX * DMAX)] = a.TP[e / (DMAX * DMAX)][e % (DMAX * DMAX)];
   __syncthreads();
-  // Reverse: gradients of the run's first DIAG_ACC gates; the host launches
+  // Reverse: gradients of the run's first NACC gates; the host launches
   // k_diag_grad beforehand for the rest.
-  dfacc acc[DIAG_ACC];
+  dfacc acc[NACC];
 #pragma unroll
-  for (int k = 0; k < DIAG_ACC; ++k) acc_zero(acc[k]);
+  for (int k = 0; k < NACC; ++k) acc_zero(acc[k]);
   if (KIND == CVQ_BH)
     bh_walk(S, Gs, wbuf, 0, S.dim,
-            [&](int64_t x, uint64_t w) { diag_run_one<ADJ, DIAG_ACC, DiagRunArg, KEEP>(S, T, TP, a, src, dst, lam, x, w, acc); });
+            [&](int64_t x, uint64_t w) { diag_run_one<ADJ, NACC, DiagRunArg, KEEP>(S, T, TP, a, src, dst, lam, x, w, acc); });
   else
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S.dim; x += (int64_t)gridDim.x * blockDim.x)
-      diag_run_one<ADJ, DIAG_ACC, DiagRunArg, KEEP>(S, T, TP, a, src, dst, lam, x, bkc_unrank(x, S), acc);
+      diag_run_one<ADJ, NACC, DiagRunArg, KEEP>(S, T, TP, a, src, dst, lam, x, bkc_unrank(x, S), acc);
   if (ADJ) {
 #pragma unroll
-    for (int k = 0; k < DIAG_ACC; ++k) {
+    for (int k = 0; k < NACC; ++k) {
       if (k < a.m) {
         const double s = block_sum(acc_to_double(acc[k]));
         if (threadIdx.x == 0) partial[(size_t)k * NBLK + blockIdx.x] = s;
+        if (blockIdx.x == 0)
+          for (int e = gridDim.x + threadIdx.x; e < NBLK; e += blockDim.x) partial[(size_t)k * NBLK + e] = 0.0;
       }
     }
   }
@@ -180,18 +186,27 @@ cudaError_t launch_diag_grad(const SectorDev& S, const DiagGradArg& a, const cdf
   return cudaGetLastError();
 }
 
+template <int KIND>
+static void launch_diag_run_kind(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
+                                 double* partial, bool adjoint, cudaStream_t st, bool keep_psi) {
+  if (!adjoint) {
+    k_diag_run<KIND, false, false, DIAG_ACC><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+  } else if (diag_run_acc(a.m) == DIAG_ACC) {
+    if (keep_psi) k_diag_run<KIND, true, true, DIAG_ACC><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    else k_diag_run<KIND, true, false, DIAG_ACC><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+  } else {
+    if (keep_psi)
+      k_diag_run<KIND, true, true, DIAG_ACC_LONG><<<NBLK / 2, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+    else
+      k_diag_run<KIND, true, false, DIAG_ACC_LONG><<<NBLK / 2, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
+  }
+}
+
 cudaError_t launch_diag_run(const SectorDev& S, const DiagRunArg& a, const cdf* src, cdf* dst, cdf* lam,
                             double* partial, bool adjoint, cudaStream_t st, bool keep_psi) {
   if (keep_psi && !adjoint) return cudaErrorInvalidValue;
-  if (S.kind == CVQ_BH) {
-    if (keep_psi) k_diag_run<CVQ_BH, true, true><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
-    else if (adjoint) k_diag_run<CVQ_BH, true, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
-    else k_diag_run<CVQ_BH, false, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
-  } else {
-    if (keep_psi) k_diag_run<CVQ_BKC, true, true><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
-    else if (adjoint) k_diag_run<CVQ_BKC, true, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
-    else k_diag_run<CVQ_BKC, false, false><<<NBLK, NTHREADS, 0, st>>>(S, a, src, dst, lam, partial);
-  }
+  if (S.kind == CVQ_BH) launch_diag_run_kind<CVQ_BH>(S, a, src, dst, lam, partial, adjoint, st, keep_psi);
+  else launch_diag_run_kind<CVQ_BKC>(S, a, src, dst, lam, partial, adjoint, st, keep_psi);
   return cudaGetLastError();
 }
 
