@@ -89,8 +89,11 @@ struct cvq_batch {
   double* partial_d = nullptr;
   std::vector<int> layer_off, layer_n;
   std::vector<char> layer_adj;
+  std::vector<char> layer_tile;  // every item is a tile range (k_batch_tile_layer)
   int n_red = 0, n_gates = 0, n_items = 0, n_theta = 0;
-  size_t smem = 0;
+  size_t smem = 0;       // dynamic shared memory of the generic layer kernel
+  size_t tile_smem = 0;  // of the tile-only layer kernel (0: no pool has one-slot tile tables)
+  size_t gen_smem = 0;   // gate tables without tile items (the small-instance kernel's table region)
   int maxblk = 0;  // most blocks of any block-gate type of the batch's pools
   // every sector fits one CTA's shared memory: one CTA per instance runs the
   // whole evaluation (k_batch_small) instead of one launch per layer
@@ -307,10 +310,14 @@ int build_plan(cvq_batch* b) {
   b->layer_off.clear();
   b->layer_n.clear();
   b->layer_adj.clear();
+  b->layer_tile.clear();
   for (size_t l = 0; l < layers.size(); ++l) {
     b->layer_off.push_back((int)items.size());
     b->layer_n.push_back((int)layers[l].size());
     b->layer_adj.push_back(adj[l]);
+    bool tile_only = !layers[l].empty();
+    for (const BItem& it : layers[l]) tile_only = tile_only && it.kind == BI_TILE;
+    b->layer_tile.push_back(tile_only ? 1 : 0);
     items.insert(items.end(), layers[l].begin(), layers[l].end());
   }
   b->n_items = (int)items.size();
@@ -382,7 +389,7 @@ int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
   if (b->small) {
     e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
     if (e == cudaSuccess)
-      e = launch_batch_small(b->kind, 0, b->n, b->smem, std::max(b->n_max, 1), b->small_smem, b->inst_d, b->segs_d,
+      e = launch_batch_small(b->kind, 0, b->n, b->gen_smem, std::max(b->n_max, 1), b->small_smem, b->inst_d, b->segs_d,
                              b->ids_d, theta, b->active_d, E, grad, st);
     return finish_capture(b, st, e, theta, E, grad);
   }
@@ -390,10 +397,16 @@ int capture(cvq_batch* b, const double* theta, double* E, double* grad) {
   if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
   // a layer needs no more CTAs than it has items (small instances leave most of the grid idle)
   const int grid_max = b->sms * b->ctas_per_sm;
-  for (size_t l = 0; l < b->layer_n.size() && e == cudaSuccess; ++l)
-    e = launch_batch_layer(b->kind, b->layer_adj[l] != 0, std::min(grid_max, b->layer_n[l]), b->smem, b->inst_d, b->segs_d,
-                           b->items_d + b->layer_off[l], b->layer_n[l], b->counters_d + l, b->ids_d, theta,
-                           b->active_d, b->partial_d, st);
+  for (size_t l = 0; l < b->layer_n.size() && e == cudaSuccess; ++l) {
+    if (b->layer_tile[l])
+      e = launch_batch_tile_layer(b->layer_adj[l] != 0, std::min(b->sms * 5, b->layer_n[l]), b->tile_smem, b->inst_d,
+                                  b->segs_d, b->items_d + b->layer_off[l], b->layer_n[l], b->counters_d + l, b->ids_d,
+                                  b->active_d, b->partial_d, st);
+    else
+      e = launch_batch_layer(b->kind, b->layer_adj[l] != 0, std::min(grid_max, b->layer_n[l]), b->smem, b->inst_d,
+                             b->segs_d, b->items_d + b->layer_off[l], b->layer_n[l], b->counters_d + l, b->ids_d,
+                             theta, b->active_d, b->partial_d, st);
+  }
   if (e == cudaSuccess) e = launch_batch_reduce(b->red_d, b->n_red, b->partial_d, b->active_d, E, grad, st);
   return finish_capture(b, st, e, theta, E, grad);
 }
@@ -508,12 +521,18 @@ int capture_screen(cvq_batch* b, const double* theta, double* grad) {
   if (e == cudaSuccess) e = launch_batch_build(b->inst_d, b->gates_d, b->n_gates, b->maxblk, b->ids_d, theta, b->active_d, st);
   const int grid = b->sms * b->ctas_per_sm;
   if (b->small && e == cudaSuccess)  // forward sweep and H psi of every instance, one CTA each
-    e = launch_batch_small(b->kind, 1, b->n, b->smem, std::max(b->n_max, 1), b->small_smem, b->inst_d, b->segs_d,
+    e = launch_batch_small(b->kind, 1, b->n, b->gen_smem, std::max(b->n_max, 1), b->small_smem, b->inst_d, b->segs_d,
                            b->ids_d, theta, b->active_d, nullptr, nullptr, st);
-  for (int l = 0; l < nfwd && e == cudaSuccess && !b->small; ++l)
-    e = launch_batch_layer(b->kind, false, std::min(grid, b->layer_n[l]), b->smem, b->inst_d, b->segs_d,
-                           b->items_d + b->layer_off[l], b->layer_n[l], b->s_counters + l, b->ids_d, theta,
-                           b->active_d, b->partial_d, st);
+  for (int l = 0; l < nfwd && e == cudaSuccess && !b->small; ++l) {
+    if (b->layer_tile[l])
+      e = launch_batch_tile_layer(false, std::min(b->sms * 5, b->layer_n[l]), b->tile_smem, b->inst_d, b->segs_d,
+                                  b->items_d + b->layer_off[l], b->layer_n[l], b->s_counters + l, b->ids_d,
+                                  b->active_d, b->partial_d, st);
+    else
+      e = launch_batch_layer(b->kind, false, std::min(grid, b->layer_n[l]), b->smem, b->inst_d, b->segs_d,
+                             b->items_d + b->layer_off[l], b->layer_n[l], b->s_counters + l, b->ids_d, theta,
+                             b->active_d, b->partial_d, st);
+  }
   if (e == cudaSuccess)
     e = launch_batch_screen(b->kind, std::min(grid, b->s_nitems), b->inst_d, b->s_items, b->s_nitems,
                             b->s_counters + nl, b->active_d,
@@ -585,6 +604,7 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
   size_t total = 0;
   std::vector<size_t> offs(n_inst);
   size_t smem = std::max(sizeof(HSmem), (size_t)(LMAX * DMAX + MAX_RUN_PAIRS * DMAX * DMAX) * sizeof(cdf));
+  size_t tsmem = 0;  // tile items (generic layer kernel, and the tile-only one)
   for (int i = 0; i < n_inst; ++i) {
     PoolView& p = b->pv[i];
     int rc = internal_pool_host(pools[i], &p.sec, &p.types, &p.ntypes, &p.op_type, &p.op_i, &p.op_j, &p.K, &p.P,
@@ -613,22 +633,24 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
       }
     for (int k = 0; p.op_tiles && k < p.K; ++k) {
       const TileMap& tm = p.op_tiles[k];
-      if (tm.idx && tm.slots == 1) smem = std::max(smem, tile_smem_bytes(p.types[p.op_type[k]], tm.nreg, tm.nsub, true, 1));
+      if (tm.idx && tm.slots == 1)
+        tsmem = std::max(tsmem, tile_smem_bytes(p.types[p.op_type[k]], tm.nreg, tm.nsub, true, 1));
     }
     offs[i] = total;
     total += 2 * a256(sizeof(cdf) * (size_t)S->dim) + a256(sizeof(cdf) * (size_t)std::max(n_max, 1) * p.ustride);
   }
-  if (smem > 200 * 1024) {
+  if (std::max(smem, tsmem) > 200 * 1024) {
     delete b;
-    return errf(CVQ_EINVAL, "gate tables need %zu bytes of shared memory", smem);
+    return errf(CVQ_EINVAL, "gate tables need %zu bytes of shared memory", std::max(smem, tsmem));
   }
-  b->smem = smem;
   {
     int64_t dmax = 0;
     for (int i = 0; i < n_inst; ++i) dmax = std::max<int64_t>(dmax, b->S[i].dim);
-    b->smem = a256(smem);
-    // every instance has at most n_max segments
-    const size_t need = batch_small_smem(b->smem, std::max(n_max, 1), dmax);
+    b->smem = a256(std::max(smem, tsmem));
+    b->tile_smem = tsmem ? a256(tsmem) : 0;
+    b->gen_smem = a256(smem);
+    // every instance has at most n_max segments (the small-instance kernel runs no tile items)
+    const size_t need = batch_small_smem(b->gen_smem, std::max(n_max, 1), dmax);
     b->small = need <= (size_t)kSmallSmem;
     b->small_smem = need;
   }
@@ -638,6 +660,7 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
   if (e == cudaSuccess) e = cudaMalloc(&b->state, total);
   if (e == cudaSuccess) e = cudaMalloc(&b->inst_d, sizeof(BInst) * n_inst);
   if (e == cudaSuccess) e = set_batch_smem_limit((int)b->smem);
+  if (e == cudaSuccess && b->tile_smem) e = set_batch_tile_smem_limit((int)b->tile_smem);
   if (e == cudaSuccess && b->small) e = set_batch_small_smem_limit(kSmallSmem);
   if (e != cudaSuccess) {
     cvq_batch_destroy(b);

@@ -466,6 +466,11 @@ cudaError_t launch_batch_layer(int kind, bool adj, int grid, size_t smem, const 
                                const BItem* items, int nitems, int* counter, const int* ids, const double* theta,
                                const int* active, double* partial, cudaStream_t st);
 cudaError_t set_batch_smem_limit(int bytes);
+// A layer of block-gate tile ranges only (BI_TILE items), 5 CTAs per SM.
+cudaError_t launch_batch_tile_layer(bool adj, int grid, size_t smem, const BInst* insts, const BSeg* segs,
+                                    const BItem* items, int nitems, int* counter, const int* ids, const int* active,
+                                    double* partial, cudaStream_t st);
+cudaError_t set_batch_tile_smem_limit(int bytes);
 cudaError_t launch_batch_reduce(const BRed* red, int n, const double* partial, const int* active, double* E,
                                 double* grad, cudaStream_t st);
 // Batches whose sectors all fit in shared memory: one CTA per instance runs

@@ -204,6 +204,63 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   }
 }
 
+// A layer whose items are all tile ranges of block gates: the same loop as
+// k_batch_layer's BI_TILE items, with only the tile code's registers, so five
+// CTAs fit on an SM (the generic layer kernel, which also holds the orbit and
+// diagonal-run code, fits two).
+template <bool ADJ>
+__global__ void __launch_bounds__(NTHREADS, 5)
+    k_batch_tile_layer(const BInst* __restrict__ insts, const BSeg* __restrict__ segs, const BItem* __restrict__ items,
+                       int nitems, int* counter, const int* __restrict__ ids, const int* __restrict__ active,
+                       double* __restrict__ partial) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ TypeDesc t;
+  __shared__ TileMap tm;
+  __shared__ int item;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int k = item;
+    if (k >= nitems) break;
+    const BItem it = items[k];
+    if (!active[it.inst]) {  // instance paused for this evaluation: skip the item
+      __syncthreads();
+      continue;
+    }
+    const BInst& I = insts[it.inst];
+    const int k0 = segs[it.seg].k0;
+    const GateArg& ga = I.ops[ids[I.ids_off + k0]];
+    copy_words(&t, &ga.t, sizeof(TypeDesc));
+    copy_words(&tm, &ga.tm, sizeof(TileMap));
+    __syncthreads();
+    const cdf* U = I.U + (size_t)k0 * I.ustride;
+    dfacc gacc;
+    acc_zero(gacc);
+    if (t.realu) tile_gate_range<ADJ, true, 1>(t, tm, U, I.P, it.a, it.b, 1, I.psi, I.lam, nullptr, smem, gacc);
+    else tile_gate_range<ADJ, false, 1>(t, tm, U, I.P, it.a, it.b, 1, I.psi, I.lam, nullptr, smem, gacc);
+    if (ADJ) {
+      const double s = block_sum(acc_to_double(gacc));
+      if (threadIdx.x == 0) partial[it.slot] = s;
+    }
+    __syncthreads();  // the shared tables and item number are reused by the next item
+  }
+}
+
+cudaError_t launch_batch_tile_layer(bool adj, int grid, size_t smem, const BInst* insts, const BSeg* segs,
+                                    const BItem* items, int nitems, int* counter, const int* ids, const int* active,
+                                    double* partial, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  if (adj) k_batch_tile_layer<true><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, active, partial);
+  else k_batch_tile_layer<false><<<grid, NTHREADS, smem, st>>>(insts, segs, items, nitems, counter, ids, active, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t set_batch_tile_smem_limit(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_tile_layer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_tile_layer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
 // out = scale * sum of `count` partials from slot0 with `stride`, in order.
 __global__ void k_batch_reduce(const BRed* __restrict__ red, int n, const double* __restrict__ partial,
                                const int* __restrict__ active, double* __restrict__ E, double* __restrict__ grad) {
