@@ -1394,12 +1394,8 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
   if (int rc = prepare_gates(s, p, op_ids, theta, n, U, st)) return rc;
   if (int rc = to_df(s, psi0, psi, st)) return rc;
   if (int rc = forward_sweep(s, p, op_ids, theta, n, U, psi, st, ck, sv)) return rc;
-  double* pE = partial + (size_t)n * NBLK;
+  double* pE = partial + (size_t)n * NBLK;  // reduced with the gradient rows at the end
   if (int rc = run_apply_H(s, psi, lam, pE, st)) return rc;
-  {
-    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK, NBLK);
-    CVQ_CUDA(launch_reduce(pE, 1, NBLK, 1.0, E_dev, st), "reduce E");
-  }
   const std::vector<Seg> segs = segments(p, op_ids, n);
   const double dim = (double)s->S.dim;
   int slot = ck ? (int)ck->seg_of.size() - 1 : -1;
@@ -1449,8 +1445,8 @@ static int energy_and_grad(const cvq_sector* s, const cvq_pool* p, const int* op
     }
   }
   {
-    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * n, (double)NBLK * n);
-    CVQ_CUDA(launch_reduce(partial, n, NBLK, 2.0, grad_dev, st), "reduce grad");
+    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * (n + 1), (double)NBLK * (n + 1));
+    CVQ_CUDA(launch_reduce_eg(partial, n, NBLK, E_dev, grad_dev, st), "reduce E and grad");
   }
   return CVQ_OK;
 }

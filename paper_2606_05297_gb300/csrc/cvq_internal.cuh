@@ -520,6 +520,8 @@ cudaError_t launch_to_df(int64_t dim, const double2* src, cdf* dst, cudaStream_t
 cudaError_t launch_from_df(int64_t dim, const cdf* src, double2* dst, cudaStream_t st);
 cudaError_t launch_apply_H(const SectorDev& S, const cdf* psi, cdf* sigma, double* partial, cudaStream_t st);
 cudaError_t launch_reduce(const double* partial, int nred, int nblk, double scale, double* out, cudaStream_t st);
+// Gradient rows 0..n-1 of partial (x 2) into grad and energy row n into E.
+cudaError_t launch_reduce_eg(const double* partial, int n, int nblk, double* E, double* grad, cudaStream_t st);
 cudaError_t launch_build_gates(const BuildArgs& a, const TypeDesc* types_dev, PoolDev P, cdf* U, cudaStream_t st);
 cudaError_t launch_gate(const SectorDev& S, const GateArg& g, PoolDev P, const cdf* src, cdf* dst, cudaStream_t st);
 // Tiled gates: the table of one gate structure, and the in-place forward gate

@@ -139,6 +139,25 @@ cudaError_t launch_reduce(const double* partial, int nred, int nblk, double scal
   return cudaGetLastError();
 }
 
+// The n gradient rows (scale 2) and the energy row after them (scale 1) in one
+// launch, each row summed as k_reduce sums it.
+__global__ void k_reduce_eg(const double* __restrict__ partial, int n, int nblk, double* __restrict__ E,
+                            double* __restrict__ grad) {
+  const int r = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += partial[(size_t)r * nblk + b];
+  v = block_sum(v);
+  if (threadIdx.x == 0) {
+    if (r < n) grad[r] = 2.0 * v;
+    else E[0] = 1.0 * v;
+  }
+}
+
+cudaError_t launch_reduce_eg(const double* partial, int n, int nblk, double* E, double* grad, cudaStream_t st) {
+  k_reduce_eg<<<n + 1, NTHREADS, 0, st>>>(partial, n, nblk, E, grad);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ Lanczos
 
 __global__ void __launch_bounds__(NTHREADS) k_lanczos_update(int64_t dim, const double2* __restrict__ vp,
