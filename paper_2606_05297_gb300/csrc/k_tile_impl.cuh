@@ -32,12 +32,14 @@ __host__ __device__ __forceinline__ size_t tile_head_bytes(const TypeDesc& t, in
   return (b + 15) & ~(size_t)15;
 }
 
-// Stages of the tile pipeline: the amplitudes of the next tile are copied
-// into one stage while the current tile is multiplied out of the other.
-constexpr int TILE_STAGES = 2;
+// Stages of the tile pipeline: while a tile is multiplied out of one stage,
+// the copies of the next tiles into the others are in flight: three stages at
+// one slot per thread, two at four (whose stages are four times larger).
+__host__ __device__ constexpr int tile_stages(int slots) { return slots == 1 ? 3 : 2; }
 
 __host__ __device__ __forceinline__ size_t tile_smem_bytes(const TypeDesc& t, int nreg, int nsub, bool adj, int slots) {
-  return tile_head_bytes(t, nreg, nsub, adj) + (size_t)TILE_STAGES * TILE_T * slots * sizeof(cdf) * (adj ? 2 : 1);
+  return tile_head_bytes(t, nreg, nsub, adj) +
+         (size_t)tile_stages(slots) * TILE_T * slots * sizeof(cdf) * (adj ? 2 : 1);
 }
 
 // 16-byte copy from global to shared memory that completes asynchronously
@@ -111,15 +113,18 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   cdf* Sbase = reinterpret_cast<cdf*>(smem + tile_head_bytes(t, tm.nreg, tm.nsub, ADJ));
   constexpr int kStage = TILE_T * S * (ADJ ? 2 : 1);  // cdf entries of one stage: psi, then lambda
   const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
-  // The pipeline: while the tile in stage stg is multiplied, the copies of the
-  // next tile into stage stg ^ 1 are in flight, and the table entries of the
-  // one after are being loaded into registers.
+  // The pipeline: tile i is multiplied out of stage i mod NST while the copies
+  // of tiles i + 1 .. i + NST - 1 are in flight.  One barrier per tile: after
+  // it every thread is done with tile i - 1, whose stage then takes the
+  // copies of tile i + NST - 1.
+  constexpr int NST = tile_stages(S);
   int64_t tile = t_begin;
-  int xa[S], xb[S];  // sector indices of the slots of the current and the next tile
+  int x0[S], x1[S], x2[S];  // sector indices of the slots of tiles i, i + 1, i + 2
 #pragma unroll
-  for (int q = 0; q < S; ++q) xa[q] = xb[q] = -1;
-  if (tile < t_end) tile_idx<S>(xa, tm, tile);
-  if (tile + t_step < t_end) tile_idx<S>(xb, tm, tile + t_step);
+  for (int q = 0; q < S; ++q) x0[q] = x1[q] = x2[q] = -1;
+  if (tile < t_end) tile_idx<S>(x0, tm, tile);
+  if (tile + t_step < t_end) tile_idx<S>(x1, tm, tile + t_step);
+  if (NST == 3 && tile + 2 * t_step < t_end) tile_idx<S>(x2, tm, tile + 2 * t_step);
   // The gate's tables, while those table entries are in flight: the block
   // unitaries by asynchronous copy (in the first tile's group), the rest
   // directly; the barrier of the first tile orders them before any use.
@@ -128,8 +133,14 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
     for (int e = threadIdx.x; e < t.nf; e += blockDim.x) Fs[e] = P.F[t.f_base + e];
   for (int e = threadIdx.x; e < tm.nreg; e += blockDim.x) Rs[e] = tm.reg[e];
   for (int e = threadIdx.x; e < tm.nsub; e += blockDim.x) Ss[e] = tm.sub[e];
-  if (tile < t_end) tile_fetch<ADJ, STORED, S>(xa, tile, psi, lam, store, Sbase, Sbase + TILE_T * S);
+  if (tile < t_end) tile_fetch<ADJ, STORED, S>(x0, tile, psi, lam, store, Sbase, Sbase + TILE_T * S);
   else cp_async_commit();
+  if (NST == 3) {  // the second tile's copies start before the loop as well
+    if (tile + t_step < t_end)
+      tile_fetch<ADJ, STORED, S>(x1, tile + t_step, psi, lam, store, Sbase + kStage, Sbase + kStage + TILE_T * S);
+    else
+      cp_async_commit();
+  }
   int stg = 0;
   // Where each of this thread's slots sits in its tile depends only on the
   // region (the tiles of a CTA climb through the regions in order), so it is
@@ -139,24 +150,23 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   int64_t reg_end = -1;
   int dec[S];
   while (tile < t_end) {
-    const int64_t next = tile + t_step, next2 = next + t_step;
+    const int64_t ahead = tile + (NST - 1) * t_step, after = ahead + t_step;
     cdf* const Sp = Sbase + stg * kStage;
     cdf* const Sl = Sp + TILE_T * S;
-    if (next < t_end) {  // stage stg ^ 1 was last read before the barrier that ended the previous tile
-      cdf* const np = Sbase + (stg ^ 1) * kStage;
-      tile_fetch<ADJ, STORED, S>(xb, next, psi, lam, store, np, np + TILE_T * S);
-    } else {
-      cp_async_commit();  // an empty group keeps one group per tile for the wait below
+    cp_async_wait<NST - 2>();  // this thread's copies of tile i have landed,
+    __syncthreads();           // and every other thread's; tile i - 1 is done
+    {
+      cdf* const np = Sbase + ((stg + NST - 1) % NST) * kStage;  // tile i - 1's stage
+      if (ahead < t_end) tile_fetch<ADJ, STORED, S>(NST == 3 ? x2 : x1, ahead, psi, lam, store, np, np + TILE_T * S);
+      else cp_async_commit();  // an empty group keeps one group per tile for the wait above
     }
-    int xc[S];
+    int xn[S];
 #pragma unroll
-    for (int q = 0; q < S; ++q) xc[q] = -1;
-    if (next2 < t_end) tile_idx<S>(xc, tm, next2);
-    cp_async_wait<1>();  // this thread's copies of the current tile have landed,
-    __syncthreads();     // and every other thread's
+    for (int q = 0; q < S; ++q) xn[q] = -1;
+    if (after < t_end) tile_idx<S>(xn, tm, after);
     int xs[S];
 #pragma unroll
-    for (int q = 0; q < S; ++q) xs[q] = xa[q];
+    for (int q = 0; q < S; ++q) xs[q] = x0[q];
     if (tile >= reg_end) {
       reg = tile_region(Rs, tm.nreg, tile);
       const TileRegion R = Rs[reg];
@@ -239,14 +249,18 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
       psi[x] = make_cdf(acc_get(ar), acc_get(ai));
       lam[x] = make_cdf(acc_get(br), acc_get(bi));
     }
-    __syncthreads();  // every thread has finished reading stage stg before it is refilled
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-      xa[q] = xb[q];
-      xb[q] = xc[q];
+      x0[q] = x1[q];
+      if (NST == 3) {
+        x1[q] = x2[q];
+        x2[q] = xn[q];
+      } else {
+        x1[q] = xn[q];
+      }
     }
-    stg ^= 1;
-    tile = next;
+    stg = (stg + 1) % NST;
+    tile += t_step;
   }
   cp_async_wait<0>();  // nothing stays in flight into shared memory past the call
 }
