@@ -192,15 +192,13 @@ __device__ __forceinline__ void screen_chunk(const SectorDev& S, const int64_t (
       df F = df_make(sq[ni][h.y + 2].x, sq[ni][h.y + 2].y);
       if (h.z >= 0) F = df_mul(F, df_make(sq[nj][h.w + 2].x, sq[nj][h.w + 2].y));
       const cdf q = psi[moved_index<KIND>(x, w, wR, fx, h.x, h.y, h.z, h.w, S, Gs)];
-      dfacc tr, ti;  // conj(s) q
-      acc_zero(tr);
-      acc_zero(ti);
-      acc_mac(tr, re_of(s), re_of(q));
-      acc_mac(tr, im_of(s), im_of(q));
-      acc_mac(ti, re_of(s), im_of(q));
-      acc_mac(ti, df_neg(im_of(s)), re_of(q));
-      acc_mac(zr[k], F, acc_get(tr));
-      acc_mac(zi[k], F, acc_get(ti));
+      // Z += conj(s) (F q): the ladder factor scales the neighbour first (two
+      // df products), then four multiply-accumulates into Z
+      const df fr = df_mul(F, re_of(q)), fi = df_mul(F, im_of(q));
+      acc_mac(zr[k], re_of(s), fr);
+      acc_mac(zr[k], im_of(s), fi);
+      acc_mac(zi[k], re_of(s), fi);
+      acc_mac(zi[k], df_neg(im_of(s)), fr);
     }
   }
 }
