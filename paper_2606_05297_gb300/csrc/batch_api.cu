@@ -646,7 +646,9 @@ extern "C" int cvq_batch_create(const cvq_sector* const* sectors, const cvq_pool
   {
     int64_t dmax = 0;
     for (int i = 0; i < n_inst; ++i) dmax = std::max<int64_t>(dmax, b->S[i].dim);
-    b->smem = a256(std::max(smem, tsmem));
+    // the generic layer kernel also holds the Bose-Hubbard items' walk buffer
+    const size_t walk = (b->kind == CVQ_BH) ? batch_walk_offset() + BATCH_WALK_BYTES : 0;
+    b->smem = a256(std::max(std::max(smem, tsmem), walk));
     b->tile_smem = tsmem ? a256(tsmem) : 0;
     b->gen_smem = a256(smem);
     // every instance has at most n_max segments (the small-instance kernel runs no tile items)

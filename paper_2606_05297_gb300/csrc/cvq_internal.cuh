@@ -173,12 +173,12 @@ __host__ __device__ __forceinline__ int walk_r(int64_t n, int64_t nwarps) {
   return (r & 1) ? r : r + 1;  // odd: the lanes' buffer writes fall on distinct bank pairs
 }
 
+// The warps taking part are warp = 0 .. nw - 1 (bh_walk: every warp of the
+// grid; bh_walk_cta: the warps of one CTA, for a range of its own).
 template <class T, class F>
-__device__ __forceinline__ void bh_walk(const SectorDev& S, const T (*G)[DMAX + 1], uint64_t* wbuf, int64_t x0,
-                                        int64_t x1, F&& f) {
+__device__ __forceinline__ void bh_walk_warps(const SectorDev& S, const T (*G)[DMAX + 1], uint64_t* wbuf, int64_t x0,
+                                              int64_t x1, int64_t warp, int64_t nw, F&& f) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int R = walk_r(x1 - x0, nw);
   const int64_t ch = 32 * (int64_t)R;
   uint64_t* buf = wbuf + (threadIdx.x >> 5) * (32 * WALK_RMAX);
@@ -200,6 +200,19 @@ __device__ __forceinline__ void bh_walk(const SectorDev& S, const T (*G)[DMAX + 
     }
     __syncwarp();
   }
+}
+
+template <class T, class F>
+__device__ __forceinline__ void bh_walk(const SectorDev& S, const T (*G)[DMAX + 1], uint64_t* wbuf, int64_t x0,
+                                        int64_t x1, F&& f) {
+  bh_walk_warps(S, G, wbuf, x0, x1, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                ((int64_t)gridDim.x * blockDim.x) >> 5, f);
+}
+
+template <class T, class F>
+__device__ __forceinline__ void bh_walk_cta(const SectorDev& S, const T (*G)[DMAX + 1], uint64_t* wbuf, int64_t x0,
+                                            int64_t x1, F&& f) {
+  bh_walk_warps(S, G, wbuf, x0, x1, threadIdx.x >> 5, blockDim.x >> 5, f);
 }
 
 // Insert two empty nibbles at modes lo < hi: the packed tuple of the other
@@ -411,6 +424,7 @@ struct DiagRunArg {
 // ------------------------------------------------------------- batched engine
 
 constexpr int BATCH_RUN = 8;  // diagonal gates per run in the batched engine
+
 enum BItemKind { BI_TODF = 0, BI_GATE = 1, BI_DIAG = 2, BI_APPLYH = 3, BI_TILE = 4 };  // BI_TILE: a range of gate tiles
 
 // One instance of a batch: its sector, pool tables and device buffers.

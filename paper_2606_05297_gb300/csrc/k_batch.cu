@@ -98,6 +98,12 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   __shared__ BShared sh;
   __shared__ int64_t G64[LMAX][DMAX + 1];
   __shared__ int32_t G32[LMAX][DMAX + 1];
+  // Bose-Hubbard matvec and diagonal-run items: the CTA's warps walk the
+  // item's range (bh_walk_cta) with their tuple buffer in dynamic shared
+  // memory after the item's tables (batch_walk_offset), and bond hops take
+  // their rank changes from Dp
+  __shared__ int32_t Dp[(KIND == CVQ_BH) ? LMAX : 1][DMAX + 1];
+  uint64_t* wbuf = reinterpret_cast<uint64_t*>(smem + batch_walk_offset());
   for (;;) {
     if (threadIdx.x == 0) sh.item = atomicAdd(counter, 1);
     __syncthreads();
@@ -129,7 +135,14 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       __syncthreads();
       dfacc eacc;
       acc_zero(eacc);
-      apply_H_range<KIND>(S, G64, H, I.psi, I.lam, it.a + threadIdx.x, it.b, NTHREADS, eacc);
+      if (KIND == CVQ_BH) {
+        load_dhop(Dp, G64, S);
+        __syncthreads();
+        bh_walk_cta(S, G64, wbuf, it.a, it.b,
+                    [&](int64_t x, uint64_t w) { apply_H_one<KIND>(S, G64, Dp, H, I.psi, I.lam, x, w, eacc); });
+      } else {
+        apply_H_range<KIND>(S, G64, H, I.psi, I.lam, it.a + threadIdx.x, it.b, NTHREADS, eacc);
+      }
       const double s = block_sum(acc_to_double(eacc));
       if (threadIdx.x == 0) partial[it.slot] = s;
     } else if (it.kind == BI_DIAG) {
@@ -141,8 +154,13 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       dfacc acc[BATCH_RUN];
 #pragma unroll
       for (int q = 0; q < BATCH_RUN; ++q) acc_zero(acc[q]);
-      diag_run_range<KIND, ADJ, BATCH_RUN>(S, G64, T, TP, sg, I.psi, I.psi, I.lam, it.a + threadIdx.x, it.b, NTHREADS,
-                                           acc);
+      if (KIND == CVQ_BH)
+        bh_walk_cta(S, G64, wbuf, it.a, it.b, [&](int64_t x, uint64_t w) {
+          diag_run_one<ADJ, BATCH_RUN>(S, T, TP, sg, I.psi, I.psi, I.lam, x, w, acc);
+        });
+      else
+        diag_run_range<KIND, ADJ, BATCH_RUN>(S, G64, T, TP, sg, I.psi, I.psi, I.lam, it.a + threadIdx.x, it.b,
+                                             NTHREADS, acc);
       if (ADJ) {
 #pragma unroll
         for (int q = 0; q < BATCH_RUN; ++q) {

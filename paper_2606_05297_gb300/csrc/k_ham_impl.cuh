@@ -34,6 +34,16 @@ struct HSmem {
   float2 hop[LMAX], pair[LMAX];
 };
 
+// Batched layer kernel, Bose-Hubbard matvec and diagonal-run items: the warp
+// walk's tuple buffer follows the item's tables (the Hamiltonian tables, or a
+// diagonal run's phase tables) in dynamic shared memory.
+__host__ __device__ constexpr size_t batch_walk_offset() {
+  return ((sizeof(HSmem) > sizeof(cdf) * (LMAX * DMAX + MAX_RUN_PAIRS * DMAX * DMAX)
+               ? sizeof(HSmem)
+               : sizeof(cdf) * (LMAX * DMAX + MAX_RUN_PAIRS * DMAX * DMAX)) + 255) & ~(size_t)255;
+}
+constexpr size_t BATCH_WALK_BYTES = (size_t)NTHREADS / 32 * 32 * WALK_RMAX * sizeof(uint64_t);
+
 __device__ __forceinline__ void load_htabs(HSmem& h, const SectorDev& S) {
   const float2* a = &S.tab->diagE[0][0];
   for (int e = threadIdx.x; e < LMAX * DMAX; e += blockDim.x) (&h.dE[0][0])[e] = a[e];
