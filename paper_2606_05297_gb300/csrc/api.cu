@@ -659,6 +659,8 @@ static int build_tiles(cvq_pool* p, const PoolBuild& pb) {
       pl.reg.push_back(R);
     }
     if (pl.sub.size() > 64) return fail(CVQ_EINVAL, "%zu block classes exceed the tiled gates' 64", pl.sub.size());
+    if (pl.ntiles * T > (int64_t)INT32_MAX)  // the gate kernels address tables and stored slots with 32-bit offsets
+      return fail(CVQ_EINVAL, "a gate table of %lld slots exceeds 2^31 - 1", (long long)(pl.ntiles * T));
     where[key] = (int)plans.size();
     plan_of[k] = (int)plans.size();
     plans.push_back(std::move(pl));

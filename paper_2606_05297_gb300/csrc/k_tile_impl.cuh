@@ -42,15 +42,15 @@ __host__ __device__ __forceinline__ size_t tile_smem_bytes(const TypeDesc& t, in
          (size_t)tile_stages(slots) * TILE_T * slots * sizeof(cdf) * (adj ? 2 : 1);
 }
 
-// 16-byte copy from global to shared memory that completes asynchronously
-// (cp.async); copies are grouped per tile and waited for with
-// cp_async_wait<N> (all but the N most recent groups complete).  L1: through
-// L1 (the forward gate: the two halves of a 32-byte sector read by different
-// warps of a tile come from L2 once), else L2 only (the reverse step, whose
-// two gathered states would only evict each other from L1; measured faster).
+// 16-byte copy from global to shared memory (address d in the shared state
+// space) that completes asynchronously (cp.async); copies are grouped per tile
+// and waited for with cp_async_wait<N> (all but the N most recent groups
+// complete).  L1: through L1 (the forward gate: the two halves of a 32-byte
+// sector read by different warps of a tile come from L2 once), else L2 only
+// (the reverse step, whose two gathered states would only evict each other
+// from L1; measured faster).
 template <bool L1>
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+__device__ __forceinline__ void cp_async16(unsigned d, const void* gmem_src) {
   if (L1) asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
   else asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
@@ -59,38 +59,71 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // The sector indices of this thread's S slots of one tile (streamed: each
-// table entry is read once per gate).
+// table entry is read once per gate).  Tile and slot offsets are 32-bit: the
+// pool build rejects tables of 2^31 or more slots.
 template <int S>
-__device__ __forceinline__ void tile_idx(int (&x)[S], const TileMap& tm, int64_t tile) {
-  const int* ti = tm.idx + tile * (TILE_T * S);
+__device__ __forceinline__ void tile_idx(int (&x)[S], const int* idx, int tile) {
+  const int* ti = idx + (tile * (TILE_T * S) + (int)threadIdx.x);
 #pragma unroll
-  for (int q = 0; q < S; ++q) x[q] = __ldcs(ti + threadIdx.x + q * TILE_T);
+  for (int q = 0; q < S; ++q) x[q] = __ldcs(ti + q * TILE_T);
 }
 
-// Starts the copies of this thread's slots of one tile into a stage: psi (or,
-// STORED, the gate's stored output values, in slot order) and lambda (ADJ).
+// Starts the copies of this thread's slots of one tile into the stage whose
+// slot threadIdx.x is at shared address d: psi (or, STORED, the gate's stored
+// output values, in slot order) and lambda (ADJ, TILE_T x S slots further).
 template <bool ADJ, bool STORED, int S>
-__device__ __forceinline__ void tile_fetch(const int (&x)[S], int64_t tile, const cdf* psi, const cdf* lam,
-                                           const cdf* store, cdf* sp, cdf* sl) {
+__device__ __forceinline__ void tile_fetch(const int (&x)[S], int tile, const cdf* psi, const cdf* lam,
+                                           const cdf* store, unsigned d) {
 #pragma unroll
   for (int q = 0; q < S; ++q) {
-    const int slot = threadIdx.x + q * TILE_T;
     if (x[q] < 0) continue;  // unused slot: no block reads it
-    cp_async16<!ADJ>(sp + slot, STORED ? store + tile * (TILE_T * S) + slot : psi + x[q]);
-    if (ADJ) cp_async16<false>(sl + slot, lam + x[q]);
+    const unsigned dq = d + (unsigned)(q * TILE_T * sizeof(cdf));
+    cp_async16<!ADJ>(dq, STORED ? store + (tile * (TILE_T * S) + (int)threadIdx.x + q * TILE_T) : psi + x[q]);
+    if (ADJ) cp_async16<false>(dq + (unsigned)(TILE_T * S * sizeof(cdf)), lam + x[q]);
   }
   cp_async_commit();
 }
 
 // Region of a tile: the last one whose first tile is <= tile.
-__device__ __forceinline__ int tile_region(const TileRegion* Rs, int nreg, int64_t tile) {
+__device__ __forceinline__ int tile_region(const TileRegion* Rs, int nreg, int tile) {
   int lo = 0, hi = nreg - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (Rs[mid].tile0 <= tile) lo = mid;
+    if ((int)Rs[mid].tile0 <= tile) lo = mid;
     else hi = mid - 1;
   }
   return lo;
+}
+
+// Where one of a thread's slots sits in the tiles of a region (the same in
+// every tile of it): block size b, member a, the staged offset pk of member 0
+// of its block (member l at pk + l G), the offset u of the unitary entries it
+// reads (forward: row a, entries u + l; reverse: column a, entries u + l b),
+// and, reverse, the generator factor F_a of the entries (a, a + 1).
+struct TileSlot {
+  int b, a, pk, u;
+  float fh, fl;
+};
+
+// acc += sum over l < b of u[l us] v[l vs] (CONJ: conj(u[l us]) v[l vs]) for a
+// row or column of a block unitary whose entry l is real when p + l is even
+// and imaginary when it is odd (REALU: every entry real).  The parity is taken
+// per entry: warps whose slots mix both parities then stay converged.
+template <bool REALU, bool CONJ>
+__device__ __forceinline__ void cb_dot(dfacc& ar, dfacc& ai, const cdf* u, int us, const cdf* v, int vs, int b, int p) {
+  for (int l = 0; l < b; ++l) cmac_cb<REALU, CONJ>(ar, ai, u[l * us], v[l * vs], (p ^ l) & 1);
+}
+
+// Two such sums over the same unitary entries: (ar, ai) over v, (br, bi) over w.
+template <bool REALU, bool CONJ>
+__device__ __forceinline__ void cb_dot2(dfacc& ar, dfacc& ai, dfacc& br, dfacc& bi, const cdf* u, int us, const cdf* v,
+                                        const cdf* w, int vs, int b, int p) {
+  for (int l = 0; l < b; ++l) {
+    const cdf uu = u[l * us];
+    const int odd = (p ^ l) & 1;
+    cmac_cb<REALU, CONJ>(ar, ai, uu, v[l * vs], odd);
+    cmac_cb<REALU, CONJ>(br, bi, uu, w[l * vs], odd);
+  }
 }
 
 // Tiles t_begin, t_begin + t_step, ... < t_end of one gate (block unitaries U,
@@ -110,102 +143,112 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
   char* after_f = reinterpret_cast<char*>(Fs) + ((((size_t)(ADJ ? t.nf : 0) * sizeof(float2)) + 15) & ~(size_t)15);
   TileRegion* Rs = reinterpret_cast<TileRegion*>(after_f);
   TileSub* Ss = reinterpret_cast<TileSub*>(Rs + tm.nreg);
-  cdf* Sbase = reinterpret_cast<cdf*>(smem + tile_head_bytes(t, tm.nreg, tm.nsub, ADJ));
-  constexpr int kStage = TILE_T * S * (ADJ ? 2 : 1);  // cdf entries of one stage: psi, then lambda
+  const char* Sbase = smem + tile_head_bytes(t, tm.nreg, tm.nsub, ADJ);
+  constexpr int TS = TILE_T * S;                                    // slots of a tile
+  constexpr unsigned kStageB = (unsigned)(TS * sizeof(cdf) * (ADJ ? 2 : 1));  // bytes of one stage: psi, then lambda
   const float cpr = (float)t.cp_re, cpi = (float)t.cp_im;
   // The pipeline: tile i is multiplied out of stage i mod NST while the copies
   // of tiles i + 1 .. i + NST - 1 are in flight.  One barrier per tile: after
   // it every thread is done with tile i - 1, whose stage then takes the
   // copies of tile i + NST - 1.
   constexpr int NST = tile_stages(S);
-  int64_t tile = t_begin;
+  const int tend = (int)t_end, tstep = (int)t_step;
+  int tile = (int)t_begin;
+  const unsigned sd = (unsigned)__cvta_generic_to_shared(Sbase) + threadIdx.x * (unsigned)sizeof(cdf);
   int x0[S], x1[S], x2[S];  // sector indices of the slots of tiles i, i + 1, i + 2
 #pragma unroll
   for (int q = 0; q < S; ++q) x0[q] = x1[q] = x2[q] = -1;
-  if (tile < t_end) tile_idx<S>(x0, tm, tile);
-  if (tile + t_step < t_end) tile_idx<S>(x1, tm, tile + t_step);
-  if (NST == 3 && tile + 2 * t_step < t_end) tile_idx<S>(x2, tm, tile + 2 * t_step);
+  if (tile < tend) tile_idx<S>(x0, tm.idx, tile);
+  if (tile + tstep < tend) tile_idx<S>(x1, tm.idx, tile + tstep);
+  if (NST == 3 && tile + 2 * tstep < tend) tile_idx<S>(x2, tm.idx, tile + 2 * tstep);
   // The gate's tables, while those table entries are in flight: the block
   // unitaries by asynchronous copy (in the first tile's group), the rest
   // directly; the barrier of the first tile orders them before any use.
-  for (int e = threadIdx.x; e < t.nu; e += blockDim.x) cp_async16<true>(Us + e, U + e);
+  {
+    const unsigned ud = (unsigned)__cvta_generic_to_shared(Us);
+    for (int e = threadIdx.x; e < t.nu; e += blockDim.x) cp_async16<true>(ud + (unsigned)e * sizeof(cdf), U + e);
+  }
   if (ADJ)
     for (int e = threadIdx.x; e < t.nf; e += blockDim.x) Fs[e] = P.F[t.f_base + e];
   for (int e = threadIdx.x; e < tm.nreg; e += blockDim.x) Rs[e] = tm.reg[e];
   for (int e = threadIdx.x; e < tm.nsub; e += blockDim.x) Ss[e] = tm.sub[e];
-  if (tile < t_end) tile_fetch<ADJ, STORED, S>(x0, tile, psi, lam, store, Sbase, Sbase + TILE_T * S);
+  if (tile < tend) tile_fetch<ADJ, STORED, S>(x0, tile, psi, lam, store, sd);
   else cp_async_commit();
   if (NST == 3) {  // the second tile's copies start before the loop as well
-    if (tile + t_step < t_end)
-      tile_fetch<ADJ, STORED, S>(x1, tile + t_step, psi, lam, store, Sbase + kStage, Sbase + kStage + TILE_T * S);
-    else
-      cp_async_commit();
+    if (tile + tstep < tend) tile_fetch<ADJ, STORED, S>(x1, tile + tstep, psi, lam, store, sd + kStageB);
+    else cp_async_commit();
   }
-  int stg = 0;
+  unsigned so = 0;  // byte offset of tile i's stage
   // Where each of this thread's slots sits in its tile depends only on the
   // region (the tiles of a CTA climb through the regions in order), so it is
-  // worked out once per region: the block class c, member a and block k of
-  // slot threadIdx.x + q TILE_T, packed as c | a << 6 | k << 10.
-  int reg = -1, G = 1;
-  int64_t reg_end = -1;
-  int dec[S];
-  while (tile < t_end) {
-    const int64_t ahead = tile + (NST - 1) * t_step, after = ahead + t_step;
-    cdf* const Sp = Sbase + stg * kStage;
-    cdf* const Sl = Sp + TILE_T * S;
+  // worked out once per region.
+  int G = 1, reg_end = -1;
+  TileSlot ts[S];
+  while (tile < tend) {
+    const int ahead = tile + (NST - 1) * tstep, after = ahead + tstep;
+    const cdf* const Sp = reinterpret_cast<const cdf*>(Sbase + so);
+    const cdf* const Sl = Sp + TS;
     cp_async_wait<NST - 2>();  // this thread's copies of tile i have landed,
     __syncthreads();           // and every other thread's; tile i - 1 is done
     {
-      cdf* const np = Sbase + ((stg + NST - 1) % NST) * kStage;  // tile i - 1's stage
-      if (ahead < t_end) tile_fetch<ADJ, STORED, S>(NST == 3 ? x2 : x1, ahead, psi, lam, store, np, np + TILE_T * S);
+      const unsigned prev = so == 0 ? (unsigned)(NST - 1) * kStageB : so - kStageB;  // tile i - 1's stage
+      if (ahead < tend) tile_fetch<ADJ, STORED, S>(NST == 3 ? x2 : x1, ahead, psi, lam, store, sd + prev);
       else cp_async_commit();  // an empty group keeps one group per tile for the wait above
     }
     int xn[S];
 #pragma unroll
     for (int q = 0; q < S; ++q) xn[q] = -1;
-    if (after < t_end) tile_idx<S>(xn, tm, after);
+    if (after < tend) tile_idx<S>(xn, tm.idx, after);
     int xs[S];
 #pragma unroll
     for (int q = 0; q < S; ++q) xs[q] = x0[q];
     if (tile >= reg_end) {
-      reg = tile_region(Rs, tm.nreg, tile);
+      const int reg = tile_region(Rs, tm.nreg, tile);
       const TileRegion R = Rs[reg];
       G = R.G;
-      reg_end = (reg + 1 < tm.nreg) ? Rs[reg + 1].tile0 : tm.ntiles;
+      reg_end = (reg + 1 < tm.nreg) ? (int)Rs[reg + 1].tile0 : (int)tm.ntiles;
 #pragma unroll
       for (int q = 0; q < S; ++q) {
         const int slot = threadIdx.x + q * TILE_T;
         int c = R.sub0 + R.nsub - 1;  // the block class whose slots hold this one
         while (c > R.sub0 && Ss[c].off > slot) --c;
-        const int rel = slot - Ss[c].off;
+        const TileSub u = Ss[c];
+        const int rel = slot - u.off;
         const int a = rel / G;
-        dec[q] = c | (a << 6) | ((rel - a * G) << 10);
+        ts[q].b = u.b;
+        ts[q].a = a;
+        ts[q].pk = u.off + (rel - a * G);
+        ts[q].u = ADJ ? u.u_off + a : u.u_off + a * u.b;
+        ts[q].fh = ts[q].fl = 0.f;
+        if (ADJ && a + 1 < u.b) {  // a slot past the region's blocks (a >= b) holds -1 in every tile
+          const float2 f = Fs[u.f_off + a];
+          ts[q].fh = f.x;
+          ts[q].fl = f.y;
+        }
       }
     }
 #pragma unroll
     for (int q = 0; q < S; ++q) {
       const int x = xs[q];
       if (x < 0) continue;
-      const int c = dec[q] & 63, a = (dec[q] >> 6) & 15, k = dec[q] >> 10;
-      const TileSub u = Ss[c];
-      const int b = u.b;
-      const cdf* Ub = Us + u.u_off;
-      const cdf* Pk = Sp + u.off + k;  // member l of this block at Pk[l * G]
+      const int b = ts[q].b, a = ts[q].a;
+      const cdf* Ub = Us + ts[q].u;
+      const cdf* Pk = Sp + ts[q].pk;  // member l of this block at Pk[l * G]
       if (!ADJ) {
         dfacc ar, ai;
         acc_zero(ar);
         acc_zero(ai);
-        for (int l = 0; l < b; ++l) cmac_cb<REALU, false>(ar, ai, Ub[a * b + l], Pk[l * G], (a ^ l) & 1);
+        cb_dot<REALU, false>(ar, ai, Ub, 1, Pk, G, b, a);  // row a of U: entry l imaginary when a + l is odd
         const cdf o = make_cdf(acc_get(ar), acc_get(ai));
         psi[x] = o;
-        if (store) __stcs(store + tile * (TILE_T * S) + threadIdx.x + q * TILE_T, o);
+        if (store) __stcs(store + (tile * TS + (int)threadIdx.x + q * TILE_T), o);
         continue;
       }
-      const cdf* Lk = Sl + u.off + k;
+      const cdf* Lk = Sl + ts[q].pk;
       if (a + 1 < b) {  // gradient term of the generator entries (a, a+1) and (a+1, a)
         const cdf lk = Lk[a * G], lk1 = Lk[(a + 1) * G];
         const cdf pk = Pk[a * G], pk1 = Pk[(a + 1) * G];
-        const df Fk = df_make(Fs[u.f_off + a].x, Fs[u.f_off + a].y);
+        const df Fk = df_make(ts[q].fh, ts[q].fl);
         if (cpr != 0.f) {  // Re z_a
           dfacc z;
           acc_zero(z);
@@ -227,11 +270,11 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
           acc_mac(gacc, Fk, df_make(-zi.h * cpi, -zi.l * cpi));
         }
       }
-      if (STORED) {  // lambda <- U^dag lambda
+      if (STORED) {  // lambda <- U^dag lambda (column a of U, conjugated)
         dfacc br, bi;
         acc_zero(br);
         acc_zero(bi);
-        for (int l = 0; l < b; ++l) cmac_cb<REALU, true>(br, bi, Ub[l * b + a], Lk[l * G], (a ^ l) & 1);
+        cb_dot<REALU, true>(br, bi, Ub, b, Lk, G, b, a);
         lam[x] = make_cdf(acc_get(br), acc_get(bi));
         continue;
       }
@@ -240,12 +283,7 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
       acc_zero(ai);
       acc_zero(br);
       acc_zero(bi);
-      for (int l = 0; l < b; ++l) {  // psi <- U^dag psi, lambda <- U^dag lambda
-        const cdf uu = Ub[l * b + a];
-        const int odd = (a ^ l) & 1;
-        cmac_cb<REALU, true>(ar, ai, uu, Pk[l * G], odd);
-        cmac_cb<REALU, true>(br, bi, uu, Lk[l * G], odd);
-      }
+      cb_dot2<REALU, true>(ar, ai, br, bi, Ub, b, Pk, Lk, G, b, a);  // psi <- U^dag psi, lambda <- U^dag lambda
       psi[x] = make_cdf(acc_get(ar), acc_get(ai));
       lam[x] = make_cdf(acc_get(br), acc_get(bi));
     }
@@ -259,8 +297,8 @@ __device__ __forceinline__ void tile_gate_range(const TypeDesc& t, const TileMap
         x1[q] = xn[q];
       }
     }
-    stg = (stg + 1) % NST;
-    tile += t_step;
+    so = so + kStageB == (unsigned)NST * kStageB ? 0u : so + kStageB;
+    tile += tstep;
   }
   cp_async_wait<0>();  // nothing stays in flight into shared memory past the call
 }

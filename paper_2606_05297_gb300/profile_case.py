@@ -9,7 +9,9 @@ bkc8 (Kitaev chain + Kerr L=8, d=8, 8,388,608 amplitudes), bkc10 (L=10, d=6,
 30,233,088 amplitudes).  Each repetition runs one cvq_energy_and_grad call
 (depth forward gates, one H psi, depth reverse steps) and one pool screen.
 mlp: each repetition runs one forward and one backward of the proposal
-scorer on a 210-row pool (the L=10 Kitaev pool's size).
+scorer on a 210-row pool (the L=10 Kitaev pool's size).  c4: each repetition
+is one batched energy-and-gradient evaluation of the 64-instance Bose-Hubbard
+sweep (one graph launch).
 """
 from __future__ import annotations
 
@@ -39,7 +41,7 @@ def make(workload: str):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="bh12", choices=["bh12", "bkc8", "bkc10", "mlp"])
+    ap.add_argument("--workload", default="bh12", choices=["bh12", "bkc8", "bkc10", "mlp", "c4"])
     ap.add_argument("--depth", type=int, default=40)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0)
@@ -57,6 +59,31 @@ def main():
     from paper_2606_05297_gb300 import build, cvq
     from paper_2606_05297_gb300 import workloads as W
     build.build()
+    if a.workload == "c4":  # the 64-instance sweep: batched evaluations (tile 4096, 2 CTAs per SM)
+        import numpy as np
+        from paper_2606_05297_gb300 import batched
+        data = batched.c4_batch_inputs(a.seed, 64, 8)
+        sectors = [cvq.Sector(m) for m, _, _, _ in data]
+        pools = [cvq.Pool(s, ops) for s, (_, ops, _, _) in zip(sectors, data)]
+        psi0 = [s.basis_state(W.mott_occupation(m.L, m.N)) for s, (m, _, _, _) in zip(sectors, data)]
+        b = cvq.Batch(sectors, pools, max(len(ids) for _, _, ids, _ in data))
+        b.set_ansatz([ids for _, _, ids, _ in data], psi0)
+        flat = np.concatenate([th for _, _, _, th in data])
+        b.theta[: flat.size].copy_(torch.from_numpy(flat))
+        b.set_schedule(4096, 2)
+        for _ in range(max(a.warm, 1)):
+            b.energy_and_grad()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        t0 = time.perf_counter()
+        for _ in range(a.reps):
+            E, _g = b.energy_and_grad()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        torch.cuda.profiler.stop()
+        print(f"c4: instances=64 amplitudes={sum(s.dim for s in sectors)} {b.info()} E[0]={E[0].item():.12f} "
+              f"{dt / a.reps * 1e3:.2f} ms/eval")
+        return
     if a.workload == "mlp":
         sc = cvq.Scorer(210, seed=a.seed)
         X = torch.from_numpy(W.scorer_inputs(210, a.seed + 1)).cuda()
