@@ -602,6 +602,33 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;  // valid in thread 0
 }
 
+// CTA sums of m <= N values per thread with two barriers in all, where N calls
+// of block_sum take 2 N: each warp reduces every value with block_sum's
+// shuffle tree, then thread k adds the eight warps' sums of value k in the
+// order of block_sum's second tree (lanes 8..31 of that tree hold zeros, and
+// adding zero is exact), so each result equals block_sum's bit for bit.
+// val(k) gives value k; it is evaluated for k < m only.  Returns the sum of
+// value k in thread k < min(m, N), 0 elsewhere.
+template <int N, class V>
+__device__ __forceinline__ double block_sums(V&& val, int m) {
+  static_assert(NTHREADS == 256, "the cross-warp order below is block_sum's for eight warps");
+  __shared__ double red[N][NTHREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // an earlier call's threads may still read red
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k < m) {
+      double x = val(k);
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) red[k][warp] = x;
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x >= min(m, N)) return 0.0;
+  const double* r = red[threadIdx.x];
+  return ((r[0] + r[4]) + (r[2] + r[6])) + ((r[1] + r[5]) + (r[3] + r[7]));
+}
+
 template <class T>
 __device__ __forceinline__ void load_G(T (*Gs)[DMAX + 1], const SectorDev& S) {
   const int64_t* src = &S.tab->G[0][0];

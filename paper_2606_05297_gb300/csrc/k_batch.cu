@@ -162,13 +162,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         diag_run_range<KIND, ADJ, BATCH_RUN>(S, G64, T, TP, sg, I.psi, I.psi, I.lam, it.a + threadIdx.x, it.b,
                                              NTHREADS, acc);
       if (ADJ) {
-#pragma unroll
-        for (int q = 0; q < BATCH_RUN; ++q) {
-          if (q < sg.m) {
-            const double s = block_sum(acc_to_double(acc[q]));
-            if (threadIdx.x == 0) partial[it.slot + q] = s;
-          }
-        }
+        const double s = block_sums<BATCH_RUN>([&](int q) { return acc_to_double(acc[q]); }, sg.m);
+        if ((int)threadIdx.x < min(sg.m, BATCH_RUN)) partial[it.slot + threadIdx.x] = s;
       }
     } else if (it.kind == BI_TILE) {  // tiles [a, b) of a block gate
       const GateArg& ga = I.ops[ids[I.ids_off + segs[it.seg].k0]];
@@ -329,21 +324,14 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       dfacc zr[SCREEN_CHUNK], zi[SCREEN_CHUNK];
       screen_chunk<KIND>(S, G64, sq, isdg, desc + (isdg ? sc.dg_off : sc.sh_off) + base, cnt, I.psi, I.lam,
                          it.a + threadIdx.x, it.b, NTHREADS, zr, zi);
-#pragma unroll
-      for (int q = 0; q < SCREEN_CHUNK; ++q) {
-        if (q >= cnt) continue;
-        if (isdg) {
-          const double r = block_sum(acc_to_double(zr[q]));
-          if (threadIdx.x == 0) partial[(size_t)it.slot + 2 * sc.nsh + base + q] = r;
-        } else {
-          const double r = block_sum(acc_to_double(zr[q]));
-          const double im = block_sum(acc_to_double(zi[q]));
-          if (threadIdx.x == 0) {
-            partial[(size_t)it.slot + 2 * (base + q)] = r;
-            partial[(size_t)it.slot + 2 * (base + q) + 1] = im;
-          }
-        }
-      }
+      // one reduction for the chunk, laid out as in k_screen
+      const int m = isdg ? cnt : 2 * cnt, q = threadIdx.x;
+      const double s = block_sums<2 * SCREEN_CHUNK>(
+          [&](int k) {
+            return acc_to_double(isdg ? zr[k & (SCREEN_CHUNK - 1)] : ((k & 1) ? zi[k >> 1] : zr[k >> 1]));
+          },
+          m);
+      if (q < m) partial[(size_t)it.slot + (isdg ? 2 * sc.nsh + base + q : 2 * base + q)] = s;
     }
     __syncthreads();  // S and the item number are reused by the next item
   }
@@ -445,13 +433,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (adj) diag_run_range<KIND, true, BATCH_RUN>(S, G64, T, TP, sg, psi, psi, lam, threadIdx.x, dim, NTHREADS, acc);
       else diag_run_range<KIND, false, BATCH_RUN>(S, G64, T, TP, sg, psi, psi, lam, threadIdx.x, dim, NTHREADS, acc);
       if (adj) {
-#pragma unroll
-        for (int q = 0; q < BATCH_RUN; ++q) {
-          if (q < sg.m) {
-            const double s = block_sum(acc_to_double(acc[q]));
-            if (threadIdx.x == 0) grad[I.theta_off + sg.k0 + q] = 2.0 * s;
-          }
-        }
+        const double s = block_sums<BATCH_RUN>([&](int q) { return acc_to_double(acc[q]); }, sg.m);
+        if ((int)threadIdx.x < min(sg.m, BATCH_RUN)) grad[I.theta_off + sg.k0 + threadIdx.x] = 2.0 * s;
       }
     } else {
       const TypeDesc& t = td_all[k];

@@ -76,21 +76,16 @@ __global__ void __launch_bounds__(NTHREADS) k_screen(const __grid_constant__ Sec
     dfacc zr[SCREEN_CHUNK], zi[SCREEN_CHUNK];
     screen_chunk<KIND>(S, Gs, sq, isdg, (isdg ? a.dg : a.sh) + base, cnt, psi, sigma,
                        (int64_t)blockIdx.x * blockDim.x + threadIdx.x, S.dim, (int64_t)gridDim.x * blockDim.x, zr, zi);
-#pragma unroll
-    for (int k = 0; k < SCREEN_CHUNK; ++k) {
-      if (k >= cnt) continue;
-      if (isdg) {
-        const double r = block_sum(acc_to_double(zr[k]));
-        if (threadIdx.x == 0) partial[(size_t)(2 * a.nsh + base + k) * NBLK + blockIdx.x] = r;
-      } else {
-        const double r = block_sum(acc_to_double(zr[k]));
-        const double i = block_sum(acc_to_double(zi[k]));
-        if (threadIdx.x == 0) {
-          partial[(size_t)(2 * (base + k)) * NBLK + blockIdx.x] = r;
-          partial[(size_t)(2 * (base + k) + 1) * NBLK + blockIdx.x] = i;
-        }
-      }
-    }
+    // one reduction for the chunk: value 2k and 2k + 1 are Re Z and Im Z of
+    // shift k (rows 2 (base + k) and 2 (base + k) + 1), or value k is D of
+    // diagonal function k (row 2 nsh + base + k)
+    const int m = isdg ? cnt : 2 * cnt, q = threadIdx.x;
+    const double s = block_sums<2 * SCREEN_CHUNK>(
+        [&](int k) {
+          return acc_to_double(isdg ? zr[k & (SCREEN_CHUNK - 1)] : ((k & 1) ? zi[k >> 1] : zr[k >> 1]));
+        },
+        m);
+    if (q < m) partial[(size_t)(isdg ? 2 * a.nsh + base + q : 2 * base + q) * NBLK + blockIdx.x] = s;
   }
 }
 

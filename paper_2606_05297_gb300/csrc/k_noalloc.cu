@@ -198,12 +198,8 @@ __global__ void __launch_bounds__(NTHREADS) k_screen_noalloc(const __grid_consta
         }
       }
     }
-#pragma unroll
-    for (int q = 0; q < NOALLOC_CHUNK; ++q) {
-      if (q >= cnt) continue;
-      const double r = block_sum(acc_to_double(acc[q]));
-      if (threadIdx.x == 0) partial[(size_t)(c0 + q) * NBLK + blockIdx.x] = r;
-    }
+    const double r = block_sums<NOALLOC_CHUNK>([&](int q) { return acc_to_double(acc[q]); }, cnt);
+    if ((int)threadIdx.x < cnt) partial[(size_t)(c0 + threadIdx.x) * NBLK + blockIdx.x] = r;
   }
 }
 
