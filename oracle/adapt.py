@@ -66,6 +66,7 @@ def run(sector, pool, psi_init, warm_ops=(), warm_theta=(), max_ops=160, grad_to
         if gmax < grad_tol:
             stop = "grad_tol"
             break
+        theta_sel = theta.tolist()  # the parameters of the state this choice was made on
         ops.append(pool[k])
         theta = np.append(theta, 0.0)
         n_adapt += 1
@@ -77,6 +78,7 @@ def run(sector, pool, psi_init, warm_ops=(), warm_theta=(), max_ops=160, grad_to
         res = bfgs.minimize(fg, theta, gtol=tol, max_iter=bfgs_max_iter, H0=H0)
         theta = res["x"]
         H = res["H"]
-        trace.append(dict(kind="adapt", op=k, gmax=gmax, E=res["f"], nfev=res["nfev"], nit=res["nit"]))
+        trace.append(dict(kind="adapt", op=k, gmax=gmax, E=res["f"], nfev=res["nfev"], nit=res["nit"],
+                          theta_sel=theta_sel))
     E_final = fg(theta)[0] if len(ops) else sector.energy(psi_init)[0]
     return dict(ops=ops, theta=theta, trace=trace, E=E_final, stop=stop, n_adapt=n_adapt)

@@ -13,7 +13,8 @@ every test run.
 Targets (files under tests/golden/):
   c1_adapt      Bose-Hubbard open chain L=4, N=4, U=2 from |1111> with the HVA
                 warm start, ADAPT to max|g| < 1e-6 (Sec. IV.B), with the
-                dense exact-diagonalisation E0 (Sec. IV.B stopping rule).
+                dense exact-diagonalisation E0 (Sec. IV.B stopping rule) and
+                the parameters of the state each operator was chosen on.
   c2_screen     Bose-Hubbard periodic L=12, N=12, U/J=3.4: Eq. (grad) for all
                 210 pool elements on a random state.
   c2_depth40    the same sector: E and dE/dtheta (Sec. IV.A/B) of a random
@@ -80,7 +81,8 @@ def c1_adapt():
              "Mott start with the HVA warm start (warm_start_thetas seed 0), to max|g| < 1e-6",
         E0_dense=E0, stop=res["stop"], n_adapt=res["n_adapt"], E_final=float(res["E"]),
         E_warm=float(res["trace"][0]["E"]), ops=[int(t["op"]) for t in steps],
-        gmax=[float(t["gmax"]) for t in steps], E=[float(t["E"]) for t in steps]))
+        gmax=[float(t["gmax"]) for t in steps], E=[float(t["E"]) for t in steps],
+        theta_sel=[[float(v) for v in t["theta_sel"]] for t in steps]))
 
 
 def c2_screen():

@@ -7,7 +7,8 @@ parity test: energies 1e-10 relative, gradients 1e-9 absolute (Sec. IV.A/B
 energy and Eq. (grad) / adjoint gradients).  The 160-gate case bounds the
 drift of the double-float state arithmetic at the gate budget of Sec. IV.B;
 the L=4 Bose-Hubbard run goes to the paper's stopping rule and must make the
-oracle's choices and reach the dense exact-diagonalisation energy.
+oracle's choices and reach the dense exact-diagonalisation energy, and on each
+of the states the oracle chose on, the GPU screen must choose the same way.
 """
 import json
 import os
@@ -130,3 +131,30 @@ def test_c1_adapt_to_the_stopping_rule(torch_cuda):
         assert abs(r["E"] - e) <= 1e-7 * max(1.0, abs(e)), (r["n"], r["E"], e)
     assert abs(res["E"] - d["E0_dense"]) <= 1e-6
     assert abs(d["E_final"] - d["E0_dense"]) <= 1e-6
+
+
+def test_c1_choices_on_the_oracle_states(torch_cuda):
+    """Each of the oracle's 58 ADAPT choices (Sec. IV.B: the pool element of
+    largest |Eq. (grad)|) made again by the GPU on the very state the oracle
+    chose on: its operators and parameters, applied on the GPU and screened
+    there.  This compares the selection rule itself, whatever path the GPU's
+    own BFGS runs take (they can settle in another minimum once rounding
+    moves a line search)."""
+    from paper_2606_05297_gb300 import cvq
+    from paper_2606_05297_gb300.adapt import select
+    d = _load("c1_adapt")
+    m = W.c1_model()
+    pool, warm = W.bh_nn_pool(m), W.hva_layer(m)
+    s = cvq.Sector(m)
+    P = cvq.Pool(s, list(pool) + list(warm))
+    psi0 = s.basis_state(W.mott_occupation(4, 4))
+    warm_ids = [len(pool) + j for j in range(len(warm))]
+    assert len(d["theta_sel"]) == len(d["ops"])
+    for i, (op, gmax, th) in enumerate(zip(d["ops"], d["gmax"], d["theta_sel"])):
+        ids = warm_ids + list(d["ops"][:i])
+        assert len(th) == len(ids)
+        psi = cvq.apply_ansatz(s, P, ids, np.array(th), psi0)
+        g = cvq.screen_pool(s, P, psi, subset=list(range(len(pool)))).cpu().numpy()
+        k, gm = select(g)
+        assert k == op, (i, k, op, sorted(np.abs(g))[-2:])
+        assert abs(gm - gmax) < G_ABS, (i, gm, gmax)
