@@ -1108,8 +1108,9 @@ extern "C" int cvq_screen_pool(const cvq_sector* s, const cvq_pool* p, const cvq
     CVQ_CUDA(launch_screen(s->S, sa, vpsi, vsig, partial, st), "screen");
   }
   {
-    ProfScope ps(KK_REDUCE, st, 8.0 * NBLK * rows, (double)NBLK * rows);
-    CVQ_CUDA(launch_reduce(partial, rows, NBLK, 1.0, z, st), "reduce");
+    const int nb = screen_grid(s->S);
+    ProfScope ps(KK_REDUCE, st, 8.0 * nb * rows, (double)nb * rows);
+    CVQ_CUDA(launch_reduce(partial, rows, nb, 1.0, z, st), "reduce");
   }
   CVQ_CUDA(launch_screen_epilogue(sm, sa.nsh, z, grad_dev, st), "screen epilogue");
   return CVQ_OK;

@@ -573,6 +573,8 @@ cudaError_t launch_scale_inv_sqrt(int64_t dim, cdf* v, const double* n2, cudaStr
 cudaError_t launch_gate_proj_adj(const SectorDev& S, const GateArg& g, const cdf* D, PoolDev P, const cdf* prev,
                                  const cdf* cur, cdf* lam, const double* rdot, const double* n2, double* partial,
                                  cudaStream_t st);
+// CTAs of the screen (at most NBLK): its partials are rows of screen_grid(S) slots.
+int screen_grid(const SectorDev& S);
 cudaError_t launch_screen(const SectorDev& S, const ScreenArg& a, const cdf* psi, const cdf* sigma, double* partial,
                           cudaStream_t st);
 cudaError_t launch_screen_epilogue(const ScreenMap& m, int nsh, const double* z, double* grad, cudaStream_t st);

@@ -3,9 +3,9 @@
 // g_k = 2 Re <H psi|A_k psi>, the fixed-order final reduction, and the
 // Lanczos vector update used for E0.
 //
-// Every kernel runs a fixed grid (NBLK CTAs x NTHREADS threads) in grid-stride
-// loops and leaves one partial sum per CTA, so the reductions are
-// deterministic for a given sector.  The matvec and the screen work on df
+// Every kernel runs a fixed grid (NBLK CTAs x NTHREADS threads, the screen
+// screen_grid CTAs) in grid-stride loops and leaves one partial sum per CTA, so
+// the reductions are deterministic for a given sector.  The matvec and the screen work on df
 // states (df.cuh); the Lanczos update works on the caller's complex128 vectors.
 #include "cvq_internal.cuh"
 #include "k_ham_impl.cuh"
@@ -59,8 +59,12 @@ cudaError_t launch_apply_H(const SectorDev& S, const cdf* psi, cdf* sigma, doubl
 // while each CTA walks its share of the sector, then leave one partial per CTA
 // (rows 2s and 2s + 1 for Re and Im of shift s, row 2 nsh + d for diagonal
 // function d).
+// Resident CTAs per SM: four for the Kitaev chain (64 registers), three for
+// Bose-Hubbard (its rank walk needs about 80).  The grid is that many per SM,
+// screen_grid, so that no second partial wave runs; row e of the partials has
+// one slot per CTA.
 template <int KIND>
-__global__ void __launch_bounds__(NTHREADS) k_screen(const __grid_constant__ SectorDev S,
+__global__ void __launch_bounds__(NTHREADS, KIND == CVQ_BKC ? 4 : 3) k_screen(const __grid_constant__ SectorDev S,
                                                      const __grid_constant__ ScreenArg a, const cdf* __restrict__ psi,
                                                      const cdf* __restrict__ sigma, double* __restrict__ partial) {
   __shared__ int64_t Gs[LMAX][DMAX + 1];
@@ -85,7 +89,7 @@ __global__ void __launch_bounds__(NTHREADS) k_screen(const __grid_constant__ Sec
           return acc_to_double(isdg ? zr[k & (SCREEN_CHUNK - 1)] : ((k & 1) ? zi[k >> 1] : zr[k >> 1]));
         },
         m);
-    if (q < m) partial[(size_t)(isdg ? 2 * a.nsh + base + q : 2 * base + q) * NBLK + blockIdx.x] = s;
+    if (q < m) partial[(size_t)(isdg ? 2 * a.nsh + base + q : 2 * base + q) * gridDim.x + blockIdx.x] = s;
   }
 }
 
@@ -104,11 +108,14 @@ __global__ void k_screen_epilogue(const __grid_constant__ ScreenMap m, int nsh, 
   }
 }
 
+int screen_grid(const SectorDev& S) { return (NBLK / 4) * (S.kind == CVQ_BH ? 3 : 4); }
+
 cudaError_t launch_screen(const SectorDev& S, const ScreenArg& a, const cdf* psi, const cdf* sigma, double* partial,
                           cudaStream_t st) {
   if (a.nsh + a.ndg <= 0) return cudaSuccess;
-  if (S.kind == CVQ_BH) k_screen<CVQ_BH><<<NBLK, NTHREADS, 0, st>>>(S, a, psi, sigma, partial);
-  else k_screen<CVQ_BKC><<<NBLK, NTHREADS, 0, st>>>(S, a, psi, sigma, partial);
+  const int grid = screen_grid(S);
+  if (S.kind == CVQ_BH) k_screen<CVQ_BH><<<grid, NTHREADS, 0, st>>>(S, a, psi, sigma, partial);
+  else k_screen<CVQ_BKC><<<grid, NTHREADS, 0, st>>>(S, a, psi, sigma, partial);
   return cudaGetLastError();
 }
 
